@@ -1,0 +1,164 @@
+/*
+ * msm377 — BLS12-377 G1 multi-scalar multiplication on NVIDIA sm_103a (GB300).
+ *
+ * C-ABI of the library libmsm377.so. The operation is the one arXiv:2502.11660
+ * accelerates: MSM, sum_i s_i * P_i over the BLS12-377 curve with a 377-bit
+ * base field (Abstract; Sec. II-C), computed by Pippenger's bucket method as a
+ * stream of elliptic-curve point additions (PADDs, Sec. II-D).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Field elements: 12 little-endian 32-bit limbs. STANDARD form is the integer
+ *   x in [0, p); MONTGOMERY form is x * 2^384 mod p in [0, p).
+ * - Affine points: x then y (24 u32). The identity O is (0, 0), which is not on
+ *   y^2 = x^3 + 1.
+ * - XYZZ points (x = X/ZZ, y = Y/ZZZ): X, Y, ZZ, ZZZ; the identity has ZZ = 0.
+ * - Scalars: 8 little-endian 32-bit limbs (any 256-bit value is accepted).
+ * - Ownership: the caller allocates and frees every buffer. Pointers are device
+ *   pointers unless the name ends in _host. No call keeps a pointer after it
+ *   returns.
+ * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream). Calls only enqueue work on it and return, except those marked
+ *   "synchronous".
+ * - Inputs out of their stated range (coordinates >= p, points off the curve)
+ *   produce unspecified output values but never out-of-bounds accesses.
+ * - Every call returns a status code below; on MSM377_ECUDA and MSM377_EINVAL,
+ *   msm377_last_error() holds a message.
+ */
+#ifndef MSM377_H
+#define MSM377_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSM377_OK 0
+#define MSM377_EINVAL (-1)   /* bad argument: null pointer, misalignment, size, option */
+#define MSM377_ENOMEM (-2)   /* the workspace passed is smaller than required */
+#define MSM377_ECUDA (-3)    /* a CUDA runtime call failed */
+#define MSM377_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define MSM377_ERANGE (-5)   /* a scalar had bits at or above opts.scalar_bits */
+
+#define MSM377_FORM_STANDARD 0
+#define MSM377_FORM_MONTGOMERY 1
+
+/* Copies the last error message of the calling thread into buf (NUL-terminated,
+ * truncated to len). Returns the length of the full message. */
+int msm377_last_error(char *buf, size_t len);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int msm377_version(void);
+
+/* ------------------------------------------------------------------------
+ * Batched field multiplication (the modular multiplication of Sec. III-C;
+ * here Montgomery's method in place of Barrett's, as Sec. V-C proposes).
+ * out_i = a_i * b_i mod p for i < n.
+ * a, b, out: device, structure-of-arrays [12][n] u32 (limb k of element i at
+ *   k * n + i), 4-byte aligned; out may alias a or b.
+ * form: MSM377_FORM_STANDARD (inputs and result in standard form) or
+ *   MSM377_FORM_MONTGOMERY (inputs and result in Montgomery form).
+ * Results are fully reduced into [0, p). n = 0 is a no-op.
+ */
+int fq_mul_batch(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, int form,
+                 void *stream);
+
+/* Standard <-> Montgomery conversion of n elements, SoA [12][n]; out may alias in. */
+int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
+int fq_from_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched mixed point addition (the bucket-accumulation PADD, Sec. II-D and
+ * the throughput experiment of Sec. V-A): out_i = acc_i + q_i.
+ * acc, out: device, XYZZ in SoA [4][12][n] (coordinate c, limb k, element i at
+ *   (c * 12 + k) * n + i). q: device, affine SoA [2][12][n], (0, 0) = O.
+ * Every case is handled: acc = O, q = O, q = acc (doubling), q = -acc (O).
+ * form: coordinates of acc, q and out in STANDARD or MONTGOMERY form. The output
+ *   is one valid XYZZ representative of the sum (compare after normalising to
+ *   affine: x = X / ZZ, y = Y / ZZZ), fully reduced limbs.
+ * out may alias acc. n = 0 is a no-op.
+ */
+int padd_batch(const uint32_t *acc, const uint32_t *q, uint32_t *out, size_t n, int form,
+               void *stream);
+
+/* Affine normalisation of n XYZZ points (SoA [4][12][n]) into affine SoA [2][12][n],
+ * same form in and out; O maps to (0, 0). */
+int xyzz_to_affine_batch(const uint32_t *xyzz, uint32_t *aff, size_t n, int form, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Fixed-base scalar multiplication by the standard G1 generator G:
+ * out_i = seeds_i * G as affine points, array-of-structures (24 u32 per point,
+ * standard form). seeds: device, 8 u32 per scalar. Used to build synthetic
+ * point sets P_i = s_i * G on the device.
+ */
+int g1_generator_mul(const uint32_t *seeds, size_t n, uint32_t *out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Multi-scalar multiplication (Sec. II-C): out = sum_{i < n} scalars_i * points_i.
+ */
+
+/* opts.flags */
+#define MSM377_POINTS_PREPARED 1u /* points are Montgomery-form (msm_points_prepare output) */
+
+typedef struct msm_opts {
+    int32_t c;             /* window width in bits, 2..20; 0 = chosen from n */
+    int32_t signed_digits; /* 1: digits in (-2^(c-1), 2^(c-1)], buckets 1..2^(c-1);
+                              0: unsigned digits in [0, 2^c), buckets 1..2^c-1 */
+    int32_t scalar_bits;   /* caller's bound: every scalar < 2^scalar_bits (1..256);
+                              0 = 256. A larger scalar makes the call fail with
+                              MSM377_ERANGE (reported through the workspace status). */
+    uint32_t flags;        /* MSM377_POINTS_PREPARED */
+    void *stream;          /* cudaStream_t */
+} msm_opts;
+
+/* Workspace bytes msm_g1 needs for n points with these options (0 on bad options). */
+size_t msm_g1_workspace_bytes(size_t n, const msm_opts *opts);
+
+/* Window width msm_g1 uses for n points when opts.c == 0. */
+int msm_g1_default_c(size_t n, int signed_digits);
+
+/* Converts n affine points in standard form (array-of-structures, 24 u32 per point,
+ * 16-byte aligned) into the resident Montgomery form that msm_g1 reads with
+ * MSM377_POINTS_PREPARED (same layout and size: 96 bytes per point). out may
+ * alias in. */
+int msm_points_prepare(const uint32_t *points_std, size_t n, uint32_t *out, void *stream);
+
+/* points: device, 24 u32 per point (standard form, or prepared with the flag),
+ *   16-byte aligned. scalars: device, 8 u32 per scalar, 16-byte aligned.
+ * out: device, 24 u32: the affine sum in standard form, (0, 0) for O.
+ * workspace: device, >= msm_g1_workspace_bytes(n, opts), 256-byte aligned; the
+ *   first 4 bytes hold the call's device status (0 or a negative code), readable
+ *   with msm_g1_status once the stream has reached the end of the call.
+ * Asynchronous on opts->stream. n = 0 writes O.
+ */
+int msm_g1(const uint32_t *points, const uint32_t *scalars, size_t n, uint32_t *out,
+           void *workspace, size_t workspace_bytes, const msm_opts *opts);
+
+/* Synchronous: waits for opts->stream and returns the device status word of the
+ * last msm_g1 / msm_g1_batched that used this workspace. */
+int msm_g1_status(const void *workspace, const msm_opts *opts);
+
+/* End-to-end variant on host buffers (synchronous): copies points_host (24 u32
+ * per point, standard form) and scalars_host (8 u32 per scalar) into the
+ * workspace, runs msm_g1 and copies the 24-u32 result into out_host. Host
+ * buffers may be pageable; pinned buffers copy faster. workspace must hold
+ * msm_g1_host_workspace_bytes(n, opts) bytes. Returns the device status. */
+size_t msm_g1_host_workspace_bytes(size_t n, const msm_opts *opts);
+int msm_g1_host(const uint32_t *points_host, const uint32_t *scalars_host, size_t n,
+                uint32_t *out_host, void *workspace, size_t workspace_bytes,
+                const msm_opts *opts);
+
+/* ------------------------------------------------------------------------
+ * Micro-benchmark for the roofline denominator: runs `iters` rounds of
+ * independent mad.lo.cc / madc.hi.cc pairs on every SM and writes the measured
+ * count of 32x32->64 limb products per second into *products_per_s. Synchronous.
+ */
+int msm377_imad_probe(int iters, double *products_per_s, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSM377_H */

@@ -1,0 +1,182 @@
+"""BLS12-377 G1 multi-scalar multiplication on sm_103a — Python binding of libmsm377.
+
+Argument marshalling only: every call goes straight to the C-ABI in
+include/msm377.h with device pointers taken from torch tensors (torch provides
+device memory and streams). Arrays of 32-bit limbs are carried in torch.int32
+tensors holding the u32 bit patterns.
+
+Layouts (see the header): field batches are structure-of-arrays [12][n];
+XYZZ batches [4][12][n]; affine batches [2][12][n]; MSM points are
+array-of-structures (n, 24) and scalars (n, 8).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import MsmError, MsmOpts, check, last_error, lib
+
+FORM_STANDARD = 0
+FORM_MONTGOMERY = 1
+POINTS_PREPARED = 1
+
+__all__ = [
+    "MsmError", "MsmOpts", "FORM_STANDARD", "FORM_MONTGOMERY", "POINTS_PREPARED",
+    "to_device", "to_host", "fq_mul_batch", "fq_to_montgomery", "fq_from_montgomery",
+    "padd_batch", "xyzz_to_affine_batch", "g1_generator_mul", "msm_points_prepare",
+    "msm_g1", "msm_g1_workspace", "msm_g1_host", "msm_g1_status", "msm_g1_default_c",
+    "imad_probe", "lib", "last_error",
+]
+
+
+def to_device(arr: np.ndarray, device="cuda") -> torch.Tensor:
+    """u32 numpy array -> int32 torch tensor on the device (same bits)."""
+    a = np.ascontiguousarray(arr, dtype=np.uint32)
+    return torch.from_numpy(a.view(np.int32)).to(device)
+
+
+def to_host(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().contiguous().numpy().view(np.uint32)
+
+
+def _p(t: torch.Tensor | None):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _s(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _check_dev(*ts):
+    for t in ts:
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("expected contiguous CUDA tensors")
+
+
+def fq_mul_batch(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None,
+                 form: int = FORM_STANDARD, stream=None) -> torch.Tensor:
+    n = a.shape[-1]
+    out = torch.empty_like(a) if out is None else out
+    _check_dev(a, b, out)
+    check(lib().fq_mul_batch(_p(a), _p(b), _p(out), n, form, _s(stream)))
+    return out
+
+
+def fq_to_montgomery(x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    out = torch.empty_like(x) if out is None else out
+    _check_dev(x, out)
+    check(lib().fq_to_montgomery(_p(x), _p(out), x.shape[-1], _s(stream)))
+    return out
+
+
+def fq_from_montgomery(x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    out = torch.empty_like(x) if out is None else out
+    _check_dev(x, out)
+    check(lib().fq_from_montgomery(_p(x), _p(out), x.shape[-1], _s(stream)))
+    return out
+
+
+def padd_batch(acc: torch.Tensor, q: torch.Tensor, out: torch.Tensor | None = None,
+               form: int = FORM_STANDARD, stream=None) -> torch.Tensor:
+    n = acc.shape[-1]
+    out = torch.empty_like(acc) if out is None else out
+    _check_dev(acc, q, out)
+    check(lib().padd_batch(_p(acc), _p(q), _p(out), n, form, _s(stream)))
+    return out
+
+
+def xyzz_to_affine_batch(xyzz: torch.Tensor, form: int = FORM_STANDARD, stream=None) -> torch.Tensor:
+    n = xyzz.shape[-1]
+    out = torch.empty((2, 12, n), dtype=torch.int32, device=xyzz.device)
+    _check_dev(xyzz)
+    check(lib().xyzz_to_affine_batch(_p(xyzz), _p(out), n, form, _s(stream)))
+    return out
+
+
+def g1_generator_mul(seeds: torch.Tensor, stream=None) -> torch.Tensor:
+    """seeds (n, 8) -> points (n, 24), P_i = seeds_i * G."""
+    n = seeds.shape[0]
+    out = torch.empty((n, 24), dtype=torch.int32, device=seeds.device)
+    _check_dev(seeds)
+    check(lib().g1_generator_mul(_p(seeds), n, _p(out), _s(stream)))
+    return out
+
+
+def msm_points_prepare(points: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    out = torch.empty_like(points) if out is None else out
+    _check_dev(points, out)
+    check(lib().msm_points_prepare(_p(points), points.shape[0], _p(out), _s(stream)))
+    return out
+
+
+def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0) -> MsmOpts:
+    """stream=0 for size queries (no CUDA context needed); None = torch's current stream."""
+    sv = 0 if (isinstance(stream, int) and stream == 0) else _s(stream).value
+    return MsmOpts(int(c), 1 if signed else 0, int(scalar_bits), POINTS_PREPARED if prepared else 0, sv)
+
+
+def msm_g1_default_c(n: int, signed: bool = True) -> int:
+    return lib().msm_g1_default_c(n, 1 if signed else 0)
+
+
+def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, device="cuda") -> torch.Tensor:
+    o = _opts(c, signed, scalar_bits, prepared)
+    nbytes = lib().msm_g1_workspace_bytes(n, ctypes.byref(o))
+    if nbytes == 0:
+        raise MsmError(-1, "bad MSM options")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None = None,
+           workspace: torch.Tensor | None = None, c: int = 0, signed: bool = True,
+           scalar_bits: int = 0, prepared: bool = False, stream=None) -> torch.Tensor:
+    """Enqueues sum_i scalars_i * points_i; returns the (24,) int32 device tensor it writes."""
+    n = points.shape[0]
+    if scalars.shape[0] != n:
+        raise ValueError("points and scalars differ in length")
+    o = _opts(c, signed, scalar_bits, prepared, None if stream is None else stream)
+    if workspace is None:
+        workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared, points.device)
+    out = torch.empty(24, dtype=torch.int32, device=points.device) if out is None else out
+    _check_dev(points, scalars, out, workspace)
+    check(lib().msm_g1(_p(points), _p(scalars), n, _p(out), _p(workspace), workspace.numel(),
+                       ctypes.byref(o)))
+    return out
+
+
+def msm_g1_status(workspace: torch.Tensor, stream=None) -> int:
+    o = _opts(stream=None if stream is None else stream)
+    return lib().msm_g1_status(_p(workspace), ctypes.byref(o))
+
+
+def msm_g1_host(points: np.ndarray, scalars: np.ndarray, workspace: torch.Tensor | None = None,
+                c: int = 0, signed: bool = True, scalar_bits: int = 0, stream=None) -> np.ndarray:
+    """Synchronous MSM on host arrays (copies in and out inside the call)."""
+    pts = np.ascontiguousarray(points, dtype=np.uint32)
+    sc = np.ascontiguousarray(scalars, dtype=np.uint32)
+    n = pts.shape[0]
+    o = _opts(c, signed, scalar_bits, False, None if stream is None else stream)
+    need = lib().msm_g1_host_workspace_bytes(n, ctypes.byref(o))
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    out = np.zeros(24, dtype=np.uint32)
+    check(lib().msm_g1_host(pts.ctypes.data_as(ctypes.c_void_p), sc.ctypes.data_as(ctypes.c_void_p), n,
+                            out.ctypes.data_as(ctypes.c_void_p), _p(workspace), workspace.numel(),
+                            ctypes.byref(o)))
+    return out
+
+
+def msm_g1_host_workspace_bytes(n: int, c=0, signed=True, scalar_bits=0) -> int:
+    o = _opts(c, signed, scalar_bits)
+    return lib().msm_g1_host_workspace_bytes(n, ctypes.byref(o))
+
+
+def imad_probe(iters: int = 20000, stream=None) -> float:
+    """Measured 32x32->64 limb products per second over all SMs."""
+    v = ctypes.c_double(0.0)
+    check(lib().msm377_imad_probe(iters, ctypes.byref(v), _s(stream)))
+    return v.value

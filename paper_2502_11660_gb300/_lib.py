@@ -1,0 +1,82 @@
+"""Loads libmsm377.so and declares the C signatures of include/msm377.h.
+
+There is no fallback: if the library cannot be built or loaded, every call
+raises. The library is built in-tree on first use when it is missing or older
+than its sources.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+c_u32p = ctypes.c_void_p   # device pointers travel as plain addresses
+c_size = ctypes.c_size_t
+c_int = ctypes.c_int
+c_void = ctypes.c_void_p
+
+
+class MsmOpts(ctypes.Structure):
+    _fields_ = [
+        ("c", ctypes.c_int32),
+        ("signed_digits", ctypes.c_int32),
+        ("scalar_bits", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+SIGNATURES = {
+    "msm377_last_error": (c_int, [ctypes.c_char_p, c_size]),
+    "msm377_version": (c_int, []),
+    "fq_mul_batch": (c_int, [c_u32p, c_u32p, c_u32p, c_size, c_int, c_void]),
+    "fq_to_montgomery": (c_int, [c_u32p, c_u32p, c_size, c_void]),
+    "fq_from_montgomery": (c_int, [c_u32p, c_u32p, c_size, c_void]),
+    "padd_batch": (c_int, [c_u32p, c_u32p, c_u32p, c_size, c_int, c_void]),
+    "xyzz_to_affine_batch": (c_int, [c_u32p, c_u32p, c_size, c_int, c_void]),
+    "g1_generator_mul": (c_int, [c_u32p, c_size, c_u32p, c_void]),
+    "msm_g1_workspace_bytes": (c_size, [c_size, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_default_c": (c_int, [c_size, c_int]),
+    "msm_points_prepare": (c_int, [c_u32p, c_size, c_u32p, c_void]),
+    "msm_g1": (c_int, [c_u32p, c_u32p, c_size, c_u32p, c_void, c_size, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_status": (c_int, [c_void, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_host_workspace_bytes": (c_size, [c_size, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_host": (c_int, [c_void, c_void, c_size, c_void, c_void, c_size, ctypes.POINTER(MsmOpts)]),
+    "msm377_imad_probe": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_void]),
+}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class MsmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"msm377 error {code}: {msg}")
+        self.code = code
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(512)
+    lib().msm377_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def check(rc: int) -> int:
+    if rc != 0:
+        raise MsmError(rc, last_error())
+    return rc

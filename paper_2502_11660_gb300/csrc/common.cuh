@@ -1,0 +1,35 @@
+// Shared host-side helpers of the msm377 library: error reporting, status
+// codes, alignment and stream casting.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/msm377.h"
+
+namespace msm377 {
+
+// Records a message for msm377_last_error (thread-local) and returns `code`.
+int set_error(int code, const char* fmt, ...);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Checks the launch that was just enqueued.
+int check_launch(const char* what);
+
+inline unsigned grid_for(size_t n, unsigned block) {
+    return static_cast<unsigned>((n + block - 1) / block);
+}
+
+}  // namespace msm377
+
+#define MSM_CUDA_TRY(expr)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return ::msm377::set_error(MSM377_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)

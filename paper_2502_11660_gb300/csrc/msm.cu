@@ -1,0 +1,726 @@
+// Pippenger multi-scalar multiplication over BLS12-377 G1 (Sec. II-C of the
+// paper: windows, bucket accumulation, bucket aggregation, group aggregation),
+// laid out for one GB300.
+//
+// Stages, all on the caller's stream:
+//  1. prepare   standard affine -> Montgomery affine (96 B per point, AoS, so a
+//               random gather of one point reads three full 32 B sectors)
+//  2. digits    c-bit window digits per scalar (signed or unsigned);
+//               key = |digit|, value = point index | sign << 31, window-major
+//  3. sort      stable LSD radix sort of (key, value) within each window,
+//               8-bit digits per pass (histogram, scans, ranked scatter)
+//  4. accumulate  the sorted stream is cut into equal chunks of K items, one per
+//               thread, so heavy buckets are spread across threads and warps;
+//               runs inside a chunk are summed with mixed PADDs and written to
+//               their bucket, runs that cross a chunk edge leave partial sums
+//  5. merge     partial sums of runs that cross chunk edges are added up
+//  6. reduce    per window sum_b b * B_b: segments of L buckets by running sums
+//               (in-thread), then sum_g g * Y_g split by the bits of g into
+//               independent sums, recombined by Horner
+//  7. combine   sum_j 2^(c j) S_j by Horner, affine normalisation, standard form
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "ec.cuh"
+
+namespace {
+
+using ec::affine;
+using ec::xyzz;
+using fq::fe;
+
+constexpr uint32_t kNone = 0xffffffffu;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
+constexpr int kRadix = 256;
+
+// ---------------------------------------------------------------- memory I/O
+
+__device__ __forceinline__ void load_affine(affine& Q, const uint4* __restrict__ pts, uint32_t idx) {
+    const uint4* p = pts + 6 * (size_t)idx;
+    uint4 a = __ldg(p + 0), b = __ldg(p + 1), c = __ldg(p + 2);
+    uint4 d = __ldg(p + 3), e = __ldg(p + 4), f = __ldg(p + 5);
+    Q.x.v[0] = a.x; Q.x.v[1] = a.y; Q.x.v[2] = a.z; Q.x.v[3] = a.w;
+    Q.x.v[4] = b.x; Q.x.v[5] = b.y; Q.x.v[6] = b.z; Q.x.v[7] = b.w;
+    Q.x.v[8] = c.x; Q.x.v[9] = c.y; Q.x.v[10] = c.z; Q.x.v[11] = c.w;
+    Q.y.v[0] = d.x; Q.y.v[1] = d.y; Q.y.v[2] = d.z; Q.y.v[3] = d.w;
+    Q.y.v[4] = e.x; Q.y.v[5] = e.y; Q.y.v[6] = e.z; Q.y.v[7] = e.w;
+    Q.y.v[8] = f.x; Q.y.v[9] = f.y; Q.y.v[10] = f.z; Q.y.v[11] = f.w;
+}
+
+__device__ __forceinline__ void load_fe4(fe& a, const uint4* p) {
+    uint4 u0 = p[0], u1 = p[1], u2 = p[2];
+    a.v[0] = u0.x; a.v[1] = u0.y; a.v[2] = u0.z; a.v[3] = u0.w;
+    a.v[4] = u1.x; a.v[5] = u1.y; a.v[6] = u1.z; a.v[7] = u1.w;
+    a.v[8] = u2.x; a.v[9] = u2.y; a.v[10] = u2.z; a.v[11] = u2.w;
+}
+
+__device__ __forceinline__ void store_fe4(uint4* p, const fe& a) {
+    p[0] = make_uint4(a.v[0], a.v[1], a.v[2], a.v[3]);
+    p[1] = make_uint4(a.v[4], a.v[5], a.v[6], a.v[7]);
+    p[2] = make_uint4(a.v[8], a.v[9], a.v[10], a.v[11]);
+}
+
+// XYZZ point in memory: 12 uint4 (X, Y, ZZ, ZZZ).
+__device__ __forceinline__ void load_xyzz(xyzz& P, const uint4* p) {
+    load_fe4(P.X, p);
+    load_fe4(P.Y, p + 3);
+    load_fe4(P.ZZ, p + 6);
+    load_fe4(P.ZZZ, p + 9);
+}
+
+__device__ __forceinline__ void store_xyzz(uint4* p, const xyzz& P) {
+    store_fe4(p, P.X);
+    store_fe4(p + 3, P.Y);
+    store_fe4(p + 6, P.ZZ);
+    store_fe4(p + 9, P.ZZZ);
+}
+
+// ---------------------------------------------------------------- stage 1
+
+__global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    fe x, y;
+    load_fe4(x, in + 6 * i);
+    load_fe4(y, in + 6 * i + 3);
+    fq::to_mont(x, x);
+    fq::to_mont(y, y);
+    store_fe4(out + 6 * i, x);
+    store_fe4(out + 6 * i + 3, y);
+}
+
+// ---------------------------------------------------------------- stage 2
+
+__global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int W, int sgn,
+                         int bits, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                         int* __restrict__ status) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint4 lo = scalars[2 * i], hi = scalars[2 * i + 1];
+    uint32_t s[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    if (bits < 256) {
+        uint32_t over = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int lo_bit = 32 * k;
+            uint32_t m = lo_bit >= bits ? 0xffffffffu
+                         : (bits - lo_bit >= 32 ? 0u : ~((1u << (bits - lo_bit)) - 1u));
+            over |= s[k] & m;
+        }
+        if (over) atomicExch(status, MSM377_ERANGE);
+    }
+    const uint32_t cmask = (1u << c) - 1u, half = 1u << (c - 1);
+    uint32_t carry = 0;
+    for (int j = 0; j < W; ++j) {
+        int b0 = j * c, w = b0 >> 5, off = b0 & 31;
+        uint32_t raw = 0;
+        if (w < 8) {
+            raw = s[w] >> off;
+            if (off + c > 32 && w + 1 < 8) raw |= s[w + 1] << (32 - off);
+            raw &= cmask;
+        }
+        uint32_t key, neg = 0;
+        if (sgn) {
+            uint32_t v = raw + carry;
+            if (v > half) {
+                key = (1u << c) - v;  // |v - 2^c|
+                neg = 1;
+                carry = 1;
+            } else {
+                key = v;
+                carry = 0;
+            }
+        } else {
+            key = raw;
+        }
+        keys[(size_t)j * n + i] = key;
+        vals[(size_t)j * n + i] = (uint32_t)i | (neg << 31);
+    }
+}
+
+// ---------------------------------------------------------------- stage 3: radix sort
+
+__global__ void k_sort_hist(const uint32_t* __restrict__ keys, size_t n, int shift, size_t tiles,
+                            uint32_t* __restrict__ hist) {
+    __shared__ uint32_t cnt[kRadix];
+    const size_t t = blockIdx.x, w = blockIdx.y;
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t* seg = keys + w * n;
+    const size_t start = t * kSortTile;
+#pragma unroll
+    for (int e = 0; e < kSortItems; ++e) {
+        size_t idx = start + (size_t)e * kSortThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&cnt[(seg[idx] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(w * kRadix + threadIdx.x) * tiles + t] = cnt[threadIdx.x];
+}
+
+// Exclusive block-wide scan of one value per thread (256 threads).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warp_sums[kSortThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < kSortThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kSortThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t before = wid ? warp_sums[wid - 1] : 0;
+    if (total) *total = warp_sums[kSortThreads / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// For each (window, digit): exclusive scan over tiles in place; the digit total goes to dtot.
+__global__ void k_sort_scan_tiles(uint32_t* __restrict__ hist, size_t tiles, uint32_t* __restrict__ dtot) {
+    const size_t d = blockIdx.x, w = blockIdx.y;
+    uint32_t* row = hist + (w * kRadix + d) * tiles;
+    const size_t per = (tiles + kSortThreads - 1) / kSortThreads;
+    const size_t lo = threadIdx.x * per;
+    uint32_t local = 0;
+    for (size_t k = 0; k < per; ++k)
+        if (lo + k < tiles) local += row[lo + k];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(local, &total);
+    for (size_t k = 0; k < per; ++k) {
+        if (lo + k < tiles) {
+            uint32_t c = row[lo + k];
+            row[lo + k] = run;
+            run += c;
+        }
+    }
+    if (threadIdx.x == 0) dtot[w * kRadix + d] = total;
+}
+
+__global__ void k_sort_scan_digits(uint32_t* __restrict__ dtot) {
+    uint32_t* row = dtot + blockIdx.x * kRadix;
+    uint32_t v = row[threadIdx.x];
+    uint32_t ex = block_exclusive_scan(v, nullptr);
+    row[threadIdx.x] = ex;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, size_t n, int shift, size_t tiles, const uint32_t* __restrict__ hist,
+    const uint32_t* __restrict__ doff) {
+    __shared__ uint32_t wcnt[kSortThreads / 32][kRadix];
+    __shared__ uint32_t base[kRadix];
+    const size_t t = blockIdx.x, w = blockIdx.y;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * kRadix; k += kSortThreads)
+        (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const size_t seg = w * n;
+    const size_t sub = t * kSortTile + (size_t)wid * (32 * kSortItems);
+    uint32_t key[kSortItems], val[kSortItems], dig[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        size_t idx = sub + (size_t)r * 32 + lane;
+        bool valid = idx < n;
+        key[r] = valid ? kin[seg + idx] : 0u;
+        val[r] = valid ? vin[seg + idx] : 0u;
+        // Items past the end sort last in the tile and are never written.
+        dig[r] = valid ? ((key[r] >> shift) & (kRadix - 1)) : (kRadix - 1);
+        uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
+        uint32_t before = wcnt[wid][dig[r]];
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) wcnt[wid][dig[r]] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+#pragma unroll
+        for (int k = 0; k < kSortThreads / 32; ++k) {
+            uint32_t c = wcnt[k][d];
+            wcnt[k][d] = run;
+            run += c;
+        }
+        base[d] = doff[w * kRadix + d] + hist[(w * kRadix + d) * tiles + t];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        size_t idx = sub + (size_t)r * 32 + lane;
+        if (idx < n) {
+            size_t pos = (size_t)base[dig[r]] + wcnt[wid][dig[r]] + rank[r];
+            if (pos < n) {  // always true when the counts agree; keeps writes in bounds
+                kout[seg + pos] = key[r];
+                vout[seg + pos] = val[r];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- stages 4-5
+
+struct AccArgs {
+    const uint32_t* keys;
+    const uint32_t* vals;
+    const uint4* pts;
+    uint4* buckets;      // [W][Bp] XYZZ
+    uint4* head;         // [nchunks] XYZZ
+    uint4* tail;         // [nchunks] XYZZ
+    uint32_t* headflag;  // 0 none, 1 run ends here, 2 run continues past this chunk
+    uint32_t* tailkey;   // composite key of the run leaving this chunk, or kNone
+    size_t N, n, nchunks;
+    uint32_t stride;     // B + 1 (composite key = window * stride + key)
+    uint32_t Bp;
+    int K;
+};
+
+__device__ __forceinline__ uint32_t composite(const AccArgs& a, size_t g) {
+    return (uint32_t)(g / a.n) * a.stride + a.keys[g];
+}
+
+__device__ __forceinline__ void bucket_store(const AccArgs& a, uint32_t ck, const xyzz& P) {
+    uint32_t w = ck / a.stride, key = ck % a.stride;
+    store_xyzz(a.buckets + ((size_t)w * a.Bp + (key - 1)) * 12, P);
+}
+
+__global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
+    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= a.nchunks) return;
+    size_t start = t * (size_t)a.K;
+    size_t end = start + a.K < a.N ? start + a.K : a.N;
+    uint32_t prev = start > 0 ? composite(a, start - 1) : kNone;
+    uint32_t next = end < a.N ? composite(a, end) : kNone;
+    a.tailkey[t] = kNone;
+    a.headflag[t] = 0;
+    xyzz acc;
+    ec::set_inf(acc);
+    uint32_t cur = composite(a, start);
+    bool first = true;
+    for (size_t g = start; g <= end; ++g) {
+        uint32_t ck = g < end ? composite(a, g) : kNone;
+        if (ck != cur) {
+            // flush the run `cur`
+            if (cur % a.stride != 0) {
+                bool sb = first && prev == cur;
+                bool ea = (g == end) && next == cur;
+                if (!sb && !ea) {
+                    bucket_store(a, cur, acc);
+                } else if (sb) {
+                    store_xyzz(a.head + t * 12, acc);
+                    a.headflag[t] = ea ? 2u : 1u;
+                } else {
+                    store_xyzz(a.tail + t * 12, acc);
+                    a.tailkey[t] = cur;
+                }
+            }
+            if (g == end) break;
+            ec::set_inf(acc);
+            cur = ck;
+            first = false;
+        }
+        if (ck % a.stride != 0) {
+            uint32_t v = a.vals[g];
+            if ((v & 0x7fffffffu) >= a.n) continue;  // cannot happen for sorted digit output
+            affine Q;
+            load_affine(Q, a.pts, v & 0x7fffffffu);
+            if (v >> 31) ec::neg(Q);
+            ec::madd(acc, Q);
+        }
+    }
+}
+
+__global__ void k_merge(AccArgs a) {
+    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= a.nchunks) return;
+    uint32_t ck = a.tailkey[t];
+    if (ck == kNone) return;
+    xyzz acc, h;
+    load_xyzz(acc, a.tail + t * 12);
+    for (size_t u = t + 1; u < a.nchunks; ++u) {
+        load_xyzz(h, a.head + u * 12);
+        ec::add(acc, h);
+        if (a.headflag[u] != 2u) break;
+    }
+    bucket_store(a, ck, acc);
+}
+
+// ---------------------------------------------------------------- stage 6
+
+// Thread (w, g): Y = sum_{i=1..L} B[gL+i], V = sum_{i=1..L} i * B[gL+i] (bucket b at index b-1).
+__global__ void k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, size_t W,
+                                  uint32_t G, uint4* __restrict__ Y, uint4* __restrict__ V) {
+    size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= W * G) return;
+    size_t w = id / G, g = id % G;
+    const uint4* seg = buckets + ((size_t)w * Bp + (size_t)g * L) * 12;
+    xyzz T, S, X;
+    ec::set_inf(T);
+    ec::set_inf(S);
+    for (int i = (int)L; i >= 1; --i) {
+        load_xyzz(X, seg + (size_t)(i - 1) * 12);
+        ec::add(T, X);
+        ec::add(S, T);
+    }
+    store_xyzz(Y + id * 12, T);
+    store_xyzz(V + id * 12, S);
+}
+
+// Thread (w, k, q): partial of Z_k = sum_{g in chunk q, bit k of g set} Y_g, or for
+// k == logG the partial of sum_{g in chunk q} V_g.
+__global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__ V, size_t W, uint32_t G,
+                          int logG, uint32_t Q, uint4* __restrict__ P) {
+    size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    size_t per_w = (size_t)(logG + 1) * Q;
+    if (id >= W * per_w) return;
+    size_t w = id / per_w;
+    int k = (int)((id % per_w) / Q);
+    uint32_t q = (uint32_t)(id % Q);
+    uint32_t span = G / Q, g0 = q * span;
+    xyzz acc, X;
+    ec::set_inf(acc);
+    for (uint32_t g = g0; g < g0 + span; ++g) {
+        if (k == logG) {
+            load_xyzz(X, V + ((size_t)w * G + g) * 12);
+        } else {
+            if (!((g >> k) & 1u)) continue;
+            load_xyzz(X, Y + ((size_t)w * G + g) * 12);
+        }
+        ec::add(acc, X);
+    }
+    store_xyzz(P + id * 12, acc);
+}
+
+// out[s][i] = sum_{e < F} in[s][i F + e], segments of m points.
+__global__ void k_sum_segments(const uint4* __restrict__ in, size_t nseg, uint32_t m, uint32_t F,
+                               uint4* __restrict__ out) {
+    size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    uint32_t mo = m / F;
+    if (id >= nseg * mo) return;
+    size_t s = id / mo, i = id % mo;
+    xyzz acc, X;
+    ec::set_inf(acc);
+    for (uint32_t e = 0; e < F; ++e) {
+        load_xyzz(X, in + (s * m + i * F + e) * 12);
+        ec::add(acc, X);
+    }
+    store_xyzz(out + id * 12, acc);
+}
+
+// Thread w: S_w = Z_V + L * sum_k 2^k Z_k (Horner over k), Z laid out [W][logG + 1].
+__global__ void k_window_horner(const uint4* __restrict__ Z, size_t W, int logG, int log2L,
+                                uint4* __restrict__ S) {
+    size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    const uint4* z = Z + w * (size_t)(logG + 1) * 12;
+    xyzz acc, X;
+    ec::set_inf(acc);
+    for (int k = logG - 1; k >= 0; --k) {
+        ec::dbl(acc);
+        load_xyzz(X, z + (size_t)k * 12);
+        ec::add(acc, X);
+    }
+    for (int l = 0; l < log2L; ++l) ec::dbl(acc);
+    load_xyzz(X, z + (size_t)logG * 12);
+    ec::add(acc, X);
+    store_xyzz(S + w * 12, acc);
+}
+
+// ---------------------------------------------------------------- stage 7
+
+__global__ void k_combine(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    xyzz acc, X;
+    ec::set_inf(acc);
+    for (int j = W - 1; j >= 0; --j) {
+        for (int k = 0; k < c; ++k) ec::dbl(acc);
+        load_xyzz(X, S + (size_t)j * 12);
+        ec::add(acc, X);
+    }
+    affine A;
+    ec::to_affine(A, acc);
+    if (!ec::is_inf(A)) {
+        fq::from_mont(A.x, A.x);
+        fq::from_mont(A.y, A.y);
+    }
+    fq::store(out, A.x);
+    fq::store(out + 12, A.y);
+}
+
+// ---------------------------------------------------------------- planning
+
+struct Plan {
+    size_t n;
+    int c, sgn, bits, W;
+    uint32_t B, Bp, stride;
+    int passes;
+    size_t tiles;
+    int K;
+    size_t N, nchunks;
+    uint32_t L, G, Q;
+    int logG, log2L;
+    size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_hist, off_dtot;
+    size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
+    size_t off_S, total;
+};
+
+int ilog2(uint64_t v) {
+    int r = 0;
+    while ((1ull << (r + 1)) <= v) ++r;
+    return r;
+}
+
+int default_c(size_t n, int sgn) {
+    int lg = n > 1 ? ilog2(n) : 0;
+    int c = lg - 4;
+    if (!sgn) c = lg - 3;
+    if (c < 4) c = 4;
+    if (c > 17) c = 17;
+    return c;
+}
+
+bool make_plan(size_t n, const msm_opts* o, Plan* p) {
+    if (!o) return false;
+    p->n = n;
+    p->sgn = o->signed_digits ? 1 : 0;
+    p->bits = o->scalar_bits ? o->scalar_bits : 256;
+    if (p->bits < 1 || p->bits > 256) return false;
+    p->c = o->c ? o->c : default_c(n, p->sgn);
+    if (p->c < 2 || p->c > 20) return false;
+    if (n >= (1ull << 31)) return false;
+    p->W = p->sgn ? (p->bits + 1 + p->c - 1) / p->c : (p->bits + p->c - 1) / p->c;
+    p->B = p->sgn ? (1u << (p->c - 1)) : ((1u << p->c) - 1u);
+    p->Bp = p->sgn ? p->B : (1u << p->c);
+    p->stride = p->B + 1;
+    p->passes = (p->c + 7) / 8;
+    p->tiles = (n + kSortTile - 1) / kSortTile;
+    p->N = (size_t)p->W * n;
+    size_t target_threads = 152 * 512;
+    size_t K = p->N / target_threads;
+    if (K < 2) K = 2;
+    if (K > 64) K = 64;
+    p->K = (int)K;
+    p->nchunks = (p->N + K - 1) / K;
+    // bucket reduction geometry
+    uint64_t total_buckets = (uint64_t)p->W * p->Bp;
+    uint32_t L = 2;
+    while (L < p->Bp && total_buckets / (2 * L) >= 65536) L <<= 1;
+    if (L > p->Bp) L = p->Bp;
+    p->L = L;
+    p->G = p->Bp / L;
+    p->logG = ilog2(p->G);
+    p->log2L = ilog2(L);
+    p->Q = p->G >= 8 ? p->G / 8 : 1;
+    // workspace layout, 256-byte aligned pieces
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o2 = off;
+        off = msm377::align_up(off + bytes, 256);
+        return o2;
+    };
+    const size_t XY = 192;  // bytes per XYZZ point
+    p->off_status = take(256);
+    p->off_points = take(o->flags & MSM377_POINTS_PREPARED ? 0 : n * 96);
+    p->off_keys0 = take(p->N * 4);
+    p->off_vals0 = take(p->N * 4);
+    p->off_keys1 = take(p->N * 4);
+    p->off_vals1 = take(p->N * 4);
+    p->off_hist = take((size_t)p->W * kRadix * (p->tiles ? p->tiles : 1) * 4);
+    p->off_dtot = take((size_t)p->W * kRadix * 4);
+    p->off_buckets = take((size_t)p->W * p->Bp * XY);
+    p->off_head = take(p->nchunks * XY);
+    p->off_tail = take(p->nchunks * XY);
+    p->off_headflag = take(p->nchunks * 4);
+    p->off_tailkey = take(p->nchunks * 4);
+    p->off_Y = take((size_t)p->W * p->G * XY);
+    p->off_V = take((size_t)p->W * p->G * XY);
+    size_t zs = (size_t)p->W * (p->logG + 1) * p->Q;
+    p->off_P0 = take(zs * XY);
+    p->off_P1 = take(zs * XY);
+    p->off_S = take((size_t)p->W * XY);
+    p->total = off;
+    return true;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+}  // namespace
+
+using namespace msm377;
+
+extern "C" int msm_g1_default_c(size_t n, int signed_digits) { return default_c(n, signed_digits ? 1 : 0); }
+
+extern "C" size_t msm_g1_workspace_bytes(size_t n, const msm_opts* opts) {
+    Plan p;
+    if (!make_plan(n, opts, &p)) return 0;
+    return p.total;
+}
+
+extern "C" int msm_points_prepare(const uint32_t* points_std, size_t n, uint32_t* out, void* stream) {
+    if (n == 0) return MSM377_OK;
+    if (!points_std || !out || !aligned(points_std, 16) || !aligned(out, 16))
+        return set_error(MSM377_EINVAL, "msm_points_prepare: null or non-16-byte-aligned pointer");
+    k_prepare<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(
+        reinterpret_cast<const uint4*>(points_std), reinterpret_cast<uint4*>(out), n);
+    return check_launch("msm_points_prepare");
+}
+
+extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out,
+                      void* workspace, size_t workspace_bytes, const msm_opts* opts) {
+    if (!opts) return set_error(MSM377_EINVAL, "msm_g1: opts is NULL");
+    if (!out) return set_error(MSM377_EINVAL, "msm_g1: out is NULL");
+    cudaStream_t s = as_stream(opts->stream);
+    Plan p;
+    if (!make_plan(n, opts, &p))
+        return set_error(MSM377_EINVAL, "msm_g1: bad options (c=%d scalar_bits=%d) or n too large",
+                         opts->c, opts->scalar_bits);
+    if (!workspace || !aligned(workspace, 256))
+        return set_error(MSM377_EINVAL, "msm_g1: workspace NULL or not 256-byte aligned");
+    if (workspace_bytes < p.total)
+        return set_error(MSM377_ENOMEM, "msm_g1: workspace %zu bytes, need %zu", workspace_bytes, p.total);
+    int* status = at<int>(workspace, p.off_status);
+    MSM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    if (n == 0) {
+        MSM_CUDA_TRY(cudaMemsetAsync(out, 0, 24 * sizeof(uint32_t), s));
+        return MSM377_OK;
+    }
+    if (!points || !scalars || !aligned(points, 16) || !aligned(scalars, 16))
+        return set_error(MSM377_EINVAL, "msm_g1: points/scalars NULL or not 16-byte aligned");
+
+    const uint4* pts = reinterpret_cast<const uint4*>(points);
+    if (!(opts->flags & MSM377_POINTS_PREPARED)) {
+        uint4* prep = at<uint4>(workspace, p.off_points);
+        k_prepare<<<grid_for(n, 256), 256, 0, s>>>(pts, prep, n);
+        pts = prep;
+    }
+    uint32_t* keys[2] = {at<uint32_t>(workspace, p.off_keys0), at<uint32_t>(workspace, p.off_keys1)};
+    uint32_t* vals[2] = {at<uint32_t>(workspace, p.off_vals0), at<uint32_t>(workspace, p.off_vals1)};
+    k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.W,
+                                              p.sgn, p.bits, keys[0], vals[0], status);
+    int r = check_launch("msm_g1 digits");
+    if (r) return r;
+
+    uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
+    uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
+    int cur = 0;
+    for (int pass = 0; pass < p.passes; ++pass) {
+        int shift = 8 * pass;
+        dim3 g((unsigned)p.tiles, (unsigned)p.W);
+        k_sort_hist<<<g, kSortThreads, 0, s>>>(keys[cur], n, shift, p.tiles, hist);
+        k_sort_scan_tiles<<<dim3(kRadix, p.W), kSortThreads, 0, s>>>(hist, p.tiles, dtot);
+        k_sort_scan_digits<<<p.W, kSortThreads, 0, s>>>(dtot);
+        k_sort_scatter<<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
+                                                  shift, p.tiles, hist, dtot);
+        cur ^= 1;
+    }
+    r = check_launch("msm_g1 sort");
+    if (r) return r;
+
+    uint4* buckets = at<uint4>(workspace, p.off_buckets);
+    MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * 192, s));
+    AccArgs a;
+    a.keys = keys[cur];
+    a.vals = vals[cur];
+    a.pts = pts;
+    a.buckets = buckets;
+    a.head = at<uint4>(workspace, p.off_head);
+    a.tail = at<uint4>(workspace, p.off_tail);
+    a.headflag = at<uint32_t>(workspace, p.off_headflag);
+    a.tailkey = at<uint32_t>(workspace, p.off_tailkey);
+    a.N = p.N;
+    a.n = n;
+    a.nchunks = p.nchunks;
+    a.stride = p.stride;
+    a.Bp = p.Bp;
+    a.K = p.K;
+    k_accumulate<<<grid_for(p.nchunks, 128), 128, 0, s>>>(a);
+    k_merge<<<grid_for(p.nchunks, 128), 128, 0, s>>>(a);
+    r = check_launch("msm_g1 accumulate");
+    if (r) return r;
+
+    uint4* Y = at<uint4>(workspace, p.off_Y);
+    uint4* V = at<uint4>(workspace, p.off_V);
+    size_t WG = (size_t)p.W * p.G;
+    k_reduce_segments<<<grid_for(WG, 128), 128, 0, s>>>(buckets, p.Bp, p.L, p.W, p.G, Y, V);
+    uint4* P0 = at<uint4>(workspace, p.off_P0);
+    uint4* P1 = at<uint4>(workspace, p.off_P1);
+    size_t nseg = (size_t)p.W * (p.logG + 1);
+    k_bitsums<<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, p.W, p.G, p.logG, p.Q, P0);
+    uint32_t m = p.Q;
+    uint4* zin = P0;
+    uint4* zout = P1;
+    while (m > 1) {
+        uint32_t F = m >= 8 ? 8 : m;
+        k_sum_segments<<<grid_for(nseg * (m / F), 128), 128, 0, s>>>(zin, nseg, m, F, zout);
+        m /= F;
+        uint4* tmp = zin;
+        zin = zout;
+        zout = tmp;
+    }
+    uint4* S = at<uint4>(workspace, p.off_S);
+    k_window_horner<<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+    k_combine<<<1, 32, 0, s>>>(S, p.W, p.c, out);
+    return check_launch("msm_g1 reduce");
+}
+
+extern "C" int msm_g1_status(const void* workspace, const msm_opts* opts) {
+    if (!workspace || !opts) return set_error(MSM377_EINVAL, "msm_g1_status: NULL argument");
+    int st = 0;
+    cudaStream_t s = as_stream(opts->stream);
+    MSM_CUDA_TRY(cudaMemcpyAsync(&st, workspace, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MSM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st == MSM377_ERANGE) return set_error(MSM377_ERANGE, "msm_g1: a scalar exceeds scalar_bits");
+    return st;
+}
+
+extern "C" size_t msm_g1_host_workspace_bytes(size_t n, const msm_opts* opts) {
+    if (!opts) return 0;
+    msm_opts o = *opts;
+    o.flags &= ~MSM377_POINTS_PREPARED;
+    size_t core = msm_g1_workspace_bytes(n, &o);
+    if (!core) return 0;
+    return core + align_up(n * 96, 256) + align_up(n * 32, 256) + 256;
+}
+
+extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_host, size_t n,
+                           uint32_t* out_host, void* workspace, size_t workspace_bytes,
+                           const msm_opts* opts) {
+    if (!opts || !out_host || !workspace) return set_error(MSM377_EINVAL, "msm_g1_host: NULL argument");
+    if (n && (!points_host || !scalars_host)) return set_error(MSM377_EINVAL, "msm_g1_host: NULL inputs");
+    size_t need = msm_g1_host_workspace_bytes(n, opts);
+    if (!need) return set_error(MSM377_EINVAL, "msm_g1_host: bad options");
+    if (workspace_bytes < need)
+        return set_error(MSM377_ENOMEM, "msm_g1_host: workspace %zu bytes, need %zu", workspace_bytes, need);
+    msm_opts o = *opts;
+    o.flags &= ~MSM377_POINTS_PREPARED;
+    size_t core = msm_g1_workspace_bytes(n, &o);
+    char* base = static_cast<char*>(workspace);
+    uint32_t* d_pts = reinterpret_cast<uint32_t*>(base + core);
+    uint32_t* d_sc = reinterpret_cast<uint32_t*>(base + core + align_up(n * 96, 256));
+    uint32_t* d_out = reinterpret_cast<uint32_t*>(base + core + align_up(n * 96, 256) + align_up(n * 32, 256));
+    cudaStream_t s = as_stream(o.stream);
+    if (n) {
+        MSM_CUDA_TRY(cudaMemcpyAsync(d_pts, points_host, n * 96, cudaMemcpyHostToDevice, s));
+        MSM_CUDA_TRY(cudaMemcpyAsync(d_sc, scalars_host, n * 32, cudaMemcpyHostToDevice, s));
+    }
+    int r = msm_g1(d_pts, d_sc, n, d_out, workspace, core, &o);
+    if (r) return r;
+    MSM_CUDA_TRY(cudaMemcpyAsync(out_host, d_out, 24 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    return msm_g1_status(workspace, &o);
+}

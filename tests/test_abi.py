@@ -1,0 +1,76 @@
+"""The C-ABI library loads on a host without a GPU and exports what include/msm377.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "msm377.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:int|size_t|void)\s+\**\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_named_calls():
+    names = declared_functions()
+    for required in ("fq_mul_batch", "padd_batch", "msm_g1", "msm_g1_workspace_bytes"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2502_11660_gb300 as pkg
+    L = pkg.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+    # every declared call has a binding signature
+    from paper_2502_11660_gb300._lib import SIGNATURES
+    assert set(declared_functions()) <= set(SIGNATURES)
+
+
+def test_host_only_entry_points():
+    import paper_2502_11660_gb300 as pkg
+    L = pkg.lib()
+    assert L.msm377_version() >= 100
+    o = pkg._opts(c=16, signed=True, scalar_bits=253)
+    ws = L.msm_g1_workspace_bytes(1 << 20, ctypes.byref(o))
+    assert ws > (1 << 20) * 16 * 8 * 2   # keys and values, double-buffered
+    assert L.msm_g1_workspace_bytes(10, ctypes.byref(pkg._opts(c=1))) == 0
+    assert L.msm_g1_workspace_bytes(10, ctypes.byref(pkg._opts(c=21))) == 0
+    assert L.msm_g1_workspace_bytes(10, ctypes.byref(pkg._opts(scalar_bits=257))) == 0
+    assert [pkg.msm_g1_default_c(1 << k) for k in (12, 20, 22)] == [8, 16, 17]
+
+
+def test_invalid_arguments_fail_before_touching_the_gpu():
+    import paper_2502_11660_gb300 as pkg
+    L = pkg.lib()
+    rc = L.msm_g1(None, None, 10, ctypes.c_void_p(16), None, 0, None)
+    assert rc == -1 and "opts" in pkg.last_error()
+    rc = L.msm_g1(None, None, 10, ctypes.c_void_p(16), None, 0, ctypes.byref(pkg._opts(c=30)))
+    assert rc == -1 and "bad options" in pkg.last_error()
+    rc = L.msm_g1(None, None, 10, None, None, 0, ctypes.byref(pkg._opts()))
+    assert rc == -1
+    assert L.fq_mul_batch(None, None, None, 5, 0, None) == -1
+    assert L.padd_batch(None, None, None, 5, 0, None) == -1
+    assert L.fq_mul_batch(None, None, None, 0, 0, None) == 0   # n = 0 is a no-op
+
+
+def test_header_constants_match_the_oracle():
+    """The CUDA field header's modulus and Montgomery constants agree with the oracle's derivation."""
+    from oracle import fq
+    src = open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", "fq.cuh")).read()
+
+    def arr(name):
+        m = re.search(name + r"\[N\] = \{([^}]*)\}", src)
+        return sum(int(w.strip().rstrip("u"), 16) << (32 * k) for k, w in enumerate(m.group(1).split(",")))
+
+    R = 1 << 384
+    assert arr("kP") == fq.P
+    assert arr("k2P") == 2 * fq.P
+    assert arr("kOne") == R % fq.P
+    assert arr("kR2") == R * R % fq.P
+    assert arr("kPm2") == fq.P - 2

@@ -1,0 +1,58 @@
+"""Test helpers: limb conversions, oracle-side normalisation, cached oracle point sets."""
+from __future__ import annotations
+
+import numpy as np
+
+import synth
+from oracle import coracle, fq, g1
+
+_POINTS: dict = {}
+
+
+def ints_of_soa(arr: np.ndarray) -> list[int]:
+    """[12][n] u32 -> list of n ints."""
+    a = np.asarray(arr, dtype=np.uint64)
+    out = [0] * a.shape[1]
+    for k in range(a.shape[0]):
+        col = a[k].tolist()
+        for i, w in enumerate(col):
+            out[i] |= int(w) << (32 * k)
+    return out
+
+
+def soa_of_ints(vals, nlimbs: int = 12) -> np.ndarray:
+    out = np.zeros((nlimbs, len(vals)), dtype=np.uint32)
+    for i, v in enumerate(vals):
+        for k in range(nlimbs):
+            out[k, i] = (v >> (32 * k)) & 0xFFFFFFFF
+    return out
+
+
+def xyzz_to_affine_int(X: int, Y: int, ZZ: int, ZZZ: int):
+    """Oracle-side normalisation x = X/ZZ, y = Y/ZZZ; ZZ = 0 is O."""
+    if ZZ % fq.P == 0:
+        return None
+    return (X * fq.inv(ZZ) % fq.P, Y * fq.inv(ZZZ) % fq.P)
+
+
+def oracle_points(seeds: np.ndarray, key=None) -> np.ndarray:
+    """P_i = seeds_i * G from the C oracle, cached per key within the session."""
+    if key is not None and key in _POINTS:
+        return _POINTS[key]
+    pts = coracle.gen_points(seeds)
+    if key is not None:
+        _POINTS[key] = pts
+    return pts
+
+
+def msm_inputs(n: int, tag: int):
+    a, s = synth.workloads.msm(n, tag)
+    return a, s, oracle_points(s, key=("msm", n, tag))
+
+
+def closed_form_limbs(seeds: np.ndarray, scalars: np.ndarray):
+    """Expected MSM result sum a_i (s_i G) = ((sum a_i s_i) mod r) G, as an affine point."""
+    k = 0
+    for a, s in zip(scalars, seeds):
+        k += synth.limbs_to_int(a) * synth.limbs_to_int(s)
+    return g1.mul(k % fq.R, g1.G)
