@@ -1,0 +1,388 @@
+"""Benchmark: BLS12-377 G1 MSM points/s at n = 2^20 (one step = one msm_g1 call).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N] [--c C]
+
+Our arm: resident Montgomery points (prepared once), fresh seeded scalars per
+step already in HBM, L2 flushed (256 MB write) between timed steps, per-step
+CUDA events on the launch stream. Prints one JSON line (rank 0).
+Reference arm (--impl reference): the CPU oracle's Pippenger (plain C, all host
+cores) on a bounded sample of the same workload; rank 0 only.
+For N > 1 (torchrun) every rank runs its own MSMs on its own GPU (replicas, no
+collective on the data path); value = all ranks' points / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "BLS12-377 MSM points/s & PADD/s at n=2^20; batched vs sequential speedup"
+PRODUCTS = {"fq_mul": 276, "fq_sqr": 210}
+PRODUCTS["madd"] = 8 * PRODUCTS["fq_mul"] + 2 * PRODUCTS["fq_sqr"]     # 2628
+PRODUCTS["add"] = 12 * PRODUCTS["fq_mul"] + 2 * PRODUCTS["fq_sqr"]     # 3732
+PRODUCTS["dbl"] = 6 * PRODUCTS["fq_mul"] + 3 * PRODUCTS["fq_sqr"]      # 2286
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 20)
+    ap.add_argument("--c", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the e2e, cpu and batch-op extras")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def digit_counts(scalars: np.ndarray, c: int, signed: bool, bits: int):
+    """Nonzero digits and distinct nonzero buckets per window (host numpy, for op counts)."""
+    words = scalars.astype(np.uint64)
+    W = -(-(bits + (1 if signed else 0)) // c)
+    carry = np.zeros(scalars.shape[0], dtype=np.int64)
+    nonzero = 0
+    runs = 0
+    half = 1 << (c - 1)
+    for j in range(W):
+        b0 = j * c
+        raw = np.zeros(scalars.shape[0], dtype=np.int64)
+        for b in range(c):
+            bit = b0 + b
+            if bit >= 256:
+                break
+            raw |= ((words[:, bit // 32] >> np.uint64(bit % 32)) & np.uint64(1)).astype(np.int64) << b
+        if signed:
+            v = raw + carry
+            neg = v > half
+            key = np.where(neg, (1 << c) - v, v)
+            carry = neg.astype(np.int64)
+        else:
+            key = raw
+        nz = key[key != 0]
+        nonzero += nz.size
+        runs += np.unique(nz).size
+    return W, nonzero, runs
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("fq.cuh", "ec.cuh", "msm.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per accumulate launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(PROFILE_DIR, "accumulate_traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    rec = json.load(open(path))
+    if rec.get("kernel_hash") != kernel_hash():
+        return None, rec
+    return rec, rec
+
+
+def cpu_baseline(n: int, reps_budget_s: float = 12.0):
+    """The oracle's C Pippenger (as it stands) on a bounded sample, all host cores."""
+    from oracle import coracle
+    a, s = synth.workloads.msm(n, tag=2)
+    pts = coracle.gen_points(s)
+    c = max(4, min(16, int(np.log2(max(n, 2))) - 3))
+    t0 = time.perf_counter()
+    runs = 0
+    while True:
+        coracle.msm(pts, a, c=c)
+        runs += 1
+        if time.perf_counter() - t0 > reps_budget_s or runs >= 20:
+            break
+    dt = (time.perf_counter() - t0) / runs
+    cores = os.cpu_count() or 1
+    return {"value": n / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "sample": f"textbook Pippenger (plain C, unsigned c={c}), n={n} points, {runs} run(s), "
+                      f"{cores} threads over windows"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    n = min(args.n, 1 << 16)
+    from oracle import coracle
+    a, s = synth.workloads.msm(n, tag=2)
+    pts = coracle.gen_points(s)
+    c = max(4, min(16, int(np.log2(max(n, 2))) - 3))
+    for _ in range(args.warmup):
+        coracle.msm(pts, a, c=c)
+    times = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        coracle.msm(pts, a, c=c)
+        times.append(time.perf_counter() - t0)
+    wall = time.perf_counter() - t_all
+    ms = 1e3 * sum(times) / len(times)
+    val = n / (ms / 1e3)
+    cores = os.cpu_count() or 1
+    out = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "points/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 (C big-integer)", "data": "synthetic",
+        "config": {"workload": f"msm_g1 BLS12-377 G1, bounded CPU sample n={n} of the n=2^20 workload",
+                   "n": n, "c": c},
+        "cpu_baseline": {"value": val, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"textbook Pippenger (plain C, unsigned c={c}), n={n} points per step"},
+        "e2e": {"value": val, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2502_11660_gb300 as pkg
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    c = args.c or pkg.msm_g1_default_c(n, True)
+    bits = 253
+
+    # resident point set P_i = s_i G, built and prepared on the device (not timed)
+    seeds = synth.scalars(synth.stream_seed(2, n, 2 + 1000 * rank), n)
+    pts_std = pkg.g1_generator_mul(pkg.to_device(seeds, dev))
+    prep = pkg.msm_points_prepare(pts_std)
+    nsets = args.steps + args.warmup
+    sc_host = [synth.scalars(synth.stream_seed(2, n, 100 + k + 1000 * rank), n) for k in range(nsets)]
+    sc_dev = [pkg.to_device(x, dev) for x in sc_host]
+    ws = pkg.msm_g1_workspace(n, c=c, scalar_bits=bits, prepared=True, device=dev)
+    out = torch.empty(24, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k, profile=False):
+        pkg.msm_g1(prep, sc_dev[k], out=out, workspace=ws, c=c, scalar_bits=bits, prepared=True,
+                   stream=stream, profile=profile)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    peak = pkg.imad_probe(20000, stream=stream)   # measured limb-product peak (products/s)
+
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = pkg.launch_count()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                 # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        step(args.warmup + k, profile=True)
+        ev[k][1].record(stream)
+        stage_ms.append(pkg.profile_last())   # synchronises on the step's last event
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    launches = pkg.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1e3)
+
+    # operation counts of one MSM (from the scalars of the timed steps)
+    W, nonzero, runs = digit_counts(sc_host[args.warmup], c, True, bits)
+    madds = nonzero - runs
+    Bp = 1 << (c - 1)
+    full_adds = 2 * W * Bp            # running sums of the bucket reduction (upper level excluded)
+    dbls = W * c
+    ops = madds + full_adds + dbls
+    acc_ms = statistics.mean(s["accumulate"] for s in stage_ms)
+    acc_products = madds * PRODUCTS["madd"]
+    achieved = acc_products / (acc_ms / 1e3)
+    rec, rec_any = recorded_traffic()
+    roofline = {"bound": "alu", "kernel": "k_accumulate", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                "unit": "Tprod/s", "frac": achieved / peak,
+                "peak_source": "of measured: msm377_imad_probe (mad.lo.cc/madc.hi.cc rows, all SMs)",
+                "algorithmic_products_per_launch": acc_products,
+                "traffic": (rec["bytes_per_launch_full"] if rec else None)}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 (12x32-bit limb Montgomery integer arithmetic)", "data": "synthetic",
+        "config": {"workload": f"msm_g1 BLS12-377 G1 n={n} signed digits c={c}, resident Montgomery points, "
+                               f"fresh scalars per step", "n": n, "c": c, "windows": W,
+                   "l2": "flushed between steps (256 MB write, outside the timed events)",
+                   "parallelism": f"replicas x{world}"},
+        "padd_per_s": world * ops / (ms / 1e3),
+        "op_counts": {"madd": madds, "bucket_running_sum_adds": full_adds, "window_dbls": dbls},
+        "stages_ms": {k2: statistics.mean(s[k2] for s in stage_ms) for k2 in stage_ms[0]},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+    }
+
+    if rank == 0 and not args.no_extras:
+        # end to end through the host-buffer C-ABI call: H2D of points and scalars, D2H of the result
+        pinned_pts = torch.from_numpy(pkg.to_host(pts_std).view(np.int32)).pin_memory()
+        hp = pinned_pts.numpy().view(np.uint32)
+        hsc = [torch.from_numpy(x.view(np.int32)).pin_memory().numpy().view(np.uint32)
+               for x in sc_host[: min(4, nsets)]]
+        hws = torch.empty(pkg.msm_g1_host_workspace_bytes(n, c=c, scalar_bits=bits), dtype=torch.uint8,
+                          device=dev)
+        pkg.msm_g1_host(hp, hsc[0], workspace=hws, c=c, scalar_bits=bits)
+        et = []
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            pkg.msm_g1_host(hp, hsc[k % len(hsc)], workspace=hws, c=c, scalar_bits=bits)
+            et.append(time.perf_counter() - t0)
+        e2e_s = sum(et) / len(et)
+        result["e2e"] = {"value": n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": n * (96 + 32),
+                         "d2h_bytes_per_step": 96, "ms_per_step": 1e3 * e2e_s,
+                         "call": "msm_g1_host (pinned host points + scalars, synchronous)"}
+        del hws
+        # standalone batched arithmetic at 2^24 (Fq Montgomery multiplications, mixed PADDs)
+        result["batch_ops"] = batch_ops(pkg, torch, dev, stream)
+        result["cpu_baseline"] = cpu_baseline(1 << 16)
+
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def batch_ops(pkg, torch, dev, stream):
+    n = 1 << 24
+    a, b = synth.workloads.fq_pairs(n, tag=1)
+    mA = pkg.fq_to_montgomery(pkg.to_device(a.T.copy(), dev))
+    mB = pkg.fq_to_montgomery(pkg.to_device(b.T.copy(), dev))
+    out = torch.empty_like(mA)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_mul = timed(lambda: pkg.fq_mul_batch(mA, mB, out=out, form=pkg.FORM_MONTGOMERY))
+    del mA, mB, out
+    # mixed PADDs on a pool of 2^16 device-generated points, XYZZ accumulators with ZZ = ZZZ = R
+    pool = pkg.g1_generator_mul(pkg.to_device(synth.scalars(3, 1 << 16), dev))
+    mpool = pkg.msm_points_prepare(pool)
+    g = torch.Generator(device=dev).manual_seed(7)
+    i1 = torch.randint(0, 1 << 16, (n,), device=dev, generator=g)
+    i2 = torch.randint(0, 1 << 16, (n,), device=dev, generator=g)
+    P, Q = mpool[i1], mpool[i2]
+    one = pkg.fq_to_montgomery(pkg.to_device(np.eye(12, 1, dtype=np.uint32).reshape(12, 1), dev))
+    acc = torch.empty((4, 12, n), dtype=torch.int32, device=dev)
+    acc[0] = P[:, :12].T
+    acc[1] = P[:, 12:].T
+    acc[2] = one.expand(12, n)
+    acc[3] = one.expand(12, n)
+    q = torch.stack([Q[:, :12].T.contiguous(), Q[:, 12:].T.contiguous()])
+    del P, Q, i1, i2
+    outp = torch.empty_like(acc)
+    ms_padd = timed(lambda: pkg.padd_batch(acc, q, out=outp, form=pkg.FORM_MONTGOMERY), reps=3)
+    return {"fq_mul_per_s": n / (ms_mul / 1e3), "fq_mul_ms_2^24": ms_mul,
+            "fq_mul_hbm_GBps": n * 144 / (ms_mul / 1e3) / 1e9,
+            "padd_per_s": n / (ms_padd / 1e3), "padd_ms_2^24": ms_padd,
+            "padd_products_per_s": n * PRODUCTS["madd"] / (ms_padd / 1e3)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -101,6 +101,7 @@ int g1_generator_mul(const uint32_t *seeds, size_t n, uint32_t *out, void *strea
 
 /* opts.flags */
 #define MSM377_POINTS_PREPARED 1u /* points are Montgomery-form (msm_points_prepare output) */
+#define MSM377_PROFILE 2u         /* record CUDA events between stages (see msm377_profile_last) */
 
 typedef struct msm_opts {
     int32_t c;             /* window width in bits, 2..20; 0 = chosen from n */
@@ -149,6 +150,19 @@ size_t msm_g1_host_workspace_bytes(size_t n, const msm_opts *opts);
 int msm_g1_host(const uint32_t *points_host, const uint32_t *scalars_host, size_t n,
                 uint32_t *out_host, void *workspace, size_t workspace_bytes,
                 const msm_opts *opts);
+
+/* Stage timings of the most recent msm_g1 call made with MSM377_PROFILE, in
+ * milliseconds, measured by CUDA events recorded on that call's stream between
+ * its stages: [0] prepare + digits, [1] sort, [2] bucket accumulation,
+ * [3] partial merge, [4] bucket reduction, [5] window combine + normalisation.
+ * Synchronous (waits for the last event). Writes min(cap, 6) values and returns
+ * the number of stages, or a negative status. Not thread-safe: one profiled
+ * call at a time per process. */
+int msm377_profile_last(float *ms, int cap);
+
+/* Number of kernels this library has launched in the process so far (host-side
+ * counter, all entry points). */
+uint64_t msm377_launch_count(void);
 
 /* ------------------------------------------------------------------------
  * Micro-benchmark for the roofline denominator: runs `iters` rounds of

@@ -21,13 +21,15 @@ from ._lib import MsmError, MsmOpts, check, last_error, lib
 FORM_STANDARD = 0
 FORM_MONTGOMERY = 1
 POINTS_PREPARED = 1
+PROFILE = 2
+MSM_STAGES = ("prepare+digits", "sort", "accumulate", "merge", "reduce", "combine")
 
 __all__ = [
     "MsmError", "MsmOpts", "FORM_STANDARD", "FORM_MONTGOMERY", "POINTS_PREPARED",
     "to_device", "to_host", "fq_mul_batch", "fq_to_montgomery", "fq_from_montgomery",
     "padd_batch", "xyzz_to_affine_batch", "g1_generator_mul", "msm_points_prepare",
     "msm_g1", "msm_g1_workspace", "msm_g1_host", "msm_g1_status", "msm_g1_default_c",
-    "imad_probe", "lib", "last_error",
+    "imad_probe", "lib", "last_error", "profile_last", "launch_count", "MSM_STAGES", "PROFILE",
 ]
 
 
@@ -113,10 +115,11 @@ def msm_points_prepare(points: torch.Tensor, out: torch.Tensor | None = None, st
     return out
 
 
-def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0) -> MsmOpts:
+def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0, profile=False) -> MsmOpts:
     """stream=0 for size queries (no CUDA context needed); None = torch's current stream."""
     sv = 0 if (isinstance(stream, int) and stream == 0) else _s(stream).value
-    return MsmOpts(int(c), 1 if signed else 0, int(scalar_bits), POINTS_PREPARED if prepared else 0, sv)
+    flags = (POINTS_PREPARED if prepared else 0) | (PROFILE if profile else 0)
+    return MsmOpts(int(c), 1 if signed else 0, int(scalar_bits), flags, sv)
 
 
 def msm_g1_default_c(n: int, signed: bool = True) -> int:
@@ -133,12 +136,12 @@ def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, de
 
 def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None = None,
            workspace: torch.Tensor | None = None, c: int = 0, signed: bool = True,
-           scalar_bits: int = 0, prepared: bool = False, stream=None) -> torch.Tensor:
+           scalar_bits: int = 0, prepared: bool = False, stream=None, profile: bool = False) -> torch.Tensor:
     """Enqueues sum_i scalars_i * points_i; returns the (24,) int32 device tensor it writes."""
     n = points.shape[0]
     if scalars.shape[0] != n:
         raise ValueError("points and scalars differ in length")
-    o = _opts(c, signed, scalar_bits, prepared, None if stream is None else stream)
+    o = _opts(c, signed, scalar_bits, prepared, None if stream is None else stream, profile)
     if workspace is None:
         workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared, points.device)
     out = torch.empty(24, dtype=torch.int32, device=points.device) if out is None else out
@@ -173,6 +176,19 @@ def msm_g1_host(points: np.ndarray, scalars: np.ndarray, workspace: torch.Tensor
 def msm_g1_host_workspace_bytes(n: int, c=0, signed=True, scalar_bits=0) -> int:
     o = _opts(c, signed, scalar_bits)
     return lib().msm_g1_host_workspace_bytes(n, ctypes.byref(o))
+
+
+def profile_last() -> dict:
+    """Stage times (ms) of the last msm_g1 call made with profile=True (synchronises)."""
+    buf = (ctypes.c_float * 8)()
+    k = lib().msm377_profile_last(buf, 8)
+    if k < 0:
+        raise MsmError(k, last_error())
+    return {name: float(buf[i]) for i, name in enumerate(MSM_STAGES[:k])}
+
+
+def launch_count() -> int:
+    return int(lib().msm377_launch_count())
 
 
 def imad_probe(iters: int = 20000, stream=None) -> float:

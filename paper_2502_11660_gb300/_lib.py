@@ -47,6 +47,8 @@ SIGNATURES = {
     "msm_g1_host_workspace_bytes": (c_size, [c_size, ctypes.POINTER(MsmOpts)]),
     "msm_g1_host": (c_int, [c_void, c_void, c_size, c_void, c_void, c_size, ctypes.POINTER(MsmOpts)]),
     "msm377_imad_probe": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_void]),
+    "msm377_profile_last": (c_int, [ctypes.POINTER(ctypes.c_float), c_int]),
+    "msm377_launch_count": (ctypes.c_uint64, []),
 }
 
 

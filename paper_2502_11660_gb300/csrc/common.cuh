@@ -21,6 +21,13 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Checks the launch that was just enqueued.
 int check_launch(const char* what);
 
+// Host-side count of kernel launches (msm377_launch_count).
+void note_launches(unsigned k);
+
+// Stage events of a profiled msm_g1 call: reset, then record after each stage.
+int profile_begin(cudaStream_t s);
+int profile_mark(cudaStream_t s);
+
 inline unsigned grid_for(size_t n, unsigned block) {
     return static_cast<unsigned>((n + block - 1) / block);
 }

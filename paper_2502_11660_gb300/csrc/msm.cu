@@ -578,6 +578,7 @@ extern "C" int msm_points_prepare(const uint32_t* points_std, size_t n, uint32_t
         return set_error(MSM377_EINVAL, "msm_points_prepare: null or non-16-byte-aligned pointer");
     k_prepare<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(
         reinterpret_cast<const uint4*>(points_std), reinterpret_cast<uint4*>(out), n);
+    note_launches(1);
     return check_launch("msm_points_prepare");
 }
 
@@ -595,6 +596,11 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     if (workspace_bytes < p.total)
         return set_error(MSM377_ENOMEM, "msm_g1: workspace %zu bytes, need %zu", workspace_bytes, p.total);
     int* status = at<int>(workspace, p.off_status);
+    const bool prof = (opts->flags & MSM377_PROFILE) != 0;
+    if (prof) {
+        int pr = profile_begin(s);
+        if (pr) return pr;
+    }
     MSM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
     if (n == 0) {
         MSM_CUDA_TRY(cudaMemsetAsync(out, 0, 24 * sizeof(uint32_t), s));
@@ -607,14 +613,17 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     if (!(opts->flags & MSM377_POINTS_PREPARED)) {
         uint4* prep = at<uint4>(workspace, p.off_points);
         k_prepare<<<grid_for(n, 256), 256, 0, s>>>(pts, prep, n);
+        note_launches(1);
         pts = prep;
     }
     uint32_t* keys[2] = {at<uint32_t>(workspace, p.off_keys0), at<uint32_t>(workspace, p.off_keys1)};
     uint32_t* vals[2] = {at<uint32_t>(workspace, p.off_vals0), at<uint32_t>(workspace, p.off_vals1)};
     k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.W,
                                               p.sgn, p.bits, keys[0], vals[0], status);
+    note_launches(1);
     int r = check_launch("msm_g1 digits");
     if (r) return r;
+    if (prof) profile_mark(s);
 
     uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
     uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
@@ -627,10 +636,12 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
         k_sort_scan_digits<<<p.W, kSortThreads, 0, s>>>(dtot);
         k_sort_scatter<<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
                                                   shift, p.tiles, hist, dtot);
+        note_launches(4);
         cur ^= 1;
     }
     r = check_launch("msm_g1 sort");
     if (r) return r;
+    if (prof) profile_mark(s);
 
     uint4* buckets = at<uint4>(workspace, p.off_buckets);
     MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * 192, s));
@@ -650,24 +661,30 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     a.Bp = p.Bp;
     a.K = p.K;
     k_accumulate<<<grid_for(p.nchunks, 128), 128, 0, s>>>(a);
+    if (prof) profile_mark(s);
     k_merge<<<grid_for(p.nchunks, 128), 128, 0, s>>>(a);
+    note_launches(2);
     r = check_launch("msm_g1 accumulate");
     if (r) return r;
+    if (prof) profile_mark(s);
 
     uint4* Y = at<uint4>(workspace, p.off_Y);
     uint4* V = at<uint4>(workspace, p.off_V);
     size_t WG = (size_t)p.W * p.G;
     k_reduce_segments<<<grid_for(WG, 128), 128, 0, s>>>(buckets, p.Bp, p.L, p.W, p.G, Y, V);
+    note_launches(1);
     uint4* P0 = at<uint4>(workspace, p.off_P0);
     uint4* P1 = at<uint4>(workspace, p.off_P1);
     size_t nseg = (size_t)p.W * (p.logG + 1);
     k_bitsums<<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, p.W, p.G, p.logG, p.Q, P0);
+    note_launches(1);
     uint32_t m = p.Q;
     uint4* zin = P0;
     uint4* zout = P1;
     while (m > 1) {
         uint32_t F = m >= 8 ? 8 : m;
         k_sum_segments<<<grid_for(nseg * (m / F), 128), 128, 0, s>>>(zin, nseg, m, F, zout);
+        note_launches(1);
         m /= F;
         uint4* tmp = zin;
         zin = zout;
@@ -675,7 +692,11 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     }
     uint4* S = at<uint4>(workspace, p.off_S);
     k_window_horner<<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+    note_launches(1);
+    if (prof) profile_mark(s);
     k_combine<<<1, 32, 0, s>>>(S, p.W, p.c, out);
+    note_launches(1);
+    if (prof) profile_mark(s);
     return check_launch("msm_g1 reduce");
 }
 
