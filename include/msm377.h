@@ -9,7 +9,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * - Field elements: 12 little-endian 32-bit limbs. STANDARD form is the integer
- *   x in [0, p); MONTGOMERY form is x * 2^384 mod p in [0, p).
+ *   x in [0, p); MONTGOMERY form is x * 2^390 mod p in [0, p).
  * - Affine points: x then y (24 u32). The identity O is (0, 0), which is not on
  *   y^2 = x^3 + 1.
  * - XYZZ points (x = X/ZZ, y = Y/ZZZ): X, Y, ZZ, ZZZ; the identity has ZZ = 0.

@@ -37,44 +37,51 @@ constexpr int kRadix = 256;
 
 // ---------------------------------------------------------------- memory I/O
 
+// Affine point in memory: 24 packed u32 (x then y), canonical Montgomery form.
 __device__ __forceinline__ void load_affine(affine& Q, const uint4* __restrict__ pts, uint32_t idx) {
     const uint4* p = pts + 6 * (size_t)idx;
     uint4 a = __ldg(p + 0), b = __ldg(p + 1), c = __ldg(p + 2);
     uint4 d = __ldg(p + 3), e = __ldg(p + 4), f = __ldg(p + 5);
-    Q.x.v[0] = a.x; Q.x.v[1] = a.y; Q.x.v[2] = a.z; Q.x.v[3] = a.w;
-    Q.x.v[4] = b.x; Q.x.v[5] = b.y; Q.x.v[6] = b.z; Q.x.v[7] = b.w;
-    Q.x.v[8] = c.x; Q.x.v[9] = c.y; Q.x.v[10] = c.z; Q.x.v[11] = c.w;
-    Q.y.v[0] = d.x; Q.y.v[1] = d.y; Q.y.v[2] = d.z; Q.y.v[3] = d.w;
-    Q.y.v[4] = e.x; Q.y.v[5] = e.y; Q.y.v[6] = e.z; Q.y.v[7] = e.w;
-    Q.y.v[8] = f.x; Q.y.v[9] = f.y; Q.y.v[10] = f.z; Q.y.v[11] = f.w;
+    const uint32_t wx[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+    const uint32_t wy[12] = {d.x, d.y, d.z, d.w, e.x, e.y, e.z, e.w, f.x, f.y, f.z, f.w};
+    fq::unpack(Q.x, wx);
+    fq::unpack(Q.y, wy);
 }
 
-__device__ __forceinline__ void load_fe4(fe& a, const uint4* p) {
-    uint4 u0 = p[0], u1 = p[1], u2 = p[2];
-    a.v[0] = u0.x; a.v[1] = u0.y; a.v[2] = u0.z; a.v[3] = u0.w;
-    a.v[4] = u1.x; a.v[5] = u1.y; a.v[6] = u1.z; a.v[7] = u1.w;
-    a.v[8] = u2.x; a.v[9] = u2.y; a.v[10] = u2.z; a.v[11] = u2.w;
-}
+// XYZZ point in memory: the 4 x 15 digit words as they are in registers (15 uint4).
+constexpr int kXyzzVec = 15;
+constexpr size_t kXyzzBytes = kXyzzVec * 16;
 
-__device__ __forceinline__ void store_fe4(uint4* p, const fe& a) {
-    p[0] = make_uint4(a.v[0], a.v[1], a.v[2], a.v[3]);
-    p[1] = make_uint4(a.v[4], a.v[5], a.v[6], a.v[7]);
-    p[2] = make_uint4(a.v[8], a.v[9], a.v[10], a.v[11]);
-}
-
-// XYZZ point in memory: 12 uint4 (X, Y, ZZ, ZZZ).
 __device__ __forceinline__ void load_xyzz(xyzz& P, const uint4* p) {
-    load_fe4(P.X, p);
-    load_fe4(P.Y, p + 3);
-    load_fe4(P.ZZ, p + 6);
-    load_fe4(P.ZZZ, p + 9);
+    uint32_t w[60];
+#pragma unroll
+    for (int k = 0; k < kXyzzVec; ++k) {
+        uint4 u = p[k];
+        w[4 * k] = u.x;
+        w[4 * k + 1] = u.y;
+        w[4 * k + 2] = u.z;
+        w[4 * k + 3] = u.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        P.X.d[k] = w[k];
+        P.Y.d[k] = w[15 + k];
+        P.ZZ.d[k] = w[30 + k];
+        P.ZZZ.d[k] = w[45 + k];
+    }
 }
 
 __device__ __forceinline__ void store_xyzz(uint4* p, const xyzz& P) {
-    store_fe4(p, P.X);
-    store_fe4(p + 3, P.Y);
-    store_fe4(p + 6, P.ZZ);
-    store_fe4(p + 9, P.ZZZ);
+    uint32_t w[60];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        w[k] = P.X.d[k];
+        w[15 + k] = P.Y.d[k];
+        w[30 + k] = P.ZZ.d[k];
+        w[45 + k] = P.ZZZ.d[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kXyzzVec; ++k) p[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
 }
 
 // ---------------------------------------------------------------- stage 1
@@ -82,13 +89,15 @@ __device__ __forceinline__ void store_xyzz(uint4* p, const xyzz& P) {
 __global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(in + 6 * i);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + 6 * i);
     fe x, y;
-    load_fe4(x, in + 6 * i);
-    load_fe4(y, in + 6 * i + 3);
-    fq::to_mont(x, x);
-    fq::to_mont(y, y);
-    store_fe4(out + 6 * i, x);
-    store_fe4(out + 6 * i + 3, y);
+    fq::load_packed(x, src);
+    fq::load_packed(y, src + 12);
+    ec::to_mont(x, x);
+    ec::to_mont(y, y);
+    fq::store_canonical(dst, x);
+    fq::store_canonical(dst + 12, y);
 }
 
 // ---------------------------------------------------------------- stage 2
@@ -294,7 +303,7 @@ __device__ __forceinline__ uint32_t composite(const AccArgs& a, size_t g) {
 
 __device__ __forceinline__ void bucket_store(const AccArgs& a, uint32_t ck, const xyzz& P) {
     uint32_t w = ck / a.stride, key = ck % a.stride;
-    store_xyzz(a.buckets + ((size_t)w * a.Bp + (key - 1)) * 12, P);
+    store_xyzz(a.buckets + ((size_t)w * a.Bp + (key - 1)) * kXyzzVec, P);
 }
 
 __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
@@ -308,6 +317,7 @@ __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
     a.headflag[t] = 0;
     xyzz acc;
     ec::set_inf(acc);
+    bool inf = true;
     uint32_t cur = composite(a, start);
     bool first = true;
     for (size_t g = start; g <= end; ++g) {
@@ -320,15 +330,16 @@ __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
                 if (!sb && !ea) {
                     bucket_store(a, cur, acc);
                 } else if (sb) {
-                    store_xyzz(a.head + t * 12, acc);
+                    store_xyzz(a.head + t * kXyzzVec, acc);
                     a.headflag[t] = ea ? 2u : 1u;
                 } else {
-                    store_xyzz(a.tail + t * 12, acc);
+                    store_xyzz(a.tail + t * kXyzzVec, acc);
                     a.tailkey[t] = cur;
                 }
             }
             if (g == end) break;
             ec::set_inf(acc);
+            inf = true;
             cur = ck;
             first = false;
         }
@@ -338,7 +349,7 @@ __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
             affine Q;
             load_affine(Q, a.pts, v & 0x7fffffffu);
             if (v >> 31) ec::neg(Q);
-            ec::madd(acc, Q);
+            ec::madd(acc, inf, Q);
         }
     }
 }
@@ -349,9 +360,9 @@ __global__ void k_merge(AccArgs a) {
     uint32_t ck = a.tailkey[t];
     if (ck == kNone) return;
     xyzz acc, h;
-    load_xyzz(acc, a.tail + t * 12);
+    load_xyzz(acc, a.tail + t * kXyzzVec);
     for (size_t u = t + 1; u < a.nchunks; ++u) {
-        load_xyzz(h, a.head + u * 12);
+        load_xyzz(h, a.head + u * kXyzzVec);
         ec::add(acc, h);
         if (a.headflag[u] != 2u) break;
     }
@@ -366,17 +377,17 @@ __global__ void k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp
     size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= W * G) return;
     size_t w = id / G, g = id % G;
-    const uint4* seg = buckets + ((size_t)w * Bp + (size_t)g * L) * 12;
+    const uint4* seg = buckets + ((size_t)w * Bp + (size_t)g * L) * kXyzzVec;
     xyzz T, S, X;
     ec::set_inf(T);
     ec::set_inf(S);
     for (int i = (int)L; i >= 1; --i) {
-        load_xyzz(X, seg + (size_t)(i - 1) * 12);
+        load_xyzz(X, seg + (size_t)(i - 1) * kXyzzVec);
         ec::add(T, X);
         ec::add(S, T);
     }
-    store_xyzz(Y + id * 12, T);
-    store_xyzz(V + id * 12, S);
+    store_xyzz(Y + id * kXyzzVec, T);
+    store_xyzz(V + id * kXyzzVec, S);
 }
 
 // Thread (w, k, q): partial of Z_k = sum_{g in chunk q, bit k of g set} Y_g, or for
@@ -394,14 +405,14 @@ __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__
     ec::set_inf(acc);
     for (uint32_t g = g0; g < g0 + span; ++g) {
         if (k == logG) {
-            load_xyzz(X, V + ((size_t)w * G + g) * 12);
+            load_xyzz(X, V + ((size_t)w * G + g) * kXyzzVec);
         } else {
             if (!((g >> k) & 1u)) continue;
-            load_xyzz(X, Y + ((size_t)w * G + g) * 12);
+            load_xyzz(X, Y + ((size_t)w * G + g) * kXyzzVec);
         }
         ec::add(acc, X);
     }
-    store_xyzz(P + id * 12, acc);
+    store_xyzz(P + id * kXyzzVec, acc);
 }
 
 // out[s][i] = sum_{e < F} in[s][i F + e], segments of m points.
@@ -414,10 +425,10 @@ __global__ void k_sum_segments(const uint4* __restrict__ in, size_t nseg, uint32
     xyzz acc, X;
     ec::set_inf(acc);
     for (uint32_t e = 0; e < F; ++e) {
-        load_xyzz(X, in + (s * m + i * F + e) * 12);
+        load_xyzz(X, in + (s * m + i * F + e) * kXyzzVec);
         ec::add(acc, X);
     }
-    store_xyzz(out + id * 12, acc);
+    store_xyzz(out + id * kXyzzVec, acc);
 }
 
 // Thread w: S_w = Z_V + L * sum_k 2^k Z_k (Horner over k), Z laid out [W][logG + 1].
@@ -425,18 +436,18 @@ __global__ void k_window_horner(const uint4* __restrict__ Z, size_t W, int logG,
                                 uint4* __restrict__ S) {
     size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (w >= W) return;
-    const uint4* z = Z + w * (size_t)(logG + 1) * 12;
+    const uint4* z = Z + w * (size_t)(logG + 1) * kXyzzVec;
     xyzz acc, X;
     ec::set_inf(acc);
     for (int k = logG - 1; k >= 0; --k) {
         ec::dbl(acc);
-        load_xyzz(X, z + (size_t)k * 12);
+        load_xyzz(X, z + (size_t)k * kXyzzVec);
         ec::add(acc, X);
     }
     for (int l = 0; l < log2L; ++l) ec::dbl(acc);
-    load_xyzz(X, z + (size_t)logG * 12);
+    load_xyzz(X, z + (size_t)logG * kXyzzVec);
     ec::add(acc, X);
-    store_xyzz(S + w * 12, acc);
+    store_xyzz(S + w * kXyzzVec, acc);
 }
 
 // ---------------------------------------------------------------- stage 7
@@ -447,17 +458,17 @@ __global__ void k_combine(const uint4* __restrict__ S, int W, int c, uint32_t* _
     ec::set_inf(acc);
     for (int j = W - 1; j >= 0; --j) {
         for (int k = 0; k < c; ++k) ec::dbl(acc);
-        load_xyzz(X, S + (size_t)j * 12);
+        load_xyzz(X, S + (size_t)j * kXyzzVec);
         ec::add(acc, X);
     }
     affine A;
     ec::to_affine(A, acc);
     if (!ec::is_inf(A)) {
-        fq::from_mont(A.x, A.x);
-        fq::from_mont(A.y, A.y);
+        ec::from_mont(A.x, A.x);
+        ec::from_mont(A.y, A.y);
     }
-    fq::store(out, A.x);
-    fq::store(out + 12, A.y);
+    fq::store_canonical(out, A.x);
+    fq::store_canonical(out + 12, A.y);
 }
 
 // ---------------------------------------------------------------- planning
@@ -531,7 +542,7 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
         off = msm377::align_up(off + bytes, 256);
         return o2;
     };
-    const size_t XY = 192;  // bytes per XYZZ point
+    const size_t XY = kXyzzBytes;  // bytes per XYZZ point in the workspace
     p->off_status = take(256);
     p->off_points = take(o->flags & MSM377_POINTS_PREPARED ? 0 : n * 96);
     p->off_keys0 = take(p->N * 4);
@@ -644,7 +655,7 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     if (prof) profile_mark(s);
 
     uint4* buckets = at<uint4>(workspace, p.off_buckets);
-    MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * 192, s));
+    MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * kXyzzBytes, s));
     AccArgs a;
     a.keys = keys[cur];
     a.vals = vals[cur];
