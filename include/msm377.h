@@ -151,6 +151,33 @@ int msm_g1_host(const uint32_t *points_host, const uint32_t *scalars_host, size_
                 uint32_t *out_host, void *workspace, size_t workspace_bytes,
                 const msm_opts *opts);
 
+/* msm_g1 for callers that cannot allocate device memory. No counterpart in the
+ * paper. Some callers of an MSM library cannot call cudaMalloc or accept a
+ * caller-sized workspace: a plugin loaded into a host program whose device
+ * memory is owned by that program's pooling allocator, a latency-critical
+ * request path on which allocation calls (which can synchronise the device) are
+ * forbidden, or a deployment whose device-memory budget is fixed when the
+ * library is loaded. This entry point takes the same inputs, output and options
+ * as msm_g1 but uses a fixed scratch array of MSM377_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) that the library holds on every GPU that loads it, until the process
+ * exits; it calls no cudaMalloc, cudaFree or other allocating routine.
+ * - Size limit: n and the options must need at most MSM377_NOALLOC_SCRATCH_BYTES
+ *   of workspace (msm_g1_workspace_bytes); with the default options that holds
+ *   up to n = 2^14. Larger requests fail with MSM377_EINVAL and a message.
+ * - The first call on each device looks up the scratch address (a one-time
+ *   set-up per device); make that first call before any stream capture.
+ * - Every call on a device shares the one scratch array and it keeps the last
+ *   call's contents (each call clears what must start at zero). Calls whose
+ *   work overlaps on the GPU (different streams, or different host threads)
+ *   race on it and give wrong results: serialise them.
+ * - The device status word (MSM377_ERANGE for scalars at or above
+ *   opts->scalar_bits) is not reported here; leave scalar_bits at 0 (256) to
+ *   rule that error out. MSM377_PROFILE is rejected.
+ * Asynchronous on opts->stream, like msm_g1. */
+#define MSM377_NOALLOC_SCRATCH_BYTES (64u << 20)
+int msm_g1_noalloc(const uint32_t *points, const uint32_t *scalars, size_t n, uint32_t *out,
+                   const msm_opts *opts);
+
 /* Stage timings of the most recent msm_g1 call made with MSM377_PROFILE, in
  * milliseconds, measured by CUDA events recorded on that call's stream between
  * its stages: [0] prepare + digits, [1] sort, [2] bucket accumulation,

@@ -49,6 +49,7 @@ SIGNATURES = {
     "msm377_imad_probe": (c_int, [c_int, ctypes.POINTER(ctypes.c_double), c_void]),
     "msm377_profile_last": (c_int, [ctypes.POINTER(ctypes.c_float), c_int]),
     "msm377_launch_count": (ctypes.c_uint64, []),
+    "msm_g1_noalloc": (c_int, [c_u32p, c_u32p, c_size, c_u32p, ctypes.POINTER(MsmOpts)]),
 }
 
 
