@@ -9,7 +9,7 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * - Field elements: 12 little-endian 32-bit limbs. STANDARD form is the integer
- *   x in [0, p); MONTGOMERY form is x * 2^390 mod p in [0, p).
+ *   x in [0, p); MONTGOMERY form is x * 2^384 mod p in [0, p).
  * - Affine points: x then y (24 u32). The identity O is (0, 0), which is not on
  *   y^2 = x^3 + 1.
  * - XYZZ points (x = X/ZZ, y = Y/ZZZ): X, Y, ZZ, ZZZ; the identity has ZZ = 0.
@@ -179,10 +179,10 @@ int msm_g1_noalloc(const uint32_t *points, const uint32_t *scalars, size_t n, ui
                    const msm_opts *opts);
 
 /* Stage timings of the most recent msm_g1 call made with MSM377_PROFILE, in
- * milliseconds, measured by CUDA events recorded on that call's stream between
- * its stages: [0] prepare + digits, [1] sort, [2] bucket accumulation,
- * [3] partial merge, [4] bucket reduction, [5] window combine + normalisation.
- * Synchronous (waits for the last event). Writes min(cap, 6) values and returns
+ * milliseconds, from CUDA events recorded on the caller's stream:
+ * [0] prepare + digits, [1] sort, [2] bucket accumulation, [3] the tail:
+ * partial merges, bucket reduction, window combination and normalisation.
+ * Synchronous (waits for the last event). Writes min(cap, 4) values and returns
  * the number of stages, or a negative status. Not thread-safe: one profiled
  * call at a time per process. */
 int msm377_profile_last(float *ms, int cap);

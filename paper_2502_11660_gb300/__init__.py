@@ -22,7 +22,7 @@ FORM_STANDARD = 0
 FORM_MONTGOMERY = 1
 POINTS_PREPARED = 1
 PROFILE = 2
-MSM_STAGES = ("prepare+digits", "sort", "accumulate", "merge", "reduce", "combine")
+MSM_STAGES = ("prepare+digits", "sort", "accumulate", "tail")
 
 __all__ = [
     "MsmError", "MsmOpts", "FORM_STANDARD", "FORM_MONTGOMERY", "POINTS_PREPARED",

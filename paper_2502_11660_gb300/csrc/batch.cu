@@ -38,9 +38,15 @@ __global__ void k_fq_mul(const uint32_t* __restrict__ a, const uint32_t* __restr
         fe x, y, r;
         fq::load_soa(x, a, i, n);
         fq::load_soa(y, b, i, n);
-        // mont(x * R^2) = x R; mont(x R * y) = x y: the standard product.
-        if (form == MSM377_FORM_STANDARD) ec::to_mont(x, x);
-        fq::mul(r, x, y);
+        if (form == MSM377_FORM_STANDARD) {
+            // mont(x * R^2) = x R; mont(x R * y) = x y: the standard product.
+            fe r2;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) r2.v[k] = fq::kR2[k];
+            fq::mul_inl(x, x, r2);
+        }
+        fq::mul_inl(r, x, y);
+        fq::canon(r, r);
         fq::store_soa(out, i, n, r);
     }
 }
@@ -52,9 +58,9 @@ __global__ void k_fq_convert(const uint32_t* __restrict__ in, uint32_t* __restri
         fe x;
         fq::load_soa(x, in, i, n);
         if (to_mont)
-            ec::to_mont(x, x);
+            fq::to_mont(x, x);
         else
-            ec::from_mont(x, x);
+            fq::from_mont(x, x);
         fq::store_soa(out, i, n, x);
     }
 }
@@ -69,19 +75,24 @@ __global__ void k_padd(const uint32_t* __restrict__ acc, const uint32_t* __restr
         fq::load_soa(Q.x, q, i, n);
         fq::load_soa(Q.y, q + 12 * n, i, n);
         if (form == MSM377_FORM_STANDARD) {
-            ec::to_mont(P.X, P.X);
-            ec::to_mont(P.Y, P.Y);
-            ec::to_mont(P.ZZ, P.ZZ);
-            ec::to_mont(P.ZZZ, P.ZZZ);
-            ec::to_mont(Q.x, Q.x);
-            ec::to_mont(Q.y, Q.y);
+            fq::to_mont(P.X, P.X);
+            fq::to_mont(P.Y, P.Y);
+            fq::to_mont(P.ZZ, P.ZZ);
+            fq::to_mont(P.ZZZ, P.ZZZ);
+            fq::to_mont(Q.x, Q.x);
+            fq::to_mont(Q.y, Q.y);
         }
         ec::madd(P, Q);
         if (form == MSM377_FORM_STANDARD) {
-            ec::from_mont(P.X, P.X);
-            ec::from_mont(P.Y, P.Y);
-            ec::from_mont(P.ZZ, P.ZZ);
-            ec::from_mont(P.ZZZ, P.ZZZ);
+            fq::from_mont(P.X, P.X);
+            fq::from_mont(P.Y, P.Y);
+            fq::from_mont(P.ZZ, P.ZZ);
+            fq::from_mont(P.ZZZ, P.ZZZ);
+        } else {
+            fq::canon(P.X, P.X);
+            fq::canon(P.Y, P.Y);
+            fq::canon(P.ZZ, P.ZZ);
+            fq::canon(P.ZZZ, P.ZZZ);
         }
         store_xyzz_soa(out, i, n, P);
     }
@@ -94,16 +105,16 @@ __global__ void k_xyzz_to_affine(const uint32_t* __restrict__ in, uint32_t* __re
         xyzz P;
         load_xyzz_soa(P, in, i, n);
         if (form == MSM377_FORM_STANDARD) {
-            ec::to_mont(P.X, P.X);
-            ec::to_mont(P.Y, P.Y);
-            ec::to_mont(P.ZZ, P.ZZ);
-            ec::to_mont(P.ZZZ, P.ZZZ);
+            fq::to_mont(P.X, P.X);
+            fq::to_mont(P.Y, P.Y);
+            fq::to_mont(P.ZZ, P.ZZ);
+            fq::to_mont(P.ZZZ, P.ZZZ);
         }
         affine A;
         ec::to_affine(A, P);
         if (form == MSM377_FORM_STANDARD) {
-            ec::from_mont(A.x, A.x);
-            ec::from_mont(A.y, A.y);
+            fq::from_mont(A.x, A.x);
+            fq::from_mont(A.y, A.y);
         }
         fq::store_soa(aff, i, n, A.x);
         fq::store_soa(aff + 12 * n, i, n, A.y);
@@ -123,18 +134,13 @@ __global__ void k_gen_mul(const uint32_t* __restrict__ seeds, size_t n, uint32_t
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         affine G;
-        {
-            uint32_t wx[12], wy[12];
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                wx[k] = kGx[k];
-                wy[k] = kGy[k];
-            }
-            fq::unpack(G.x, wx);
-            fq::unpack(G.y, wy);
+        for (int k = 0; k < 12; ++k) {
+            G.x.v[k] = kGx[k];
+            G.y.v[k] = kGy[k];
         }
-        ec::to_mont(G.x, G.x);
-        ec::to_mont(G.y, G.y);
+        fq::to_mont(G.x, G.x);
+        fq::to_mont(G.y, G.y);
         uint32_t s[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) s[k] = seeds[8 * i + k];
@@ -148,11 +154,11 @@ __global__ void k_gen_mul(const uint32_t* __restrict__ seeds, size_t n, uint32_t
         affine A;
         ec::to_affine(A, P);
         if (!ec::is_inf(A)) {
-            ec::from_mont(A.x, A.x);
-            ec::from_mont(A.y, A.y);
+            fq::from_mont(A.x, A.x);
+            fq::from_mont(A.y, A.y);
         }
-        fq::store_canonical(out + 24 * i, A.x);
-        fq::store_canonical(out + 24 * i + 12, A.y);
+        fq::store(out + 24 * i, A.x);
+        fq::store(out + 24 * i + 12, A.y);
     }
 }
 

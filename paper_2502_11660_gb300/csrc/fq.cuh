@@ -1,342 +1,351 @@
 // Fq = GF(p), p the 377-bit BLS12-377 base-field prime, on sm_103a.
 //
-// Representation in registers: 15 digits of radix 2^26 (390 bits), each held in
-// a 32-bit register with headroom, Montgomery form x * R mod p with R = 2^390.
-// This is the paper's element format idea (Sec. III-B/III-D: 25-bit elements in
-// 32-bit lanes, up to 26 bits per element, carries propagated coarsely instead
-// of exactly) carried over to the GPU: a product of two 26-bit digits is one
-// mad.wide.u32 (32x32 + 64 -> 64) into a 64-bit column sum, and 30 such terms
-// fit in 64 bits, so the 29 columns of a*b accumulate with no carry chains at
-// all; the 15 Montgomery steps (m_i = -c_i mod 2^26, because p = 1 mod 2^46)
-// add m_i * p into the columns the same way; and the result leaves in two
-// rounds of coarse carry propagation (mask, shift, add), the paper's step0 /
-// step1, not an exact serial carry.
+// Elements are 12 little-endian 32-bit limbs in Montgomery form x*R mod p with
+// R = 2^384. Multiplication is word-serial Montgomery (CIOS): for each limb a_i
+// the row a_i*b is added with a mad.lo.cc / madc.hi.cc carry chain, then
+// m = -t_0 (because -p^-1 = 0xffffffff mod 2^32, p = 1 mod 2^46) and the row
+// m*p is added the same way, and the accumulator drops one word. Every chain of
+// one row sits in one asm statement so the carry flag never crosses statements.
 //
-// Invariants (checked by the bound analysis in ec.cuh and by the tests):
-//  * digits of any multiplication input are < 2^29, its value < 2^383;
-//    then every column sum stays below 15*2^58 + 15*2^52 < 2^62 and the
-//    Montgomery output value is < a*b/R + p < 2p.
-//  * multiplication outputs are "normal": digits 0..13 <= 2^26 + 2^10,
-//    digit 14 < 2^14 (value < 2p).
-//  * add() is digit-wise (no carries); sub<K>(a, b) is a - b + K*p digit-wise
-//    with K*p written in a redundant form whose digits 0..13 are >= 2^28 - 4,
-//    so it never goes negative as long as b < (K - 1) p and b's digits are
-//    below 2^28 - 4.
-// Memory formats stay the packed 12 x 32-bit little-endian limbs (pack/unpack).
+// mul() is one out-of-line function. A point operation makes 10-14 calls; with
+// the body inlined at every call site the code of one point addition is about
+// 100 KB, which thrashes the instruction cache: measured on GB300, one thread's
+// XYZZ doubling takes 63k cycles inlined and 27k out of line, and a full grid of
+// doublings runs 1.1-1.6 G/s inlined and 1.8-1.9 G/s out of line. mul_inl() is the
+// inlined body for kernels with a single multiplication per element.
+//
+// Lazy reduction (the GPU form of the paper's skipped fine reduction and
+// unreduced intermediate additions, Sec. III-E): a product of inputs a, b with
+// a*b < p*R leaves mul() in [0, 2p) without the final conditional subtraction.
+// All values kept in registers or memory by the curve code live in [0, 2p);
+// add/sub fold back into [0, 2p) with one masked correction of 2p, so every
+// product satisfies a*b < 4p^2 < p*R (R/p > 152). canon() maps [0, 2p) to [0, p).
+// Accumulator bound: with b < 2^383 the running value before each shift stays
+// below 2^416, so 13 words hold it and the final hi-chain carries are zero.
+//
+// (A carry-save variant in the style of the paper's Sec. III-D -- 16 digits of
+// 24 bits, 64-bit mad.wide column sums, two coarse carry rounds -- was built and
+// measured: 2.7x lower multiplication latency than inlined CIOS but, at the
+// quarter-rate 64-bit mad.wide, 1.3x lower throughput in full point operations,
+// and slower than out-of-line CIOS in both; it is not used.)
 #pragma once
 #include <stdint.h>
 
 namespace fq {
 
-constexpr int N = 15;      // digits per element
-constexpr int NW = 12;     // 32-bit words per packed element
-constexpr uint32_t MASK = (1u << 26) - 1u;
+constexpr int N = 12;
 
 struct fe {
-    uint32_t d[N];
+    uint32_t v[N];
 };
 
-// radix-2^26 digits of p
-__host__ __device__ constexpr uint32_t p26(int i) {
-    switch (i) {
-        case 0: return 0x1u;
-        case 1: return 0x2300000u;
-        case 2: return 0x850u;
-        case 3: return 0x110c000u;
-        case 4: return 0x170b5du;
-        case 5: return 0x2825200u;
-        case 6: return 0x33622fbu;
-        case 7: return 0x4e3c7bu;
-        case 8: return 0x1f300f5u;
-        case 9: return 0x2c688b6u;
-        case 10: return 0x2ca1493u;
-        case 11: return 0xec1701u;
-        case 12: return 0x110eac6u;
-        case 13: return 0x29185f1u;
-        default: return 0x1ae3u;
-    }
-}
+// p, 2p, R mod p (Montgomery one), R^2 mod p (to-Montgomery factor), R^3 mod p.
+__device__ __constant__ static const uint32_t kP[N] = {
+    0x00000001u, 0x8508c000u, 0x30000000u, 0x170b5d44u, 0xba094800u, 0x1ef3622fu,
+    0x00f5138fu, 0x1a22d9f3u, 0x6ca1493bu, 0xc63b05c0u, 0x17c510eau, 0x01ae3a46u};
+__device__ __constant__ static const uint32_t k2P[N] = {
+    0x00000002u, 0x0a118000u, 0x60000001u, 0x2e16ba88u, 0x74129000u, 0x3de6c45fu,
+    0x01ea271eu, 0x3445b3e6u, 0xd9429276u, 0x8c760b80u, 0x2f8a21d5u, 0x035c748cu};
+__device__ __constant__ static const uint32_t kOne[N] = {
+    0xffffff68u, 0x02cdffffu, 0x7fffffb1u, 0x51409f83u, 0x8a7d3ff2u, 0x9f7db3a9u,
+    0x6e7c6305u, 0x7b4e97b7u, 0x803c84e8u, 0x4cf495bfu, 0xe2fdf49au, 0x008d6661u};
+__device__ __constant__ static const uint32_t kR2[N] = {
+    0x9400cd22u, 0xb786686cu, 0xb00431b1u, 0x0329fcaau, 0x62d6b46du, 0x22a5f111u,
+    0x827dc3acu, 0xbfdf7d03u, 0x41790bf9u, 0x837e92f0u, 0x1e914b88u, 0x006dfccbu};
+__device__ __constant__ static const uint32_t kR3[N] = {
+    0x8815de20u, 0x581f532fu, 0xbe329585u, 0xe50f4148u, 0x0449f513u, 0x2be8b118u,
+    0xc804a20eu, 0x6a2a9516u, 0x13590cb9u, 0x3f725407u, 0xc0e7dda5u, 0x01065ab4u};
 
-// canonical radix-2^26 digit i of K*p (the top digit keeps any carry)
-__host__ __device__ constexpr uint32_t kp_digit(int K, int i) {
-    uint64_t c = 0;
-    uint32_t out = 0;
-    for (int j = 0; j <= i; ++j) {
-        uint64_t t = (uint64_t)K * p26(j) + c;
-        out = (j == N - 1) ? (uint32_t)t : (uint32_t)(t & MASK);
-        c = t >> 26;
-    }
-    return out;
-}
-
-// digit i of K*p in the redundant form used by sub<K>: 2^28 is added to digits
-// 0..13 and 4 is borrowed from each next digit (2^28 = 4 * 2^26), value unchanged.
-__host__ __device__ constexpr uint32_t sub_digit(int K, int i) {
-    return kp_digit(K, i) + (i < N - 1 ? (1u << 28) : 0u) - (i > 0 ? 4u : 0u);
-}
-
-// 2^390 mod p (Montgomery one) and 2^780 mod p (to-Montgomery factor), radix 2^26.
-__host__ __device__ constexpr uint32_t one26(int i) {
-    switch (i) {
-        case 0: return 0x3ffd9ebu;
-        case 1: return 0x20fffffu;
-        case 2: return 0x2c35c9cu;
-        case 3: return 0x1203fffu;
-        case 4: return 0x26c393au;
-        case 5: return 0x3234524u;
-        case 6: return 0x35dc785u;
-        case 7: return 0x9aa955u;
-        case 8: return 0xec8afeu;
-        case 9: return 0x16bb283u;
-        case 10: return 0x25e6384u;
-        case 11: return 0x137dc5cu;
-        case 12: return 0x2c350fau;
-        case 13: return 0x2e3314u;
-        default: return 0xedu;
-    }
-}
-
-__host__ __device__ constexpr uint32_t r2_26(int i) {
-    switch (i) {
-        case 0: return 0xd21be9u;
-        case 1: return 0x3625003u;
-        case 2: return 0x19584fbu;
-        case 3: return 0x7fcc6cu;
-        case 4: return 0x605039u;
-        case 5: return 0x3d455f5u;
-        case 6: return 0x2a84fb8u;
-        case 7: return 0x30f4b26u;
-        case 8: return 0x34ef1e7u;
-        case 9: return 0x184d1b5u;
-        case 10: return 0x91d1b4u;
-        case 11: return 0x329f86du;
-        case 12: return 0x58072du;
-        case 13: return 0x34f7770u;
-        default: return 0x3c5u;
-    }
-}
+// 2p limbs as compile-time values for masked corrections.
+#define FQ_2P_LIMBS 0x00000002u, 0x0a118000u, 0x60000001u, 0x2e16ba88u, 0x74129000u, \
+    0x3de6c45fu, 0x01ea271eu, 0x3445b3e6u, 0xd9429276u, 0x8c760b80u, 0x2f8a21d5u, 0x035c748cu
+#define FQ_P_LIMBS 0x00000001u, 0x8508c000u, 0x30000000u, 0x170b5d44u, 0xba094800u, \
+    0x1ef3622fu, 0x00f5138fu, 0x1a22d9f3u, 0x6ca1493bu, 0xc63b05c0u, 0x17c510eau, 0x01ae3a46u
 
 __device__ __forceinline__ void set_zero(fe& r) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = 0;
+    for (int k = 0; k < N; ++k) r.v[k] = 0;
 }
 
 __device__ __forceinline__ void set_one(fe& r) {
+    const uint32_t one[N] = {0xffffff68u, 0x02cdffffu, 0x7fffffb1u, 0x51409f83u, 0x8a7d3ff2u,
+                             0x9f7db3a9u, 0x6e7c6305u, 0x7b4e97b7u, 0x803c84e8u, 0x4cf495bfu,
+                             0xe2fdf49au, 0x008d6661u};
 #pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = one26(k);
+    for (int k = 0; k < N; ++k) r.v[k] = one[k];
 }
 
-__device__ __forceinline__ void set_r2(fe& r) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = r2_26(k);
-}
-
-// Montgomery step i on the column window c[i .. i+15]: column i is complete
-// (every a_k b_{i-k} and m_k p_{i-k} with k < i is in), so m_i = -c_i mod 2^26
-// zeroes its low 26 bits (p_0 = 1), m_i p_j goes into columns i + j and the
-// column's high part carries into column i + 1. Columns below i are dead, so
-// only 16 column sums are live at a time.
-#define FQ_REDUCE_STEP(c, i)                                                  \
-    {                                                                         \
-        const uint32_t m_ = (0u - (uint32_t)c[(i)]) & MASK;                   \
-        c[(i)] += m_;                                                         \
-        _Pragma("unroll") for (int j_ = 1; j_ < N; ++j_) c[(i) + j_] +=       \
-            (uint64_t)m_ * p26(j_);                                           \
-        c[(i) + 1] += c[(i)] >> 26;                                           \
-    }
-
-// Two rounds of coarse carry propagation over the result columns c[N .. 2N-1]
-// (Sec. III-D step0 / step1); digits 0..13 end <= 2^26 + 2^10.
-#define FQ_FINISH(r, c)                                                                     \
-    {                                                                                       \
-        uint64_t e_[N];                                                                     \
-        e_[0] = c[N] & MASK;                                                                \
-        _Pragma("unroll") for (int k_ = 1; k_ < N; ++k_) e_[k_] =                           \
-            (c[N + k_] & MASK) + (c[N + k_ - 1] >> 26); /* c[2N-1] = 0 */                  \
-        r.d[0] = (uint32_t)e_[0];                                                           \
-        _Pragma("unroll") for (int k_ = 1; k_ < N - 1; ++k_) r.d[k_] =                      \
-            (uint32_t)((e_[k_] & MASK) + (e_[k_ - 1] >> 26));                               \
-        r.d[N - 1] = (uint32_t)(e_[N - 1] + (e_[N - 2] >> 26)); /* value bound: < 2^14 */  \
-    }
-
-// r = a * b * 2^-390 mod p, result normal (value < 2p).
-__device__ __forceinline__ void mul(fe& r, const fe& a, const fe& b) {
-    uint64_t c[2 * N];
-#pragma unroll
-    for (int k = 0; k < 2 * N; ++k) c[k] = 0;
+// r = a*b*R^-1 mod p, result in [0, 2p) when a*b < p*R. Inlined body.
+__device__ __forceinline__ void mul_inl(fe& r, const fe& a, const fe& bb) {
+    const uint32_t* b = bb.v;
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0, t9 = 0,
+             t10 = 0, t11 = 0, t12 = 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) c[i + j] += (uint64_t)a.d[i] * b.d[j];
-        FQ_REDUCE_STEP(c, i)
+        asm(
+        "mad.lo.cc.u32 %0, %13, %14, %0;\n\t"
+        "madc.lo.cc.u32 %1, %13, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, %16, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, %17, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, %18, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, %19, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, %20, %6;\n\t"
+        "madc.lo.cc.u32 %7, %13, %21, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, %22, %8;\n\t"
+        "madc.lo.cc.u32 %9, %13, %23, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, %24, %10;\n\t"
+        "madc.lo.cc.u32 %11, %13, %25, %11;\n\t"
+        "addc.u32 %12, %12, 0;\n\t"
+        "mad.hi.cc.u32 %1, %13, %14, %1;\n\t"
+        "madc.hi.cc.u32 %2, %13, %15, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, %16, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, %18, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, %19, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, %20, %7;\n\t"
+        "madc.hi.cc.u32 %8, %13, %21, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, %22, %9;\n\t"
+        "madc.hi.cc.u32 %10, %13, %23, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, %24, %11;\n\t"
+        "madc.hi.u32 %12, %13, %25, %12;"
+            : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9), "+r"(t10), "+r"(t11), "+r"(t12)
+            : "r"(a.v[i]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
+        uint32_t m = 0u - t0;
+        asm(
+        "add.cc.u32 %0, %0, %13;\n\t"
+        "madc.lo.cc.u32 %1, %13, 0x8508c000, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, 0x30000000, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, 0x170b5d44, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, 0xba094800, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, 0x1ef3622f, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, 0x00f5138f, %6;\n\t"
+        "madc.lo.cc.u32 %7, %13, 0x1a22d9f3, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, 0x6ca1493b, %8;\n\t"
+        "madc.lo.cc.u32 %9, %13, 0xc63b05c0, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, 0x17c510ea, %10;\n\t"
+        "madc.lo.cc.u32 %11, %13, 0x01ae3a46, %11;\n\t"
+        "addc.u32 %12, %12, 0;\n\t"
+        "mad.hi.cc.u32 %2, %13, 0x8508c000, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, 0x30000000, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, 0x170b5d44, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, 0xba094800, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, 0x1ef3622f, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, 0x00f5138f, %7;\n\t"
+        "madc.hi.cc.u32 %8, %13, 0x1a22d9f3, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, 0x6ca1493b, %9;\n\t"
+        "madc.hi.cc.u32 %10, %13, 0xc63b05c0, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, 0x17c510ea, %11;\n\t"
+        "madc.hi.u32 %12, %13, 0x01ae3a46, %12;"
+            : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9), "+r"(t10), "+r"(t11), "+r"(t12)
+            : "r"(m));
+        t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8; t8 = t9;
+        t9 = t10; t10 = t11; t11 = t12; t12 = 0;
     }
-    FQ_FINISH(r, c)
+    r.v[0] = t0; r.v[1] = t1; r.v[2] = t2; r.v[3] = t3; r.v[4] = t4; r.v[5] = t5;
+    r.v[6] = t6; r.v[7] = t7; r.v[8] = t8; r.v[9] = t9; r.v[10] = t10; r.v[11] = t11;
 }
 
-// r = a^2 * 2^-390 mod p: the symmetric products once, doubled. Row i adds
-// a_i^2 and 2 a_i a_j (j > i); column i is complete after row i as in mul().
-__device__ __forceinline__ void sqr(fe& r, const fe& a) {
-    uint64_t c[2 * N];
+// Out-of-line multiplication used by the point arithmetic (one copy of the code).
+static __device__ __noinline__ void mul(fe& r, const fe& a, const fe& b) { mul_inl(r, a, b); }
+
+__device__ __forceinline__ void sqr(fe& r, const fe& a) { mul(r, a, a); }
+
+// r = a + b, inputs in [0, 2p); result folded into [0, 2p).
+__device__ __forceinline__ void add(fe& rr, const fe& a, const fe& bb) {
+    uint32_t r[N];
+    const uint32_t* b = bb.v;
 #pragma unroll
-    for (int k = 0; k < 2 * N; ++k) c[k] = 0;
+    for (int k = 0; k < N; ++k) r[k] = a.v[k];
+    asm(
+        "add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, %13;\n\t"
+        "addc.cc.u32 %2, %2, %14;\n\t"
+        "addc.cc.u32 %3, %3, %15;\n\t"
+        "addc.cc.u32 %4, %4, %16;\n\t"
+        "addc.cc.u32 %5, %5, %17;\n\t"
+        "addc.cc.u32 %6, %6, %18;\n\t"
+        "addc.cc.u32 %7, %7, %19;\n\t"
+        "addc.cc.u32 %8, %8, %20;\n\t"
+        "addc.cc.u32 %9, %9, %21;\n\t"
+        "addc.cc.u32 %10, %10, %22;\n\t"
+        "addc.u32 %11, %11, %23;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
+    uint32_t u[N], mask;
+    asm(
+        "sub.cc.u32 %0, %13, 0x00000002;\n\t"
+        "subc.cc.u32 %1, %14, 0x0a118000;\n\t"
+        "subc.cc.u32 %2, %15, 0x60000001;\n\t"
+        "subc.cc.u32 %3, %16, 0x2e16ba88;\n\t"
+        "subc.cc.u32 %4, %17, 0x74129000;\n\t"
+        "subc.cc.u32 %5, %18, 0x3de6c45f;\n\t"
+        "subc.cc.u32 %6, %19, 0x01ea271e;\n\t"
+        "subc.cc.u32 %7, %20, 0x3445b3e6;\n\t"
+        "subc.cc.u32 %8, %21, 0xd9429276;\n\t"
+        "subc.cc.u32 %9, %22, 0x8c760b80;\n\t"
+        "subc.cc.u32 %10, %23, 0x2f8a21d5;\n\t"
+        "subc.cc.u32 %11, %24, 0x035c748c;\n\t"
+        "subc.u32 %12, 0, 0;"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+          "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(mask)
+        : "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+          "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]));
+    // mask = ~0 when a + b < 2p (keep the sum), 0 otherwise (take the difference)
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        c[2 * i] += (uint64_t)a.d[i] * a.d[i];
-        const uint32_t a2 = a.d[i] << 1;
-#pragma unroll
-        for (int j = i + 1; j < N; ++j) c[i + j] += (uint64_t)a2 * a.d[j];
-        FQ_REDUCE_STEP(c, i)
-    }
-    FQ_FINISH(r, c)
+    for (int k = 0; k < N; ++k) rr.v[k] = (r[k] & mask) | (u[k] & ~mask);
 }
 
-// r = a + b, digit-wise (no carries).
-__device__ __forceinline__ void add(fe& r, const fe& a, const fe& b) {
+// r = a - b, inputs in [0, 2p); adds 2p when the difference is negative.
+__device__ __forceinline__ void sub(fe& rr, const fe& a, const fe& bb) {
+    uint32_t r[N], mask;
+    const uint32_t* b = bb.v;
 #pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
+    for (int k = 0; k < N; ++k) r[k] = a.v[k];
+    asm(
+        "sub.cc.u32 %0, %0, %13;\n\t"
+        "subc.cc.u32 %1, %1, %14;\n\t"
+        "subc.cc.u32 %2, %2, %15;\n\t"
+        "subc.cc.u32 %3, %3, %16;\n\t"
+        "subc.cc.u32 %4, %4, %17;\n\t"
+        "subc.cc.u32 %5, %5, %18;\n\t"
+        "subc.cc.u32 %6, %6, %19;\n\t"
+        "subc.cc.u32 %7, %7, %20;\n\t"
+        "subc.cc.u32 %8, %8, %21;\n\t"
+        "subc.cc.u32 %9, %9, %22;\n\t"
+        "subc.cc.u32 %10, %10, %23;\n\t"
+        "subc.cc.u32 %11, %11, %24;\n\t"
+        "subc.u32 %12, 0, 0;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "=r"(mask)
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
+    const uint32_t twop[N] = {FQ_2P_LIMBS};
+    uint32_t c[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) c[k] = twop[k] & mask;
+    asm(
+        "add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, %13;\n\t"
+        "addc.cc.u32 %2, %2, %14;\n\t"
+        "addc.cc.u32 %3, %3, %15;\n\t"
+        "addc.cc.u32 %4, %4, %16;\n\t"
+        "addc.cc.u32 %5, %5, %17;\n\t"
+        "addc.cc.u32 %6, %6, %18;\n\t"
+        "addc.cc.u32 %7, %7, %19;\n\t"
+        "addc.cc.u32 %8, %8, %20;\n\t"
+        "addc.cc.u32 %9, %9, %21;\n\t"
+        "addc.cc.u32 %10, %10, %22;\n\t"
+        "addc.u32 %11, %11, %23;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+        : "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(c[5]), "r"(c[6]),
+          "r"(c[7]), "r"(c[8]), "r"(c[9]), "r"(c[10]), "r"(c[11]));
+#pragma unroll
+    for (int k = 0; k < N; ++k) rr.v[k] = r[k];
 }
 
-// r = a - b + K p, digit-wise. Needs b < (K - 1) p and b's digits 0..13 < 2^28 - 4.
-template <int K>
-__device__ __forceinline__ void sub(fe& r, const fe& a, const fe& b) {
+__device__ __forceinline__ void dbl(fe& r, const fe& a) { add(r, a, a); }
+
+// [0, 2p) -> [0, p)
+__device__ __forceinline__ void canon(fe& rr, const fe& a) {
+    uint32_t u[N], mask;
+    asm(
+        "sub.cc.u32 %0, %13, 0x00000001;\n\t"
+        "subc.cc.u32 %1, %14, 0x8508c000;\n\t"
+        "subc.cc.u32 %2, %15, 0x30000000;\n\t"
+        "subc.cc.u32 %3, %16, 0x170b5d44;\n\t"
+        "subc.cc.u32 %4, %17, 0xba094800;\n\t"
+        "subc.cc.u32 %5, %18, 0x1ef3622f;\n\t"
+        "subc.cc.u32 %6, %19, 0x00f5138f;\n\t"
+        "subc.cc.u32 %7, %20, 0x1a22d9f3;\n\t"
+        "subc.cc.u32 %8, %21, 0x6ca1493b;\n\t"
+        "subc.cc.u32 %9, %22, 0xc63b05c0;\n\t"
+        "subc.cc.u32 %10, %23, 0x17c510ea;\n\t"
+        "subc.cc.u32 %11, %24, 0x01ae3a46;\n\t"
+        "subc.u32 %12, 0, 0;"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+          "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(mask)
+        : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]),
+          "r"(a.v[6]), "r"(a.v[7]), "r"(a.v[8]), "r"(a.v[9]), "r"(a.v[10]), "r"(a.v[11]));
 #pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + sub_digit(K, k) - b.d[k];
+    for (int k = 0; k < N; ++k) rr.v[k] = (a.v[k] & mask) | (u[k] & ~mask);
 }
 
-// Two rounds of coarse carry propagation (Sec. III-D step0/step1): value unchanged,
-// digits 0..13 <= 2^26 afterwards for input digits < 2^31; the top digit keeps its excess.
-__device__ __forceinline__ void settle(fe& a) {
-    uint32_t t[N];
-    t[0] = a.d[0] & MASK;
-#pragma unroll
-    for (int k = 1; k < N - 1; ++k) t[k] = (a.d[k] & MASK) + (a.d[k - 1] >> 26);
-    t[N - 1] = a.d[N - 1] + (a.d[N - 2] >> 26);
-    a.d[0] = t[0];
-#pragma unroll
-    for (int k = 1; k < N - 1; ++k) a.d[k] = (t[k] & MASK) + (t[k - 1] >> 26);
-    a.d[N - 1] = t[N - 1] + (t[N - 2] >> 26);
-}
-
-// Exact digits (each < 2^26 except the top one) by a serial carry pass.
-__device__ __forceinline__ void exact(fe& a) {
-    uint32_t c = 0;
-#pragma unroll
-    for (int k = 0; k < N - 1; ++k) {
-        uint32_t t = a.d[k] + c;
-        a.d[k] = t & MASK;
-        c = t >> 26;
-    }
-    a.d[N - 1] += c;
-}
-
-// a >= p for exact digits
-__device__ __forceinline__ bool geq_p(const fe& a) {
-#pragma unroll
-    for (int k = N - 1; k >= 0; --k) {
-        if (a.d[k] != p26(k)) return a.d[k] > p26(k);
-    }
-    return true;
-}
-
-// a -= p for exact digits with a >= p (result exact)
-__device__ __forceinline__ void sub_p_exact(fe& a) {
-    int32_t borrow = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        int32_t t = (int32_t)a.d[k] - (int32_t)p26(k) - borrow;
-        borrow = t < 0;
-        a.d[k] = (uint32_t)(t + (borrow ? (1 << 26) : 0));
-    }
-}
-
-// Canonical exact digits in [0, p) from any value < 64 p.
-__device__ __forceinline__ void canon(fe& a) {
-    exact(a);
-    while (geq_p(a)) sub_p_exact(a);
-}
-
-// value == 0 mod p, for a normal value (< 2p): exact digits are 0 or p.
-__device__ __forceinline__ bool is_zero_normal(fe a) {
-    exact(a);
-    uint32_t z = 0, q = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-        z |= a.d[k];
-        q |= a.d[k] ^ p26(k);
-    }
-    return z == 0 || q == 0;
-}
-
-// value == 0 mod p for any value < 64 p (slow path).
-__device__ __forceinline__ bool is_zero_any(fe a) {
-    canon(a);
-    uint32_t z = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) z |= a.d[k];
-    return z == 0;
+// r = -a for a in [0, 2p): 2p - a, then folded into [0, 2p) (maps 0 to 0).
+__device__ __forceinline__ void neg(fe& r, const fe& a) {
+    fe z;
+    set_zero(z);
+    sub(r, z, a);
 }
 
 __device__ __forceinline__ bool is_zero_raw(const fe& a) {
-    uint32_t z = 0;
+    uint32_t o = 0;
 #pragma unroll
-    for (int k = 0; k < N; ++k) z |= a.d[k];
-    return z == 0;
+    for (int k = 0; k < N; ++k) o |= a.v[k];
+    return o == 0;
 }
 
-// ---- packed 12 x 32-bit limbs <-> digits
-
-__device__ __forceinline__ void unpack(fe& r, const uint32_t (&w)[NW]) {
+// a in [0, 2p) represents zero iff a == 0 or a == p.
+__device__ __forceinline__ bool is_zero(const fe& a) {
+    const uint32_t p[N] = {FQ_P_LIMBS};
+    uint32_t o = 0, q = 0;
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const int bit = 26 * i, k = bit >> 5, off = bit & 31;
-        uint32_t lo = w[k] >> off;
-        uint32_t hi = (off > 6 && k + 1 < NW) ? (w[k + 1] << (32 - off)) : 0u;
-        r.d[i] = (lo | hi) & MASK;
+    for (int k = 0; k < N; ++k) {
+        o |= a.v[k];
+        q |= a.v[k] ^ p[k];
     }
+    return o == 0 || q == 0;
 }
 
-// Needs exact digits (< 2^26) and a value < 2^384.
-__device__ __forceinline__ void pack(uint32_t (&w)[NW], const fe& a) {
-#pragma unroll
-    for (int k = 0; k < NW; ++k) w[k] = 0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const int bit = 26 * i, k = bit >> 5, off = bit & 31;
-        w[k] |= a.d[i] << off;
-        if (off > 6 && k + 1 < NW) w[k + 1] |= a.d[i] >> (32 - off);
-    }
+// a == b as field elements, both in [0, 2p).
+__device__ __forceinline__ bool equal(const fe& a, const fe& b) {
+    fe d;
+    sub(d, a, b);
+    return is_zero(d);
 }
 
-__device__ __forceinline__ void load_packed(fe& r, const uint32_t* p) {
-    uint32_t w[NW];
+__device__ __forceinline__ void to_mont(fe& r, const fe& a_std) {
+    fe r2;
 #pragma unroll
-    for (int k = 0; k < NW; ++k) w[k] = p[k];
-    unpack(r, w);
+    for (int k = 0; k < N; ++k) r2.v[k] = kR2[k];
+    mul(r, a_std, r2);
+    canon(r, r);
 }
 
-// Stores canonical [0, p) packed limbs.
-__device__ __forceinline__ void store_canonical(uint32_t* p, fe a) {
-    canon(a);
-    uint32_t w[NW];
-    pack(w, a);
-#pragma unroll
-    for (int k = 0; k < NW; ++k) p[k] = w[k];
+__device__ __forceinline__ void from_mont(fe& r, const fe& a) {
+    fe one;
+    set_zero(one);
+    one.v[0] = 1;
+    mul(r, a, one);
+    canon(r, r);
 }
 
-// Strided (structure-of-arrays) packed access: limb k of element i at base[k * stride + i].
+__device__ __forceinline__ void load(fe& r, const uint32_t* p) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) r.v[k] = p[k];
+}
+
+__device__ __forceinline__ void store(uint32_t* p, const fe& a) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) p[k] = a.v[k];
+}
+
+// Strided (structure-of-arrays) access: limb k of element i at base[k * stride + i].
 __device__ __forceinline__ void load_soa(fe& r, const uint32_t* base, size_t i, size_t stride) {
-    uint32_t w[NW];
 #pragma unroll
-    for (int k = 0; k < NW; ++k) w[k] = base[k * stride + i];
-    unpack(r, w);
+    for (int k = 0; k < N; ++k) r.v[k] = base[k * stride + i];
 }
 
-__device__ __forceinline__ void store_soa(uint32_t* base, size_t i, size_t stride, fe a) {
-    canon(a);
-    uint32_t w[NW];
-    pack(w, a);
+__device__ __forceinline__ void store_soa(uint32_t* base, size_t i, size_t stride, const fe& a) {
 #pragma unroll
-    for (int k = 0; k < NW; ++k) base[k * stride + i] = w[k];
+    for (int k = 0; k < N; ++k) base[k * stride + i] = a.v[k];
+}
+
+// a < p for a standard-form input (used to validate boundary data).
+__device__ __forceinline__ bool lt_p(const fe& a) {
+    const uint32_t p[N] = {FQ_P_LIMBS};
+#pragma unroll
+    for (int k = N - 1; k >= 0; --k) {
+        if (a.v[k] != p[k]) return a.v[k] < p[k];
+    }
+    return false;
 }
 
 }  // namespace fq

@@ -2,22 +2,26 @@
 // paper: windows, bucket accumulation, bucket aggregation, group aggregation),
 // laid out for one GB300.
 //
-// Stages, all on the caller's stream:
-//  1. prepare   standard affine -> Montgomery affine (96 B per point, AoS, so a
-//               random gather of one point reads three full 32 B sectors)
-//  2. digits    c-bit window digits per scalar (signed or unsigned);
-//               key = |digit|, value = point index | sign << 31, window-major
-//  3. sort      stable LSD radix sort of (key, value) within each window,
-//               8-bit digits per pass (histogram, scans, ranked scatter)
-//  4. accumulate  the sorted stream is cut into equal chunks of K items, one per
-//               thread, so heavy buckets are spread across threads and warps;
-//               runs inside a chunk are summed with mixed PADDs and written to
-//               their bucket, runs that cross a chunk edge leave partial sums
-//  5. merge     partial sums of runs that cross chunk edges are added up
-//  6. reduce    per window sum_b b * B_b: segments of L buckets by running sums
-//               (in-thread), then sum_g g * Y_g split by the bits of g into
-//               independent sums, recombined by Horner
-//  7. combine   sum_j 2^(c j) S_j by Horner, affine normalisation, standard form
+// Stages:
+//  1. prepare     standard affine -> Montgomery affine (96 B per point, AoS, so a
+//                 random gather of one point reads three full 32 B sectors)
+//  2. digits      c-bit window digits per scalar (signed or unsigned);
+//                 key = |digit|, value = point index | sign << 31, window-major
+//  3. sort        stable LSD radix sort of (key, value) within each window,
+//                 8-bit digits per pass (histogram, scans, ranked scatter)
+//  4. accumulate  per window, the sorted stream is cut into equal chunks of K
+//                 items, one per thread, so heavy buckets spread over threads;
+//                 runs inside a chunk are summed with mixed PADDs and written
+//                 to their bucket, runs
+//                 crossing a chunk edge leave partial sums
+//  5. merge       partial sums of runs that cross chunk edges are added up
+//  6. reduce      per window sum_b b * B_b: segments of L buckets by running sums
+//                 in-thread, then sum_g g * Y_g split by the bits of g into
+//                 independent sums, recombined by Horner
+//  7. combine     sum_j 2^(c j) S_j by Horner over windows, one inversion,
+//                 affine standard form
+//
+// Everything runs on the caller's stream, one launch per stage over all windows.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -34,70 +38,73 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
 constexpr int kRadix = 256;
+constexpr int kXyzzVec = 12;                // XYZZ in memory: 4 x 12 packed words = 12 uint4
+constexpr size_t kXyzzBytes = kXyzzVec * 16;
 
 // ---------------------------------------------------------------- memory I/O
 
-// Affine point in memory: 24 packed u32 (x then y), canonical Montgomery form.
 __device__ __forceinline__ void load_affine(affine& Q, const uint4* __restrict__ pts, uint32_t idx) {
     const uint4* p = pts + 6 * (size_t)idx;
     uint4 a = __ldg(p + 0), b = __ldg(p + 1), c = __ldg(p + 2);
     uint4 d = __ldg(p + 3), e = __ldg(p + 4), f = __ldg(p + 5);
-    const uint32_t wx[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-    const uint32_t wy[12] = {d.x, d.y, d.z, d.w, e.x, e.y, e.z, e.w, f.x, f.y, f.z, f.w};
-    fq::unpack(Q.x, wx);
-    fq::unpack(Q.y, wy);
+    Q.x.v[0] = a.x; Q.x.v[1] = a.y; Q.x.v[2] = a.z; Q.x.v[3] = a.w;
+    Q.x.v[4] = b.x; Q.x.v[5] = b.y; Q.x.v[6] = b.z; Q.x.v[7] = b.w;
+    Q.x.v[8] = c.x; Q.x.v[9] = c.y; Q.x.v[10] = c.z; Q.x.v[11] = c.w;
+    Q.y.v[0] = d.x; Q.y.v[1] = d.y; Q.y.v[2] = d.z; Q.y.v[3] = d.w;
+    Q.y.v[4] = e.x; Q.y.v[5] = e.y; Q.y.v[6] = e.z; Q.y.v[7] = e.w;
+    Q.y.v[8] = f.x; Q.y.v[9] = f.y; Q.y.v[10] = f.z; Q.y.v[11] = f.w;
 }
 
-// XYZZ point in memory: the 4 x 15 digit words as they are in registers (15 uint4).
-constexpr int kXyzzVec = 15;
-constexpr size_t kXyzzBytes = kXyzzVec * 16;
+__device__ __forceinline__ void load_fe(fe& a, const uint4* p) {
+    uint4 u0 = p[0], u1 = p[1], u2 = p[2];
+    a.v[0] = u0.x; a.v[1] = u0.y; a.v[2] = u0.z; a.v[3] = u0.w;
+    a.v[4] = u1.x; a.v[5] = u1.y; a.v[6] = u1.z; a.v[7] = u1.w;
+    a.v[8] = u2.x; a.v[9] = u2.y; a.v[10] = u2.z; a.v[11] = u2.w;
+}
 
+__device__ __forceinline__ void store_fe(uint4* p, const fe& a) {
+    p[0] = make_uint4(a.v[0], a.v[1], a.v[2], a.v[3]);
+    p[1] = make_uint4(a.v[4], a.v[5], a.v[6], a.v[7]);
+    p[2] = make_uint4(a.v[8], a.v[9], a.v[10], a.v[11]);
+}
+
+// XYZZ point in memory: 12 uint4 (X, Y, ZZ, ZZZ), each coordinate in [0, 2p).
 __device__ __forceinline__ void load_xyzz(xyzz& P, const uint4* p) {
-    uint32_t w[60];
-#pragma unroll
-    for (int k = 0; k < kXyzzVec; ++k) {
-        uint4 u = p[k];
-        w[4 * k] = u.x;
-        w[4 * k + 1] = u.y;
-        w[4 * k + 2] = u.z;
-        w[4 * k + 3] = u.w;
-    }
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-        P.X.d[k] = w[k];
-        P.Y.d[k] = w[15 + k];
-        P.ZZ.d[k] = w[30 + k];
-        P.ZZZ.d[k] = w[45 + k];
-    }
+    load_fe(P.X, p);
+    load_fe(P.Y, p + 3);
+    load_fe(P.ZZ, p + 6);
+    load_fe(P.ZZZ, p + 9);
 }
 
 __device__ __forceinline__ void store_xyzz(uint4* p, const xyzz& P) {
-    uint32_t w[60];
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-        w[k] = P.X.d[k];
-        w[15 + k] = P.Y.d[k];
-        w[30 + k] = P.ZZ.d[k];
-        w[45 + k] = P.ZZZ.d[k];
-    }
-#pragma unroll
-    for (int k = 0; k < kXyzzVec; ++k) p[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+    store_fe(p, P.X);
+    store_fe(p + 3, P.Y);
+    store_fe(p + 6, P.ZZ);
+    store_fe(p + 9, P.ZZZ);
 }
+
+// Second operand of ec::add_q() read from memory coordinate by coordinate.
+struct MemQ {
+    const uint4* p;
+    __device__ __forceinline__ void X(fe& r) const { load_fe(r, p); }
+    __device__ __forceinline__ void Y(fe& r) const { load_fe(r, p + 3); }
+    __device__ __forceinline__ void ZZ(fe& r) const { load_fe(r, p + 6); }
+    __device__ __forceinline__ void ZZZ(fe& r) const { load_fe(r, p + 9); }
+    __device__ __forceinline__ void all(xyzz& r) const { load_xyzz(r, p); }
+};
 
 // ---------------------------------------------------------------- stage 1
 
 __global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(in + 6 * i);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(out + 6 * i);
     fe x, y;
-    fq::load_packed(x, src);
-    fq::load_packed(y, src + 12);
-    ec::to_mont(x, x);
-    ec::to_mont(y, y);
-    fq::store_canonical(dst, x);
-    fq::store_canonical(dst + 12, y);
+    load_fe(x, in + 6 * i);
+    load_fe(y, in + 6 * i + 3);
+    fq::to_mont(x, x);
+    fq::to_mont(y, y);
+    store_fe(out + 6 * i, x);
+    store_fe(out + 6 * i + 3, y);
 }
 
 // ---------------------------------------------------------------- stage 2
@@ -283,68 +290,66 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
 // ---------------------------------------------------------------- stages 4-5
 
 struct AccArgs {
-    const uint32_t* keys;
-    const uint32_t* vals;
+    const uint32_t* keys;  // [W][n]
+    const uint32_t* vals;  // [W][n]
     const uint4* pts;
-    uint4* buckets;      // [W][Bp] XYZZ
-    uint4* head;         // [nchunks] XYZZ
-    uint4* tail;         // [nchunks] XYZZ
-    uint32_t* headflag;  // 0 none, 1 run ends here, 2 run continues past this chunk
-    uint32_t* tailkey;   // composite key of the run leaving this chunk, or kNone
-    size_t N, n, nchunks;
-    uint32_t stride;     // B + 1 (composite key = window * stride + key)
+    uint4* buckets;        // [W][Bp] XYZZ
+    uint4* head;           // [W][cpw] XYZZ
+    uint4* tail;           // [W][cpw] XYZZ
+    uint32_t* headflag;    // 0 none, 1 run ends here, 2 run continues past this chunk
+    uint32_t* tailkey;     // key of the run leaving this chunk, or kNone
+    size_t n;              // items per window
+    uint32_t cpw;          // chunks per window
     uint32_t Bp;
     int K;
+    int w0, nwin;          // window range of this launch
 };
 
-__device__ __forceinline__ uint32_t composite(const AccArgs& a, size_t g) {
-    return (uint32_t)(g / a.n) * a.stride + a.keys[g];
-}
-
-__device__ __forceinline__ void bucket_store(const AccArgs& a, uint32_t ck, const xyzz& P) {
-    uint32_t w = ck / a.stride, key = ck % a.stride;
-    store_xyzz(a.buckets + ((size_t)w * a.Bp + (key - 1)) * kXyzzVec, P);
-}
-
+// Mixed additions of one chunk. Flushes each run to its
+// bucket, or to the chunk's head / tail partial when it crosses a chunk edge.
 __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
-    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (t >= a.nchunks) return;
-    size_t start = t * (size_t)a.K;
-    size_t end = start + a.K < a.N ? start + a.K : a.N;
-    uint32_t prev = start > 0 ? composite(a, start - 1) : kNone;
-    uint32_t next = end < a.N ? composite(a, end) : kNone;
-    a.tailkey[t] = kNone;
-    a.headflag[t] = 0;
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (uint32_t)a.nwin * a.cpw) return;
+    const int w = a.w0 + (int)(id / a.cpw);
+    const uint32_t t = id % a.cpw;
+    const size_t ci = (size_t)w * a.cpw + t;
+    const uint32_t* keys = a.keys + (size_t)w * a.n;
+    const uint32_t* vals = a.vals + (size_t)w * a.n;
+    const size_t start = (size_t)t * a.K;
+    const size_t end = start + a.K < a.n ? start + a.K : a.n;
+    const uint32_t prev = start > 0 ? keys[start - 1] : kNone;
+    const uint32_t next = end < a.n ? keys[end] : kNone;
+    a.tailkey[ci] = kNone;
+    a.headflag[ci] = 0;
     xyzz acc;
     ec::set_inf(acc);
     bool inf = true;
-    uint32_t cur = composite(a, start);
+    uint32_t cur = keys[start];
     bool first = true;
     for (size_t g = start; g <= end; ++g) {
-        uint32_t ck = g < end ? composite(a, g) : kNone;
-        if (ck != cur) {
-            // flush the run `cur`
-            if (cur % a.stride != 0) {
-                bool sb = first && prev == cur;
-                bool ea = (g == end) && next == cur;
+        const uint32_t key = g < end ? keys[g] : kNone;
+        if (key != cur) {
+            if (cur != 0) {  // key 0 = zero digit, contributes nothing
+                const bool sb = first && prev == cur;
+                const bool ea = (g == end) && next == cur;
                 if (!sb && !ea) {
-                    bucket_store(a, cur, acc);
+                    store_xyzz(a.buckets + ((size_t)w * a.Bp + (cur - 1)) * kXyzzVec, acc);
                 } else if (sb) {
-                    store_xyzz(a.head + t * kXyzzVec, acc);
-                    a.headflag[t] = ea ? 2u : 1u;
+                    store_xyzz(a.head + ci * kXyzzVec, acc);
+                    a.headflag[ci] = ea ? 2u : 1u;
                 } else {
-                    store_xyzz(a.tail + t * kXyzzVec, acc);
-                    a.tailkey[t] = cur;
+                    store_xyzz(a.tail + ci * kXyzzVec, acc);
+                    a.tailkey[ci] = cur;
                 }
             }
             if (g == end) break;
             ec::set_inf(acc);
             inf = true;
-            cur = ck;
+            cur = key;
             first = false;
         }
-        if (ck % a.stride != 0) {
-            uint32_t v = a.vals[g];
+        if (key != 0) {
+            const uint32_t v = vals[g];
             if ((v & 0x7fffffffu) >= a.n) continue;  // cannot happen for sorted digit output
             affine Q;
             load_affine(Q, a.pts, v & 0x7fffffffu);
@@ -354,63 +359,113 @@ __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
     }
 }
 
-__global__ void k_merge(AccArgs a) {
-    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (t >= a.nchunks) return;
-    uint32_t ck = a.tailkey[t];
-    if (ck == kNone) return;
-    xyzz acc, h;
-    load_xyzz(acc, a.tail + t * kXyzzVec);
-    for (size_t u = t + 1; u < a.nchunks; ++u) {
-        load_xyzz(h, a.head + u * kXyzzVec);
-        ec::add(acc, h);
-        if (a.headflag[u] != 2u) break;
+// Partial sums of runs that cross chunk edges are combined in log depth, so a
+// bucket holding a large share of the window (all-equal scalars, a nearly empty
+// top window) costs O(log) serial additions, not O(chunks):
+//  * k_merge_scan: start[u] = the last chunk t < u whose run leaves it (a tail),
+//    a prefix maximum per window (one block per window);
+//  * k_merge_round(d): for heads at offset j = u - start[u] - 1 with j % 2d == 0,
+//    head[u] += head[u + d] when u + d continues the same run; ceil(log2 cpw) rounds
+//    leave each run's sum of heads at its first head;
+//  * k_merge_final: bucket = tail[start] + that sum.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_merge_scan(AccArgs a, int32_t* __restrict__ start) {
+    __shared__ int32_t part[kScanThreads];
+    const int w = a.w0 + blockIdx.x;
+    const size_t base = (size_t)w * a.cpw;
+    const uint32_t per = (a.cpw + kScanThreads - 1) / kScanThreads;
+    const uint32_t lo = threadIdx.x * per;
+    int32_t m = -1;
+    for (uint32_t u = lo; u < lo + per && u < a.cpw; ++u)
+        if (a.tailkey[base + u] != kNone) m = (int32_t)u;
+    part[threadIdx.x] = m;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {  // inclusive max-scan of the partials
+        int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : -1;
+        __syncthreads();
+        if (v > part[threadIdx.x]) part[threadIdx.x] = v;
+        __syncthreads();
     }
-    bucket_store(a, ck, acc);
+    int32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : -1;  // exclusive prefix
+    for (uint32_t u = lo; u < lo + per && u < a.cpw; ++u) {
+        start[base + u] = run;   // last tail strictly before u
+        if (a.tailkey[base + u] != kNone) run = (int32_t)u;
+    }
+}
+
+__global__ void k_merge_round(AccArgs a, const int32_t* __restrict__ start, uint32_t d) {
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (uint32_t)a.nwin * a.cpw) return;
+    const int w = a.w0 + (int)(id / a.cpw);
+    const uint32_t u = id % a.cpw;
+    const size_t base = (size_t)w * a.cpw;
+    if (a.headflag[base + u] == 0) return;
+    const int32_t t0 = start[base + u];
+    if (t0 < 0) return;
+    const uint32_t j = u - (uint32_t)t0 - 1;
+    if (j % (2 * d) != 0) return;
+    const uint32_t v = u + d;
+    if (v >= a.cpw || a.headflag[base + v] == 0 || start[base + v] != t0) return;
+    xyzz acc;
+    load_xyzz(acc, a.head + (base + u) * kXyzzVec);
+    ec::add_q(acc, MemQ{a.head + (base + v) * kXyzzVec});
+    store_xyzz(a.head + (base + u) * kXyzzVec, acc);
+}
+
+__global__ void k_merge_final(AccArgs a) {
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (uint32_t)a.nwin * a.cpw) return;
+    const int w = a.w0 + (int)(id / a.cpw);
+    const uint32_t t = id % a.cpw;
+    const size_t ci = (size_t)w * a.cpw + t;
+    const uint32_t key = a.tailkey[ci];
+    if (key == kNone) return;
+    xyzz acc;
+    load_xyzz(acc, a.tail + ci * kXyzzVec);
+    if (t + 1 < a.cpw && a.headflag[ci + 1] != 0) ec::add_q(acc, MemQ{a.head + (ci + 1) * kXyzzVec});
+    store_xyzz(a.buckets + ((size_t)w * a.Bp + (key - 1)) * kXyzzVec, acc);
 }
 
 // ---------------------------------------------------------------- stage 6
 
-// Thread (w, g): Y = sum_{i=1..L} B[gL+i], V = sum_{i=1..L} i * B[gL+i] (bucket b at index b-1).
-__global__ void k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, size_t W,
+// Thread (wi, g): Y = sum_{i=1..L} B[gL+i], V = sum_{i=1..L} i * B[gL+i] (bucket b at index b-1).
+__global__ void k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, int w0, int nwin,
                                   uint32_t G, uint4* __restrict__ Y, uint4* __restrict__ V) {
-    size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (id >= W * G) return;
-    size_t w = id / G, g = id % G;
-    const uint4* seg = buckets + ((size_t)w * Bp + (size_t)g * L) * kXyzzVec;
-    xyzz T, S, X;
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)nwin * G) return;
+    const size_t wi = id / G, g = id % G;
+    const uint4* seg = buckets + ((size_t)(w0 + wi) * Bp + g * L) * kXyzzVec;
+    xyzz T, S;
     ec::set_inf(T);
     ec::set_inf(S);
     for (int i = (int)L; i >= 1; --i) {
-        load_xyzz(X, seg + (size_t)(i - 1) * kXyzzVec);
-        ec::add(T, X);
-        ec::add(S, T);
+        ec::add_q(T, MemQ{seg + (size_t)(i - 1) * kXyzzVec});   // T += B
+        ec::add(S, T);                                          // S += T
     }
     store_xyzz(Y + id * kXyzzVec, T);
     store_xyzz(V + id * kXyzzVec, S);
 }
 
-// Thread (w, k, q): partial of Z_k = sum_{g in chunk q, bit k of g set} Y_g, or for
+// Thread (wi, k, q): partial of Z_k = sum_{g in chunk q, bit k of g set} Y_g, or for
 // k == logG the partial of sum_{g in chunk q} V_g.
-__global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__ V, size_t W, uint32_t G,
+__global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__ V, int nwin, uint32_t G,
                           int logG, uint32_t Q, uint4* __restrict__ P) {
-    size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    size_t per_w = (size_t)(logG + 1) * Q;
-    if (id >= W * per_w) return;
-    size_t w = id / per_w;
-    int k = (int)((id % per_w) / Q);
-    uint32_t q = (uint32_t)(id % Q);
-    uint32_t span = G / Q, g0 = q * span;
-    xyzz acc, X;
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t per_w = (size_t)(logG + 1) * Q;
+    if (id >= (size_t)nwin * per_w) return;
+    const size_t wi = id / per_w;
+    const int k = (int)((id % per_w) / Q);
+    const uint32_t q = (uint32_t)(id % Q);
+    const uint32_t span = G / Q, g0 = q * span;
+    xyzz acc;
     ec::set_inf(acc);
     for (uint32_t g = g0; g < g0 + span; ++g) {
         if (k == logG) {
-            load_xyzz(X, V + ((size_t)w * G + g) * kXyzzVec);
-        } else {
-            if (!((g >> k) & 1u)) continue;
-            load_xyzz(X, Y + ((size_t)w * G + g) * kXyzzVec);
+            ec::add_q(acc, MemQ{V + (wi * G + g) * kXyzzVec});
+        } else if ((g >> k) & 1u) {
+            ec::add_q(acc, MemQ{Y + (wi * G + g) * kXyzzVec});
         }
-        ec::add(acc, X);
     }
     store_xyzz(P + id * kXyzzVec, acc);
 }
@@ -418,57 +473,61 @@ __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__
 // out[s][i] = sum_{e < F} in[s][i F + e], segments of m points.
 __global__ void k_sum_segments(const uint4* __restrict__ in, size_t nseg, uint32_t m, uint32_t F,
                                uint4* __restrict__ out) {
-    size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    uint32_t mo = m / F;
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const uint32_t mo = m / F;
     if (id >= nseg * mo) return;
-    size_t s = id / mo, i = id % mo;
-    xyzz acc, X;
+    const size_t s = id / mo, i = id % mo;
+    xyzz acc;
     ec::set_inf(acc);
-    for (uint32_t e = 0; e < F; ++e) {
-        load_xyzz(X, in + (s * m + i * F + e) * kXyzzVec);
-        ec::add(acc, X);
-    }
+    for (uint32_t e = 0; e < F; ++e) ec::add_q(acc, MemQ{in + (s * m + i * F + e) * kXyzzVec});
     store_xyzz(out + id * kXyzzVec, acc);
 }
 
-// Thread w: S_w = Z_V + L * sum_k 2^k Z_k (Horner over k), Z laid out [W][logG + 1].
-__global__ void k_window_horner(const uint4* __restrict__ Z, size_t W, int logG, int log2L,
-                                uint4* __restrict__ S) {
-    size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (w >= W) return;
-    const uint4* z = Z + w * (size_t)(logG + 1) * kXyzzVec;
-    xyzz acc, X;
+// Thread wi: S_w = Z_V + L * sum_k 2^k Z_k (Horner over k), Z laid out [nwin][logG + 1].
+__global__ void k_window_horner(const uint4* __restrict__ Z, int nwin, int logG, int log2L, uint4* __restrict__ S) {
+    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (wi >= nwin) return;
+    const uint4* z = Z + (size_t)wi * (logG + 1) * kXyzzVec;
+    xyzz acc;
     ec::set_inf(acc);
     for (int k = logG - 1; k >= 0; --k) {
         ec::dbl(acc);
-        load_xyzz(X, z + (size_t)k * kXyzzVec);
-        ec::add(acc, X);
+        ec::add_q(acc, MemQ{z + (size_t)k * kXyzzVec});
     }
     for (int l = 0; l < log2L; ++l) ec::dbl(acc);
-    load_xyzz(X, z + (size_t)logG * kXyzzVec);
-    ec::add(acc, X);
-    store_xyzz(S + w * kXyzzVec, acc);
+    ec::add_q(acc, MemQ{z + (size_t)logG * kXyzzVec});
+    store_xyzz(S + (size_t)wi * kXyzzVec, acc);
 }
 
 // ---------------------------------------------------------------- stage 7
 
-__global__ void k_combine(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
+// One thread: acc = 2^(c) acc + S_w for w = w_hi - 1 down to w_lo (acc starts at
+// O for the top window of the MSM); when w_lo = 0 it normalises acc and writes
+// the affine result in standard form.
+__global__ void k_chain(const uint4* __restrict__ S, int w_hi, int w_lo, int W, int c, uint4* __restrict__ accp,
+                        uint32_t* __restrict__ out) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    xyzz acc, X;
-    ec::set_inf(acc);
-    for (int j = W - 1; j >= 0; --j) {
+    xyzz acc;
+    if (w_hi == W)
+        ec::set_inf(acc);
+    else
+        load_xyzz(acc, accp);
+    for (int w = w_hi - 1; w >= w_lo; --w) {
         for (int k = 0; k < c; ++k) ec::dbl(acc);
-        load_xyzz(X, S + (size_t)j * kXyzzVec);
-        ec::add(acc, X);
+        ec::add_q(acc, MemQ{S + (size_t)w * kXyzzVec});
+    }
+    if (w_lo > 0) {
+        store_xyzz(accp, acc);
+        return;
     }
     affine A;
     ec::to_affine(A, acc);
     if (!ec::is_inf(A)) {
-        ec::from_mont(A.x, A.x);
-        ec::from_mont(A.y, A.y);
+        fq::from_mont(A.x, A.x);
+        fq::from_mont(A.y, A.y);
     }
-    fq::store_canonical(out, A.x);
-    fq::store_canonical(out + 12, A.y);
+    fq::store(out, A.x);
+    fq::store(out + 12, A.y);
 }
 
 // ---------------------------------------------------------------- planning
@@ -476,16 +535,18 @@ __global__ void k_combine(const uint4* __restrict__ S, int W, int c, uint32_t* _
 struct Plan {
     size_t n;
     int c, sgn, bits, W;
-    uint32_t B, Bp, stride;
+    uint32_t B, Bp;
     int passes;
     size_t tiles;
     int K;
-    size_t N, nchunks;
+    uint32_t cpw;   // chunks per window
+    int gw;         // windows per group
+    int ngroups;
     uint32_t L, G, Q;
     int logG, log2L;
     size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_hist, off_dtot;
     size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
-    size_t off_S, total;
+    size_t off_S, off_acc, off_start, total;
 };
 
 int ilog2(uint64_t v) {
@@ -515,20 +576,21 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->W = p->sgn ? (p->bits + 1 + p->c - 1) / p->c : (p->bits + p->c - 1) / p->c;
     p->B = p->sgn ? (1u << (p->c - 1)) : ((1u << p->c) - 1u);
     p->Bp = p->sgn ? p->B : (1u << p->c);
-    p->stride = p->B + 1;
     p->passes = (p->c + 7) / 8;
     p->tiles = (n + kSortTile - 1) / kSortTile;
-    p->N = (size_t)p->W * n;
-    size_t target_threads = 152 * 512;
-    size_t K = p->N / target_threads;
+    // about 150 resident threads x 512 per SM worth of chunks over all windows
+    size_t K = ((size_t)p->W * n) / (152 * 512);
     if (K < 2) K = 2;
     if (K > 64) K = 64;
     p->K = (int)K;
-    p->nchunks = (p->N + K - 1) / K;
-    // bucket reduction geometry
-    uint64_t total_buckets = (uint64_t)p->W * p->Bp;
+    p->cpw = (uint32_t)((n + K - 1) / K);
+    if (p->cpw == 0) p->cpw = 1;
+    p->gw = p->W;
+    p->ngroups = 1;
+    // bucket reduction geometry: enough level-1 threads over all windows
+    uint64_t group_buckets = (uint64_t)p->W * p->Bp;
     uint32_t L = 2;
-    while (L < p->Bp && total_buckets / (2 * L) >= 65536) L <<= 1;
+    while (L < p->Bp && group_buckets / (2 * L) >= 65536) L <<= 1;
     if (L > p->Bp) L = p->Bp;
     p->L = L;
     p->G = p->Bp / L;
@@ -542,26 +604,29 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
         off = msm377::align_up(off + bytes, 256);
         return o2;
     };
-    const size_t XY = kXyzzBytes;  // bytes per XYZZ point in the workspace
+    const size_t XY = kXyzzBytes;
+    const size_t chunks = (size_t)p->W * p->cpw;
     p->off_status = take(256);
     p->off_points = take(o->flags & MSM377_POINTS_PREPARED ? 0 : n * 96);
-    p->off_keys0 = take(p->N * 4);
-    p->off_vals0 = take(p->N * 4);
-    p->off_keys1 = take(p->N * 4);
-    p->off_vals1 = take(p->N * 4);
+    p->off_keys0 = take((size_t)p->W * n * 4);
+    p->off_vals0 = take((size_t)p->W * n * 4);
+    p->off_keys1 = take((size_t)p->W * n * 4);
+    p->off_vals1 = take((size_t)p->W * n * 4);
     p->off_hist = take((size_t)p->W * kRadix * (p->tiles ? p->tiles : 1) * 4);
     p->off_dtot = take((size_t)p->W * kRadix * 4);
     p->off_buckets = take((size_t)p->W * p->Bp * XY);
-    p->off_head = take(p->nchunks * XY);
-    p->off_tail = take(p->nchunks * XY);
-    p->off_headflag = take(p->nchunks * 4);
-    p->off_tailkey = take(p->nchunks * 4);
-    p->off_Y = take((size_t)p->W * p->G * XY);
-    p->off_V = take((size_t)p->W * p->G * XY);
-    size_t zs = (size_t)p->W * (p->logG + 1) * p->Q;
+    p->off_head = take(chunks * XY);
+    p->off_tail = take(chunks * XY);
+    p->off_headflag = take(chunks * 4);
+    p->off_tailkey = take(chunks * 4);
+    p->off_start = take(chunks * 4);
+    p->off_Y = take((size_t)p->gw * p->G * XY);
+    p->off_V = take((size_t)p->gw * p->G * XY);
+    const size_t zs = (size_t)p->gw * (p->logG + 1) * p->Q;
     p->off_P0 = take(zs * XY);
     p->off_P1 = take(zs * XY);
     p->off_S = take((size_t)p->W * XY);
+    p->off_acc = take(XY);
     p->total = off;
     return true;
 }
@@ -619,7 +684,7 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     }
     if (!points || !scalars || !aligned(points, 16) || !aligned(scalars, 16))
         return set_error(MSM377_EINVAL, "msm_g1: points/scalars NULL or not 16-byte aligned");
-
+    // 1-2. prepare, digits
     const uint4* pts = reinterpret_cast<const uint4*>(points);
     if (!(opts->flags & MSM377_POINTS_PREPARED)) {
         uint4* prep = at<uint4>(workspace, p.off_points);
@@ -636,6 +701,7 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     if (r) return r;
     if (prof) profile_mark(s);
 
+    // 3. sort
     uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
     uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
     int cur = 0;
@@ -652,10 +718,10 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     }
     r = check_launch("msm_g1 sort");
     if (r) return r;
-    if (prof) profile_mark(s);
-
     uint4* buckets = at<uint4>(workspace, p.off_buckets);
     MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * kXyzzBytes, s));
+    if (prof) profile_mark(s);
+
     AccArgs a;
     a.keys = keys[cur];
     a.vals = vals[cur];
@@ -665,35 +731,49 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     a.tail = at<uint4>(workspace, p.off_tail);
     a.headflag = at<uint32_t>(workspace, p.off_headflag);
     a.tailkey = at<uint32_t>(workspace, p.off_tailkey);
-    a.N = p.N;
     a.n = n;
-    a.nchunks = p.nchunks;
-    a.stride = p.stride;
+    a.cpw = p.cpw;
     a.Bp = p.Bp;
     a.K = p.K;
-    k_accumulate<<<grid_for(p.nchunks, 128), 128, 0, s>>>(a);
-    if (prof) profile_mark(s);
-    k_merge<<<grid_for(p.nchunks, 128), 128, 0, s>>>(a);
-    note_launches(2);
+    uint4* Y = at<uint4>(workspace, p.off_Y);
+    uint4* V = at<uint4>(workspace, p.off_V);
+    uint4* P0 = at<uint4>(workspace, p.off_P0);
+    uint4* P1 = at<uint4>(workspace, p.off_P1);
+    uint4* S = at<uint4>(workspace, p.off_S);
+    uint4* accp = at<uint4>(workspace, p.off_acc);
+
+    // 4. bucket accumulation, all windows
+    a.w0 = 0;
+    a.nwin = p.W;
+    const size_t nchunks = (size_t)p.W * p.cpw;
+    k_accumulate<<<grid_for(nchunks, 128), 128, 0, s>>>(a);
+    note_launches(1);
     r = check_launch("msm_g1 accumulate");
     if (r) return r;
     if (prof) profile_mark(s);
 
-    uint4* Y = at<uint4>(workspace, p.off_Y);
-    uint4* V = at<uint4>(workspace, p.off_V);
-    size_t WG = (size_t)p.W * p.G;
-    k_reduce_segments<<<grid_for(WG, 128), 128, 0, s>>>(buckets, p.Bp, p.L, p.W, p.G, Y, V);
+    // 5. merge partial sums of runs crossing chunk edges (log depth)
+    int32_t* start = at<int32_t>(workspace, p.off_start);
+    k_merge_scan<<<p.W, kScanThreads, 0, s>>>(a, start);
     note_launches(1);
-    uint4* P0 = at<uint4>(workspace, p.off_P0);
-    uint4* P1 = at<uint4>(workspace, p.off_P1);
-    size_t nseg = (size_t)p.W * (p.logG + 1);
+    for (uint32_t d = 1; d < p.cpw; d <<= 1) {
+        k_merge_round<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d);
+        note_launches(1);
+    }
+    k_merge_final<<<grid_for(nchunks, 128), 128, 0, s>>>(a);
+    note_launches(1);
+
+    // 6. bucket reduction, all windows
+    const size_t WG = (size_t)p.W * p.G;
+    k_reduce_segments<<<grid_for(WG, 128), 128, 0, s>>>(buckets, p.Bp, p.L, 0, p.W, p.G, Y, V);
+    const size_t nseg = (size_t)p.W * (p.logG + 1);
     k_bitsums<<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, p.W, p.G, p.logG, p.Q, P0);
-    note_launches(1);
+    note_launches(2);
     uint32_t m = p.Q;
     uint4* zin = P0;
     uint4* zout = P1;
     while (m > 1) {
-        uint32_t F = m >= 8 ? 8 : m;
+        const uint32_t F = m >= 8 ? 8 : m;
         k_sum_segments<<<grid_for(nseg * (m / F), 128), 128, 0, s>>>(zin, nseg, m, F, zout);
         note_launches(1);
         m /= F;
@@ -701,14 +781,14 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
         zin = zout;
         zout = tmp;
     }
-    uint4* S = at<uint4>(workspace, p.off_S);
     k_window_horner<<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
     note_launches(1);
-    if (prof) profile_mark(s);
-    k_combine<<<1, 32, 0, s>>>(S, p.W, p.c, out);
+
+    // 7. window combination and normalisation
+    k_chain<<<1, 32, 0, s>>>(S, p.W, 0, p.W, p.c, accp, out);
     note_launches(1);
     if (prof) profile_mark(s);
-    return check_launch("msm_g1 reduce");
+    return check_launch("msm_g1 tail");
 }
 
 extern "C" int msm_g1_status(const void* workspace, const msm_opts* opts) {

@@ -60,20 +60,19 @@ def test_invalid_arguments_fail_before_touching_the_gpu():
 
 
 def test_header_constants_match_the_oracle():
-    """The CUDA field header's radix-2^26 digits of p and its Montgomery constants
-    (R = 2^390) agree with the oracle's derivation of p from the BLS12 seed."""
+    """The CUDA field header's modulus and Montgomery constants (R = 2^384) agree
+    with the oracle's derivation of p from the BLS12 seed."""
     from oracle import fq
     src = open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", "fq.cuh")).read()
 
-    def digits(name):
-        m = re.search(r"constexpr uint32_t " + name + r"\(int i\) \{(.*?)\n\}", src, flags=re.S)
-        body = m.group(1)
-        cases = dict((int(k), int(v, 16)) for k, v in re.findall(r"case (\d+): return (0x[0-9a-f]+)u;", body))
-        cases[14] = int(re.search(r"default: return (0x[0-9a-f]+)u;", body).group(1), 16)
-        return sum(cases[k] << (26 * k) for k in range(15))
+    def limbs(name):
+        m = re.search(name + r"\[N\] = \{([^}]*)\}", src)
+        return sum(int(w.strip().rstrip("u"), 16) << (32 * k) for k, w in enumerate(m.group(1).split(",")))
 
-    R = 1 << 390
-    assert digits("p26") == fq.P
-    assert digits("one26") == R % fq.P
-    assert digits("r2_26") == R * R % fq.P
-    assert fq.P % (1 << 26) == 1   # so the Montgomery digit is m = -c mod 2^26
+    R = 1 << 384
+    assert limbs("kP") == fq.P
+    assert limbs("k2P") == 2 * fq.P
+    assert limbs("kOne") == R % fq.P
+    assert limbs("kR2") == R * R % fq.P
+    assert limbs("kR3") == R ** 3 % fq.P
+    assert fq.P % (1 << 32) == 1   # so the Montgomery digit is m = -t0 mod 2^32

@@ -19,7 +19,7 @@ EDGE = [0, 1, 2, 3, fq.P - 1, fq.P - 2, (fq.P - 1) // 2, (fq.P + 1) // 2,
 
 
 def _mont(v):
-    return v * (1 << 390) % fq.P
+    return v * (1 << 384) % fq.P
 
 
 def test_fq_mul_standard_random_and_ragged():
