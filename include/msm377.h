@@ -137,6 +137,34 @@ int msm_points_prepare(const uint32_t *points_std, size_t n, uint32_t *out, void
 int msm_g1(const uint32_t *points, const uint32_t *scalars, size_t n, uint32_t *out,
            void *workspace, size_t workspace_bytes, const msm_opts *opts);
 
+/* ------------------------------------------------------------------------
+ * Batched MSM: many independent MSMs of uneven size in one call. The per-job
+ * preparation, digits and sort run on library-owned helper streams; the bucket
+ * accumulation of all jobs is one persistent kernel that drains a queue of
+ * (job, window, chunk) items; the jobs' reductions and window combinations run
+ * on the helper streams again, so the serial tails overlap each other. Every
+ * step forks from and joins back into opts->stream through events, so the call
+ * can be captured into a CUDA graph once the first call on the device has
+ * created the helper streams (make one uncaptured call first).
+ */
+typedef struct msm_job {
+    const uint32_t *points;  /* device, 24 u32 per point (standard, or prepared with the flag) */
+    const uint32_t *scalars; /* device, 8 u32 per scalar */
+    size_t n;
+    uint32_t *out;           /* device, 24 u32: affine result in standard form */
+    int32_t c;               /* window bits for this job, 0 = opts->c or the size default */
+    int32_t reserved;
+} msm_job;
+
+/* Workspace for a batch (0 on bad options or more than 128 jobs). */
+size_t msm_g1_batched_workspace_bytes(const msm_job *jobs, size_t njobs, const msm_opts *opts);
+
+/* Runs njobs <= 128 MSMs; opts applies to all jobs (except c, see msm_job).
+ * Asynchronous on opts->stream. The per-job device status words are not
+ * reported; leave scalar_bits at 0 (256) to rule the range error out. */
+int msm_g1_batched(const msm_job *jobs, size_t njobs, void *workspace, size_t workspace_bytes,
+                   const msm_opts *opts);
+
 /* Synchronous: waits for opts->stream and returns the device status word of the
  * last msm_g1 / msm_g1_batched that used this workspace. */
 int msm_g1_status(const void *workspace, const msm_opts *opts);
@@ -180,9 +208,9 @@ int msm_g1_noalloc(const uint32_t *points, const uint32_t *scalars, size_t n, ui
 
 /* Stage timings of the most recent msm_g1 call made with MSM377_PROFILE, in
  * milliseconds, from CUDA events recorded on the caller's stream:
- * [0] prepare + digits, [1] sort, [2] bucket accumulation, [3] the tail:
- * partial merges, bucket reduction, window combination and normalisation.
- * Synchronous (waits for the last event). Writes min(cap, 4) values and returns
+ * [0] head: preparation, digits, sort, bucket reset; [1] bucket accumulation;
+ * [2] tail: partial merges, bucket reduction, window combination and
+ * normalisation. Synchronous (waits for the last event). Writes min(cap, 3) values and returns
  * the number of stages, or a negative status. Not thread-safe: one profiled
  * call at a time per process. */
 int msm377_profile_last(float *ms, int cap);

@@ -16,13 +16,13 @@ import ctypes
 import numpy as np
 import torch
 
-from ._lib import MsmError, MsmOpts, check, last_error, lib
+from ._lib import MsmError, MsmJob, MsmOpts, check, last_error, lib
 
 FORM_STANDARD = 0
 FORM_MONTGOMERY = 1
 POINTS_PREPARED = 1
 PROFILE = 2
-MSM_STAGES = ("prepare+digits", "sort", "accumulate", "tail")
+MSM_STAGES = ("head", "accumulate", "tail")
 
 __all__ = [
     "MsmError", "MsmOpts", "FORM_STANDARD", "FORM_MONTGOMERY", "POINTS_PREPARED",
@@ -30,6 +30,7 @@ __all__ = [
     "padd_batch", "xyzz_to_affine_batch", "g1_generator_mul", "msm_points_prepare",
     "msm_g1", "msm_g1_workspace", "msm_g1_host", "msm_g1_status", "msm_g1_default_c",
     "imad_probe", "lib", "last_error", "profile_last", "launch_count", "MSM_STAGES", "PROFILE",
+    "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace",
 ]
 
 
@@ -149,6 +150,51 @@ def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None
     check(lib().msm_g1(_p(points), _p(scalars), n, _p(out), _p(workspace), workspace.numel(),
                        ctypes.byref(o)))
     return out
+
+
+def _jobs_array(points_list, scalars_list, outs, cs):
+    arr = (MsmJob * len(points_list))()
+    for i, (pt, sc, o) in enumerate(zip(points_list, scalars_list, outs)):
+        arr[i].points = pt.data_ptr() if pt.shape[0] else 0
+        arr[i].scalars = sc.data_ptr() if sc.shape[0] else 0
+        arr[i].n = pt.shape[0]
+        arr[i].out = o.data_ptr()
+        arr[i].c = int(cs[i]) if cs is not None else 0
+    return arr
+
+
+def msm_g1_batched_workspace(points_list, c_list=None, signed=True, scalar_bits=0, prepared=False,
+                             device="cuda") -> torch.Tensor:
+    arr = (MsmJob * len(points_list))()
+    for i, pt in enumerate(points_list):
+        arr[i].n = pt.shape[0]
+        arr[i].c = int(c_list[i]) if c_list is not None else 0
+    o = _opts(0, signed, scalar_bits, prepared)
+    nbytes = lib().msm_g1_batched_workspace_bytes(arr, len(points_list), ctypes.byref(o))
+    if nbytes == 0:
+        raise MsmError(-1, "bad batched MSM options")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def msm_g1_batched(points_list, scalars_list, outs=None, workspace: torch.Tensor | None = None,
+                   c_list=None, signed: bool = True, scalar_bits: int = 0, prepared: bool = False,
+                   stream=None):
+    """Enqueues len(points_list) <= 128 independent MSMs; returns their (24,) output tensors."""
+    if len(points_list) != len(scalars_list):
+        raise ValueError("points and scalars lists differ in length")
+    dev = points_list[0].device
+    if outs is None:
+        outs = [torch.empty(24, dtype=torch.int32, device=dev) for _ in points_list]
+    if workspace is None:
+        workspace = msm_g1_batched_workspace(points_list, c_list, signed, scalar_bits, prepared, dev)
+    for pt, sc in zip(points_list, scalars_list):
+        if pt.shape[0] != sc.shape[0]:
+            raise ValueError("points and scalars differ in length")
+        _check_dev(pt, sc)
+    arr = _jobs_array(points_list, scalars_list, outs, c_list)
+    o = _opts(0, signed, scalar_bits, prepared, None if stream is None else stream)
+    check(lib().msm_g1_batched(arr, len(points_list), _p(workspace), workspace.numel(), ctypes.byref(o)))
+    return outs
 
 
 def msm_g1_status(workspace: torch.Tensor, stream=None) -> int:

@@ -30,6 +30,17 @@ class MsmOpts(ctypes.Structure):
     ]
 
 
+class MsmJob(ctypes.Structure):
+    _fields_ = [
+        ("points", ctypes.c_void_p),
+        ("scalars", ctypes.c_void_p),
+        ("n", ctypes.c_size_t),
+        ("out", ctypes.c_void_p),
+        ("c", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 SIGNATURES = {
     "msm377_last_error": (c_int, [ctypes.c_char_p, c_size]),
     "msm377_version": (c_int, []),
@@ -50,6 +61,8 @@ SIGNATURES = {
     "msm377_profile_last": (c_int, [ctypes.POINTER(ctypes.c_float), c_int]),
     "msm377_launch_count": (ctypes.c_uint64, []),
     "msm_g1_noalloc": (c_int, [c_u32p, c_u32p, c_size, c_u32p, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_batched_workspace_bytes": (c_size, [ctypes.POINTER(MsmJob), c_size, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_batched": (c_int, [ctypes.POINTER(MsmJob), c_size, c_void, c_size, ctypes.POINTER(MsmOpts)]),
 }
 
 

@@ -24,6 +24,8 @@
 // Everything runs on the caller's stream, one launch per stage over all windows.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "ec.cuh"
 
@@ -305,13 +307,9 @@ struct AccArgs {
     int w0, nwin;          // window range of this launch
 };
 
-// Mixed additions of one chunk. Flushes each run to its
-// bucket, or to the chunk's head / tail partial when it crosses a chunk edge.
-__global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
-    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (uint32_t)a.nwin * a.cpw) return;
-    const int w = a.w0 + (int)(id / a.cpw);
-    const uint32_t t = id % a.cpw;
+// Mixed additions of chunk t of window w. Flushes each run to its bucket, or to
+// the chunk's head / tail partial when it crosses a chunk edge.
+__device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32_t t) {
     const size_t ci = (size_t)w * a.cpw + t;
     const uint32_t* keys = a.keys + (size_t)w * a.n;
     const uint32_t* vals = a.vals + (size_t)w * a.n;
@@ -355,6 +353,44 @@ __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
             load_affine(Q, a.pts, v & 0x7fffffffu);
             if (v >> 31) ec::neg(Q);
             ec::madd(acc, inf, Q);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (uint32_t)a.nwin * a.cpw) return;
+    accumulate_chunk(a, a.w0 + (int)(id / a.cpw), id % a.cpw);
+}
+
+// Batched MSMs: one persistent kernel drains a queue of (job, window, chunk)
+// items of all jobs. Each warp takes 32 consecutive items with one atomic.
+constexpr int kMaxBatch = 128;
+struct BatchAcc {
+    AccArgs job[kMaxBatch];
+    uint32_t prefix[kMaxBatch + 1];  // cumulative W * cpw over jobs
+    int njobs;
+    uint32_t* counter;
+};
+
+__global__ void __launch_bounds__(128) k_accumulate_batched(const __grid_constant__ BatchAcc b) {
+    const uint32_t total = b.prefix[b.njobs];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(b.counter, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= total) break;
+        const uint32_t item = base + lane;
+        if (item < total) {
+            int lo = 0, hi = b.njobs - 1;   // last job with prefix <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (b.prefix[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            const AccArgs& a = b.job[lo];
+            const uint32_t local = item - b.prefix[lo];
+            accumulate_chunk(a, (int)(local / a.cpw), local % a.cpw);
         }
     }
 }
@@ -658,33 +694,15 @@ extern "C" int msm_points_prepare(const uint32_t* points_std, size_t n, uint32_t
     return check_launch("msm_points_prepare");
 }
 
-extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out,
-                      void* workspace, size_t workspace_bytes, const msm_opts* opts) {
-    if (!opts) return set_error(MSM377_EINVAL, "msm_g1: opts is NULL");
-    if (!out) return set_error(MSM377_EINVAL, "msm_g1: out is NULL");
-    cudaStream_t s = as_stream(opts->stream);
-    Plan p;
-    if (!make_plan(n, opts, &p))
-        return set_error(MSM377_EINVAL, "msm_g1: bad options (c=%d scalar_bits=%d) or n too large",
-                         opts->c, opts->scalar_bits);
-    if (!workspace || !aligned(workspace, 256))
-        return set_error(MSM377_EINVAL, "msm_g1: workspace NULL or not 256-byte aligned");
-    if (workspace_bytes < p.total)
-        return set_error(MSM377_ENOMEM, "msm_g1: workspace %zu bytes, need %zu", workspace_bytes, p.total);
+namespace {
+
+// Phase 1-3 of one MSM on stream s: status reset, preparation, digits, sort,
+// bucket reset. Fills `a` with the job's accumulation arguments.
+int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars, void* workspace,
+                 const msm_opts* opts, cudaStream_t s, AccArgs* a_out) {
+    const size_t n = p.n;
     int* status = at<int>(workspace, p.off_status);
-    const bool prof = (opts->flags & MSM377_PROFILE) != 0;
-    if (prof) {
-        int pr = profile_begin(s);
-        if (pr) return pr;
-    }
     MSM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
-    if (n == 0) {
-        MSM_CUDA_TRY(cudaMemsetAsync(out, 0, 24 * sizeof(uint32_t), s));
-        return MSM377_OK;
-    }
-    if (!points || !scalars || !aligned(points, 16) || !aligned(scalars, 16))
-        return set_error(MSM377_EINVAL, "msm_g1: points/scalars NULL or not 16-byte aligned");
-    // 1-2. prepare, digits
     const uint4* pts = reinterpret_cast<const uint4*>(points);
     if (!(opts->flags & MSM377_POINTS_PREPARED)) {
         uint4* prep = at<uint4>(workspace, p.off_points);
@@ -697,11 +715,6 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.W,
                                               p.sgn, p.bits, keys[0], vals[0], status);
     note_launches(1);
-    int r = check_launch("msm_g1 digits");
-    if (r) return r;
-    if (prof) profile_mark(s);
-
-    // 3. sort
     uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
     uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
     int cur = 0;
@@ -716,13 +729,9 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
         note_launches(4);
         cur ^= 1;
     }
-    r = check_launch("msm_g1 sort");
-    if (r) return r;
     uint4* buckets = at<uint4>(workspace, p.off_buckets);
     MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * kXyzzBytes, s));
-    if (prof) profile_mark(s);
-
-    AccArgs a;
+    AccArgs& a = *a_out;
     a.keys = keys[cur];
     a.vals = vals[cur];
     a.pts = pts;
@@ -735,23 +744,21 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     a.cpw = p.cpw;
     a.Bp = p.Bp;
     a.K = p.K;
+    a.w0 = 0;
+    a.nwin = p.W;
+    return check_launch("msm head");
+}
+
+// Phase 5-7 of one MSM on stream s: partial merges, bucket reduction, window
+// combination and normalisation into out.
+int enqueue_tail(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s) {
     uint4* Y = at<uint4>(workspace, p.off_Y);
     uint4* V = at<uint4>(workspace, p.off_V);
     uint4* P0 = at<uint4>(workspace, p.off_P0);
     uint4* P1 = at<uint4>(workspace, p.off_P1);
     uint4* S = at<uint4>(workspace, p.off_S);
     uint4* accp = at<uint4>(workspace, p.off_acc);
-
-    // 4. bucket accumulation, all windows
-    a.w0 = 0;
-    a.nwin = p.W;
     const size_t nchunks = (size_t)p.W * p.cpw;
-    k_accumulate<<<grid_for(nchunks, 128), 128, 0, s>>>(a);
-    note_launches(1);
-    r = check_launch("msm_g1 accumulate");
-    if (r) return r;
-    if (prof) profile_mark(s);
-
     // 5. merge partial sums of runs crossing chunk edges (log depth)
     int32_t* start = at<int32_t>(workspace, p.off_start);
     k_merge_scan<<<p.W, kScanThreads, 0, s>>>(a, start);
@@ -762,10 +769,9 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     }
     k_merge_final<<<grid_for(nchunks, 128), 128, 0, s>>>(a);
     note_launches(1);
-
     // 6. bucket reduction, all windows
     const size_t WG = (size_t)p.W * p.G;
-    k_reduce_segments<<<grid_for(WG, 128), 128, 0, s>>>(buckets, p.Bp, p.L, 0, p.W, p.G, Y, V);
+    k_reduce_segments<<<grid_for(WG, 128), 128, 0, s>>>(a.buckets, p.Bp, p.L, 0, p.W, p.G, Y, V);
     const size_t nseg = (size_t)p.W * (p.logG + 1);
     k_bitsums<<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, p.W, p.G, p.logG, p.Q, P0);
     note_launches(2);
@@ -783,12 +789,200 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     }
     k_window_horner<<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
     note_launches(1);
-
     // 7. window combination and normalisation
     k_chain<<<1, 32, 0, s>>>(S, p.W, 0, p.W, p.c, accp, out);
     note_launches(1);
+    return check_launch("msm tail");
+}
+
+// Library-owned helper streams for batched calls, per device, created once.
+constexpr int kMaxDevices = 64;
+constexpr int kAuxStreams = 16;
+struct DeviceAux {
+    bool ready = false;
+    int sms = 0, acc_blocks_per_sm = 0;
+    cudaStream_t st[kAuxStreams];
+    cudaEvent_t fork, done[kAuxStreams];
+};
+DeviceAux g_aux[kMaxDevices];
+std::mutex g_aux_mu;
+
+int device_aux(DeviceAux** out) {
+    int dev = 0;
+    MSM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(MSM377_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_aux_mu);
+    DeviceAux& a = g_aux[dev];
+    if (!a.ready) {
+        MSM_CUDA_TRY(cudaDeviceGetAttribute(&a.sms, cudaDevAttrMultiProcessorCount, dev));
+        MSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a.acc_blocks_per_sm, k_accumulate_batched, 128, 0));
+        if (a.acc_blocks_per_sm < 1) a.acc_blocks_per_sm = 1;
+        for (int i = 0; i < kAuxStreams; ++i) {
+            MSM_CUDA_TRY(cudaStreamCreateWithFlags(&a.st[i], cudaStreamNonBlocking));
+            MSM_CUDA_TRY(cudaEventCreateWithFlags(&a.done[i], cudaEventDisableTiming));
+        }
+        MSM_CUDA_TRY(cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming));
+        a.ready = true;
+    }
+    *out = &a;
+    return MSM377_OK;
+}
+
+// Helper streams wait for work already on s; then s waits for the helpers.
+int fork_from(DeviceAux* aux, cudaStream_t s, int k) {
+    MSM_CUDA_TRY(cudaEventRecord(aux->fork, s));
+    for (int i = 0; i < k; ++i) MSM_CUDA_TRY(cudaStreamWaitEvent(aux->st[i], aux->fork, 0));
+    return MSM377_OK;
+}
+int join_into(DeviceAux* aux, cudaStream_t s, int k) {
+    for (int i = 0; i < k; ++i) {
+        MSM_CUDA_TRY(cudaEventRecord(aux->done[i], aux->st[i]));
+        MSM_CUDA_TRY(cudaStreamWaitEvent(s, aux->done[i], 0));
+    }
+    return MSM377_OK;
+}
+
+}  // namespace
+
+extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out,
+                      void* workspace, size_t workspace_bytes, const msm_opts* opts) {
+    if (!opts) return set_error(MSM377_EINVAL, "msm_g1: opts is NULL");
+    if (!out) return set_error(MSM377_EINVAL, "msm_g1: out is NULL");
+    cudaStream_t s = as_stream(opts->stream);
+    Plan p;
+    if (!make_plan(n, opts, &p))
+        return set_error(MSM377_EINVAL, "msm_g1: bad options (c=%d scalar_bits=%d) or n too large",
+                         opts->c, opts->scalar_bits);
+    if (!workspace || !aligned(workspace, 256))
+        return set_error(MSM377_EINVAL, "msm_g1: workspace NULL or not 256-byte aligned");
+    if (workspace_bytes < p.total)
+        return set_error(MSM377_ENOMEM, "msm_g1: workspace %zu bytes, need %zu", workspace_bytes, p.total);
+    const bool prof = (opts->flags & MSM377_PROFILE) != 0;
+    if (prof) {
+        int pr = profile_begin(s);
+        if (pr) return pr;
+    }
+    if (n == 0) {
+        MSM_CUDA_TRY(cudaMemsetAsync(at<int>(workspace, p.off_status), 0, sizeof(int), s));
+        MSM_CUDA_TRY(cudaMemsetAsync(out, 0, 24 * sizeof(uint32_t), s));
+        return MSM377_OK;
+    }
+    if (!points || !scalars || !aligned(points, 16) || !aligned(scalars, 16))
+        return set_error(MSM377_EINVAL, "msm_g1: points/scalars NULL or not 16-byte aligned");
+    AccArgs a;
+    int r = enqueue_head(p, points, scalars, workspace, opts, s, &a);
+    if (r) return r;
     if (prof) profile_mark(s);
-    return check_launch("msm_g1 tail");
+    k_accumulate<<<grid_for((size_t)p.W * p.cpw, 128), 128, 0, s>>>(a);
+    note_launches(1);
+    r = check_launch("msm_g1 accumulate");
+    if (r) return r;
+    if (prof) profile_mark(s);
+    r = enqueue_tail(p, a, workspace, out, s);
+    if (r) return r;
+    if (prof) profile_mark(s);
+    return MSM377_OK;
+}
+
+namespace {
+constexpr size_t kBatchHeader = 256;
+
+// c for job i of a batch: the job's own, else the options', else the size default.
+bool batch_plans(const msm_job* jobs, size_t njobs, const msm_opts* opts, Plan* plans, size_t* total) {
+    size_t off = kBatchHeader;
+    for (size_t i = 0; i < njobs; ++i) {
+        msm_opts o = *opts;
+        if (jobs[i].c) o.c = jobs[i].c;
+        if (!make_plan(jobs[i].n, &o, &plans[i])) return false;
+        off += align_up(plans[i].total, 256);
+    }
+    *total = off;
+    return true;
+}
+}  // namespace
+
+extern "C" size_t msm_g1_batched_workspace_bytes(const msm_job* jobs, size_t njobs, const msm_opts* opts) {
+    if (!jobs || !opts || njobs == 0 || njobs > (size_t)kMaxBatch) return 0;
+    Plan plans[kMaxBatch];
+    size_t total = 0;
+    if (!batch_plans(jobs, njobs, opts, plans, &total)) return 0;
+    return total;
+}
+
+extern "C" int msm_g1_batched(const msm_job* jobs, size_t njobs, void* workspace, size_t workspace_bytes,
+                              const msm_opts* opts) {
+    if (!jobs || !opts) return set_error(MSM377_EINVAL, "msm_g1_batched: NULL argument");
+    if (njobs == 0) return MSM377_OK;
+    if (njobs > (size_t)kMaxBatch)
+        return set_error(MSM377_EINVAL, "msm_g1_batched: %zu jobs, at most %d per call", njobs, kMaxBatch);
+    if (opts->flags & MSM377_PROFILE)
+        return set_error(MSM377_EINVAL, "msm_g1_batched: MSM377_PROFILE is not supported");
+    Plan plans[kMaxBatch];
+    size_t total = 0;
+    if (!batch_plans(jobs, njobs, opts, plans, &total))
+        return set_error(MSM377_EINVAL, "msm_g1_batched: bad options or n too large in some job");
+    if (!workspace || !aligned(workspace, 256))
+        return set_error(MSM377_EINVAL, "msm_g1_batched: workspace NULL or not 256-byte aligned");
+    if (workspace_bytes < total)
+        return set_error(MSM377_ENOMEM, "msm_g1_batched: workspace %zu bytes, need %zu", workspace_bytes, total);
+    for (size_t i = 0; i < njobs; ++i) {
+        if (!jobs[i].out) return set_error(MSM377_EINVAL, "msm_g1_batched: job %zu has no output", i);
+        if (jobs[i].n && (!jobs[i].points || !jobs[i].scalars || !aligned(jobs[i].points, 16) ||
+                          !aligned(jobs[i].scalars, 16)))
+            return set_error(MSM377_EINVAL, "msm_g1_batched: job %zu points/scalars NULL or misaligned", i);
+    }
+    DeviceAux* aux = nullptr;
+    int r = device_aux(&aux);
+    if (r) return r;
+    cudaStream_t s = as_stream(opts->stream);
+    const int nst = njobs < (size_t)kAuxStreams ? (int)njobs : kAuxStreams;
+
+    // heads of all jobs on the helper streams
+    BatchAcc b;
+    b.njobs = 0;
+    b.prefix[0] = 0;
+    uint32_t* counter = static_cast<uint32_t*>(workspace);
+    MSM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(uint32_t), s));
+    r = fork_from(aux, s, nst);
+    if (r) return r;
+    char* base = static_cast<char*>(workspace) + kBatchHeader;
+    void* ws[kMaxBatch];
+    for (size_t i = 0; i < njobs; ++i) {
+        ws[i] = base;
+        base += align_up(plans[i].total, 256);
+        cudaStream_t si = aux->st[i % nst];
+        if (jobs[i].n == 0) {
+            MSM_CUDA_TRY(cudaMemsetAsync(jobs[i].out, 0, 24 * sizeof(uint32_t), si));
+            continue;
+        }
+        r = enqueue_head(plans[i], jobs[i].points, jobs[i].scalars, ws[i], opts, si, &b.job[b.njobs]);
+        if (r) return r;
+        b.prefix[b.njobs + 1] = b.prefix[b.njobs] + (uint32_t)(plans[i].W * plans[i].cpw);
+        ++b.njobs;
+    }
+    r = join_into(aux, s, nst);
+    if (r) return r;
+
+    // every job's bucket accumulation in one persistent launch
+    if (b.njobs > 0) {
+        b.counter = counter;
+        const unsigned grid = (unsigned)(aux->sms * aux->acc_blocks_per_sm);
+        k_accumulate_batched<<<grid, 128, 0, s>>>(b);
+        note_launches(1);
+        r = check_launch("msm_g1_batched accumulate");
+        if (r) return r;
+    }
+
+    // tails of all jobs on the helper streams
+    r = fork_from(aux, s, nst);
+    if (r) return r;
+    for (size_t i = 0, k = 0; i < njobs; ++i) {
+        if (jobs[i].n == 0) continue;
+        r = enqueue_tail(plans[i], b.job[k], ws[i], jobs[i].out, aux->st[i % nst]);
+        if (r) return r;
+        ++k;
+    }
+    return join_into(aux, s, nst);
 }
 
 extern "C" int msm_g1_status(const void* workspace, const msm_opts* opts) {
