@@ -39,7 +39,7 @@ PROFILE_DIR = os.path.join(ROOT, "profiles")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1 << 20)
@@ -99,7 +99,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -326,6 +326,8 @@ def run_ours(args):
         result["batch_ops"] = batch_ops(pkg, torch, dev, stream)
         # 64 MSMs of log-uniform n in [2^10, 2^20]: one graph launch vs 64 sequential calls
         result["batched_msm"] = batched_msm(pkg, torch, dev)
+        # 2000 Poisson requests over 8 resident sets of 2^22 points
+        result["serving"] = serve(pkg, torch, dev)
         result["cpu_baseline"] = cpu_baseline(1 << 16)
 
     if world > 1:
@@ -386,6 +388,31 @@ def batched_msm(pkg, torch, dev, njobs=64, reps=3):
             "batched_points_per_s": total / (batched_ms / 1e3), "results_identical": bool(same),
             "form": "msm_g1_batched captured in one CUDA graph (persistent accumulation kernel over all "
                     "jobs) vs 64 msm_g1 calls on one stream"}
+
+
+def serve(pkg, torch, dev, nreq=2000, nsets=8, set_size=1 << 22, load=0.8):
+    from paper_2502_11660_gb300 import serving
+    seeds = [synth.scalars(synth.stream_seed(4, set_size, 700 + k), set_size) for k in range(nsets)]
+    t0 = time.perf_counter()
+    rs = serving.ResidentSets(seeds, device=dev)
+    setup_s = time.perf_counter() - t0
+    srv = serving.MsmServer(rs, slots=8, device=dev)
+    # sustained capacity from a back-to-back burst of the same size mix, then 0.8 of it
+    calib = serving.poisson_requests(48, rate=1.0, nsets=nsets, set_size=set_size, lo_log2=12, hi_log2=22, tag=5)
+    srv.run(calib[:8], realtime=False)
+    cap = srv.run(calib, realtime=False)
+    mean_n = float(np.mean([r.n for r in calib]))
+    rate = load * cap["points_per_s"] / mean_n
+    reqs = serving.poisson_requests(nreq, rate=rate, nsets=nsets, set_size=set_size, lo_log2=12, hi_log2=22, tag=4)
+    rep = srv.run(reqs, realtime=True)
+    return {"requests": rep["requests"], "points": rep["points"], "rate_req_per_s": rate,
+            "offered_load": load, "capacity_points_per_s": cap["points_per_s"],
+            "sustained_points_per_s": rep["points_per_s"], "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
+            "mean_ms": rep["mean_ms"], "max_inflight": rep["max_inflight"], "slots": 8,
+            "mem_budget_GB": rep["mem_budget_bytes"] / 1e9, "max_footprint_GB": rep["max_footprint_bytes"] / 1e9,
+            "resident_sets": f"{nsets} x {set_size} points ({nsets * set_size * 96 / 1e9:.1f} GB)",
+            "setup_s": setup_s, "n": "log-uniform [2^12, 2^22]",
+            "scalars": "fresh per request, drawn on the device from the request seed"}
 
 
 def batch_ops(pkg, torch, dev, stream):
