@@ -120,6 +120,11 @@ size_t msm_g1_workspace_bytes(size_t n, const msm_opts *opts);
 /* Window width msm_g1 uses for n points when opts.c == 0. */
 int msm_g1_default_c(size_t n, int signed_digits);
 
+/* Installs measured window widths for signed digits: c_by_log2n[k] is used for
+ * n in [2^k, 2^(k+1)) when opts.c == 0 (0 keeps the built-in rule). len <= 32;
+ * len = 0 clears the table. Process-wide; written by the autotuner. */
+int msm_g1_set_window_table(const int32_t *c_by_log2n, int len);
+
 /* Converts n affine points in standard form (array-of-structures, 24 u32 per point,
  * 16-byte aligned) into the resident Montgomery form that msm_g1 reads with
  * MSM377_POINTS_PREPARED (same layout and size: 96 bytes per point). out may

@@ -146,7 +146,14 @@ __device__ __forceinline__ void mul_inl(fe& r, const fe& a, const fe& bb) {
 }
 
 // Out-of-line multiplication used by the point arithmetic (one copy of the code).
-static __device__ __noinline__ void mul(fe& r, const fe& a, const fe& b) { mul_inl(r, a, b); }
+// Operands and result pass by value so the call keeps them in registers (a
+// by-reference signature forces them through the stack in local memory).
+static __device__ __noinline__ fe mul_v(fe a, fe b) {
+    fe r;
+    mul_inl(r, a, b);
+    return r;
+}
+__device__ __forceinline__ void mul(fe& r, const fe& a, const fe& b) { r = mul_v(a, b); }
 
 __device__ __forceinline__ void sqr(fe& r, const fe& a) { mul(r, a, a); }
 

@@ -24,6 +24,7 @@
 // Everything runs on the caller's stream, one launch per stage over all windows.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -591,8 +592,16 @@ int ilog2(uint64_t v) {
     return r;
 }
 
+// Tuned window widths for signed digits by floor(log2 n) (0 = not tuned), set by
+// msm_g1_set_window_table from a measured table.
+std::atomic<int> g_ctable[32];
+
 int default_c(size_t n, int sgn) {
     int lg = n > 1 ? ilog2(n) : 0;
+    if (sgn && lg < 32) {
+        const int t = g_ctable[lg].load(std::memory_order_relaxed);
+        if (t > 0) return t;
+    }
     int c = lg - 4;
     if (!sgn) c = lg - 3;
     if (c < 4) c = 4;
@@ -677,6 +686,16 @@ T* at(void* ws, size_t off) {
 using namespace msm377;
 
 extern "C" int msm_g1_default_c(size_t n, int signed_digits) { return default_c(n, signed_digits ? 1 : 0); }
+
+extern "C" int msm_g1_set_window_table(const int32_t* c_by_log2n, int len) {
+    if (len < 0 || len > 32 || (len > 0 && !c_by_log2n))
+        return set_error(MSM377_EINVAL, "msm_g1_set_window_table: bad table (len %d)", len);
+    for (int k = 0; k < len; ++k)
+        if (c_by_log2n[k] != 0 && (c_by_log2n[k] < 2 || c_by_log2n[k] > 20))
+            return set_error(MSM377_EINVAL, "msm_g1_set_window_table: c = %d at log2 n = %d", c_by_log2n[k], k);
+    for (int k = 0; k < 32; ++k) g_ctable[k].store(k < len ? c_by_log2n[k] : 0, std::memory_order_relaxed);
+    return MSM377_OK;
+}
 
 extern "C" size_t msm_g1_workspace_bytes(size_t n, const msm_opts* opts) {
     Plan p;

@@ -76,3 +76,22 @@ def test_header_constants_match_the_oracle():
     assert limbs("kR2") == R * R % fq.P
     assert limbs("kR3") == R ** 3 % fq.P
     assert fq.P % (1 << 32) == 1   # so the Montgomery digit is m = -t0 mod 2^32
+
+
+def test_window_table_install_and_reject():
+    import paper_2502_11660_gb300 as pkg
+    from paper_2502_11660_gb300 import autotune
+    base = pkg.msm_g1_default_c(1 << 20)
+    try:
+        autotune.install([0] * 20 + [13])
+        assert pkg.msm_g1_default_c(1 << 20) == 13
+        assert pkg.msm_g1_default_c((1 << 21) - 1) == 13
+        assert pkg.msm_g1_default_c(1 << 21) == base or pkg.msm_g1_default_c(1 << 21) != 13
+        assert pkg.msm_g1_default_c(1 << 20, signed=False) != 13 or base == 13
+        with pytest.raises(pkg.MsmError):
+            autotune.install([1, 2, 3])
+        with pytest.raises(pkg.MsmError):
+            autotune.install([0] * 40)
+    finally:
+        autotune.clear()
+    assert pkg.msm_g1_default_c(1 << 20) == base
