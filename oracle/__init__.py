@@ -20,6 +20,12 @@ Multiplication"):
 * `msm`    — the result the method reaches, sum_i s_i * P_i, by its definition
              (naive double-and-add) and by textbook Pippenger bucket
              accumulation / bucket aggregation / group aggregation (Sec. II-C).
+* `edwards`— the paper's twisted Edwards model -x^2 + y^2 = 1 + (k/2) x^2 y^2
+             (Sec. II-D): the map from y^2 = x^3 + 1, its inverse, the affine
+             Edwards law and the stored form (X, Y, U = k T) with Z = 1.
+* `glv`    — the endomorphism phi(x, y) = (beta x, y) = lambda P on the order-r
+             subgroup and the split k = k1 + lambda k2 (a schedule change, not in
+             the paper), with a Pippenger over (P_i, phi(P_i)).
 * `coracle`— ctypes binding of `oracle.c`, a plain C big-integer version of the
              same arithmetic (schoolbook product + Barrett reduction, 64-bit
              words), used for large inputs and as the timed CPU baseline.
