@@ -1,10 +1,14 @@
 """Benchmark: BLS12-377 G1 MSM points/s at n = 2^20 (one step = one msm_g1 call).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N] [--c C]
+                [--mode xyzz|edwards|glv|edwards+glv|best]
 
-Our arm: resident Montgomery points (prepared once), fresh seeded scalars per
+Our arm: resident prepared points (prepared once), fresh seeded scalars per
 step already in HBM, L2 flushed (256 MB write) between timed steps, per-step
-CUDA events on the launch stream. Prints one JSON line (rank 0).
+CUDA events on the launch stream. Every curve-model / GLV mode is autotuned and
+timed; the headline (`value`) is the fastest mode unless --mode names one (the
+workload's points P_i = s_i G lie in the order-r subgroup, which the Edwards and
+GLV modes require). Prints one JSON line (rank 0).
 Reference arm (--impl reference): the CPU oracle's Pippenger (plain C, all host
 cores) on a bounded sample of the same workload; rank 0 only.
 For N > 1 (torchrun) every rank runs its own MSMs on its own GPU (replicas, no
@@ -33,6 +37,14 @@ PRODUCTS = {"fq_mul": 276, "fq_sqr": 210}
 PRODUCTS["madd"] = 8 * PRODUCTS["fq_mul"] + 2 * PRODUCTS["fq_sqr"]     # 2628
 PRODUCTS["add"] = 12 * PRODUCTS["fq_mul"] + 2 * PRODUCTS["fq_sqr"]     # 3732
 PRODUCTS["dbl"] = 6 * PRODUCTS["fq_mul"] + 3 * PRODUCTS["fq_sqr"]      # 2286
+# twisted Edwards, extended coordinates (a = -1): madd 7M, add 9M (with k T2), dbl 4M + 4S
+PRODUCTS["ed_madd"] = 7 * PRODUCTS["fq_mul"]                            # 1932
+PRODUCTS["ed_add"] = 9 * PRODUCTS["fq_mul"]                             # 2484
+PRODUCTS["ed_dbl"] = 4 * PRODUCTS["fq_mul"] + 4 * PRODUCTS["fq_sqr"]    # 1944
+MODES = {"xyzz": (False, False), "edwards": (True, False), "glv": (False, True), "edwards+glv": (True, True)}
+X0 = 0x8508C00000000001
+R_ORDER = X0 ** 4 - X0 ** 2 + 1
+GLV_LAMBDA = X0 * X0 - 1
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 
@@ -44,6 +56,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--c", type=int, default=0)
+    ap.add_argument("--mode", default="best", choices=["best"] + list(MODES))
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, cpu and batch-op extras")
     return ap.parse_args()
 
@@ -53,6 +66,22 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def glv_halves(scalars: np.ndarray) -> np.ndarray:
+    """(n, 8) scalars -> (2n, 8): rows 2i, 2i + 1 = k1, k2 of k mod r = k1 + lambda k2
+    (the split the library makes; used here only to count the work)."""
+    k = np.zeros(scalars.shape[0], dtype=object)
+    for w in range(8):
+        k += scalars[:, w].astype(object) << (32 * w)
+    k %= R_ORDER
+    k2 = k // GLV_LAMBDA
+    k1 = k - k2 * GLV_LAMBDA
+    out = np.zeros((2 * scalars.shape[0], 8), dtype=np.uint32)
+    for w in range(4):
+        out[0::2, w] = ((k1 >> (32 * w)) & 0xFFFFFFFF).astype(np.uint64).astype(np.uint32)
+        out[1::2, w] = ((k2 >> (32 * w)) & 0xFFFFFFFF).astype(np.uint64).astype(np.uint32)
+    return out
 
 
 def digit_counts(scalars: np.ndarray, c: int, signed: bool, bits: int):
@@ -133,18 +162,20 @@ class ClockSampler:
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("fq.cuh", "ec.cuh", "msm.cu"):
+    for f in ("fq.cuh", "ec.cuh", "ed.cuh", "msm.cu"):
         h.update(open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per accumulate launch from the committed ncu summary, if it matches this source."""
+def recorded_traffic(mode: str):
+    """DRAM bytes per accumulate launch of `mode` from the committed ncu summary, if it
+    matches this source."""
     path = os.path.join(PROFILE_DIR, "accumulate_traffic.json")
     if not os.path.exists(path):
         return None, None
-    rec = json.load(open(path))
-    if rec.get("kernel_hash") != kernel_hash():
+    recs = json.load(open(path))
+    rec = recs.get(mode) if isinstance(recs, dict) and "kernel_hash" not in recs else None
+    if rec is None or rec.get("kernel_hash") != kernel_hash():
         return None, rec
     return rec, rec
 
@@ -204,11 +235,24 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def op_counts(sc_host: np.ndarray, c: int, bits: int, edwards: bool, glv: bool):
+    """Additions and doublings of one MSM, and the textbook products of its accumulation."""
+    sc = glv_halves(sc_host) if glv else sc_host
+    W, nonzero, runs = digit_counts(sc, c, True, 127 if glv else bits)
+    madds = nonzero - runs            # the first point of each run is an assignment
+    full_adds = 2 * W * (1 << (c - 1))  # running sums of the bucket reduction
+    dbls = W * c
+    pm = PRODUCTS["ed_madd" if edwards else "madd"]
+    return {"windows": W, "madd": madds, "bucket_running_sum_adds": full_adds, "window_dbls": dbls,
+            "products_per_madd": pm, "accumulate_products": madds * pm}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
     import paper_2502_11660_gb300 as pkg
+    from paper_2502_11660_gb300 import autotune
 
     world, rank, local = dist_env()
     if world > 1:
@@ -217,60 +261,79 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     n = args.n
     bits = 253
-    tuning = None
-    if args.c:
-        c = args.c
-    else:
-        # window width measured on this GPU among 12..17 (the autotuner), installed for c = 0 calls
-        from paper_2502_11660_gb300 import autotune
-        k = int(np.log2(n))
-        tuning = autotune.tune(log2_sizes=[k], reps=3, device=dev)
-        autotune.install(tuning["table"])
-        c = pkg.msm_g1_default_c(n, True)
+    k = int(np.log2(n))
 
-    # resident point set P_i = s_i G, built and prepared on the device (not timed)
+    # resident point set P_i = s_i G, built on the device and prepared per mode (not timed)
     seeds = synth.scalars(synth.stream_seed(2, n, 2 + 1000 * rank), n)
     pts_std = pkg.g1_generator_mul(pkg.to_device(seeds, dev))
-    prep = pkg.msm_points_prepare(pts_std)
     nsets = args.steps + args.warmup
-    sc_host = [synth.scalars(synth.stream_seed(2, n, 100 + k + 1000 * rank), n) for k in range(nsets)]
+    sc_host = [synth.scalars(synth.stream_seed(2, n, 100 + j + 1000 * rank), n) for j in range(nsets)]
     sc_dev = [pkg.to_device(x, dev) for x in sc_host]
-    ws = pkg.msm_g1_workspace(n, c=c, scalar_bits=bits, prepared=True, device=dev)
     out = torch.empty(24, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(k, profile=False):
-        pkg.msm_g1(prep, sc_dev[k], out=out, workspace=ws, c=c, scalar_bits=bits, prepared=True,
-                   stream=stream, profile=profile)
+    def timed_steps(prep, ws, c, edw, gl, steps, offset, profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stages = []
+        for j in range(steps):
+            flush.fill_(j & 0xFF)                 # L2 flush between timed steps (outside the events)
+            ev[j][0].record(stream)
+            pkg.msm_g1(prep, sc_dev[(offset + j) % nsets], out=out, workspace=ws, c=c, scalar_bits=bits,
+                       prepared=True, stream=stream, profile=profile, edwards=edw, glv=gl)
+            ev[j][1].record(stream)
+            if profile:
+                stages.append(pkg.profile_last())   # synchronises on the step's last event
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], stages
 
-    for k in range(args.warmup):
-        step(k)
-    torch.cuda.synchronize()
+    # every mode: window width measured on this GPU (the autotuner) unless --c, then a short timing
+    survey = {}
+    preps = {}
+    for name, (edw, gl) in MODES.items():
+        if args.mode != "best" and name != args.mode:
+            continue
+        tuning = None
+        if args.c:
+            c = args.c
+        else:
+            tuning = autotune.tune(log2_sizes=[k], reps=3, device=dev, edwards=edw, glv=gl)
+            autotune.install(tuning["table"], edwards=edw, glv=gl)
+            c = pkg.msm_g1_default_c(n, True, edw, gl)
+        prep = pkg.msm_points_prepare(pts_std, edwards=edw, glv=gl)
+        ws = pkg.msm_g1_workspace(n, c=c, scalar_bits=bits, prepared=True, device=dev, edwards=edw, glv=gl)
+        for j in range(args.warmup):
+            pkg.msm_g1(prep, sc_dev[j], out=out, workspace=ws, c=c, scalar_bits=bits, prepared=True,
+                       stream=stream, edwards=edw, glv=gl)
+        torch.cuda.synchronize()
+        ms, st = timed_steps(prep, ws, c, edw, gl, 10, args.warmup, True)
+        survey[name] = {"c": c, "ms_per_step": statistics.mean(ms),
+                        "points_per_s": world * n / (statistics.mean(ms) / 1e3),
+                        "stages_ms": {s2: statistics.mean(x[s2] for x in st) for s2 in st[0]},
+                        "c_by_autotuner": ({str(cc): round(v, 3) for cc, v in tuning["timings"][k].items()}
+                                           if tuning else "given")}
+        preps[name] = (prep, ws, c, edw, gl)
+    mode = min(survey, key=lambda m: survey[m]["ms_per_step"])
+    prep, ws, c, edw, gl = preps[mode]
+    for other in list(preps):
+        if other != mode:
+            del preps[other]
     peak = pkg.imad_probe(20000, stream=stream)   # measured limb-product peak (products/s)
 
+    # the timed region: K steps of the headline mode
     clocks = ClockSampler(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_ms = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     launches0 = pkg.launch_count()
     t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)                 # L2 flush between timed steps (outside the events)
-        ev[k][0].record(stream)
-        step(args.warmup + k, profile=True)
-        ev[k][1].record(stream)
-        stage_ms.append(pkg.profile_last())   # synchronises on the step's last event
-    torch.cuda.synchronize()
+    step_ms, stage_ms = timed_steps(prep, ws, c, edw, gl, args.steps, args.warmup, True)
     wall = time.perf_counter() - t_wall
     launches = pkg.launch_count() - launches0
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -278,37 +341,31 @@ def run_ours(args):
         ms = float(t.item())
     value = world * n / (ms / 1e3)
 
-    # operation counts of one MSM (from the scalars of the timed steps)
-    W, nonzero, runs = digit_counts(sc_host[args.warmup], c, True, bits)
-    madds = nonzero - runs
-    Bp = 1 << (c - 1)
-    full_adds = 2 * W * Bp            # running sums of the bucket reduction (upper level excluded)
-    dbls = W * c
-    ops = madds + full_adds + dbls
-    acc_ms = statistics.mean(s["accumulate"] for s in stage_ms)
-    acc_products = madds * PRODUCTS["madd"]
-    achieved = acc_products / (acc_ms / 1e3)
-    rec, rec_any = recorded_traffic()
-    roofline = {"bound": "alu", "kernel": "k_accumulate", "achieved": achieved / 1e12, "peak": peak / 1e12,
+    ops = op_counts(sc_host[args.warmup], c, bits, edw, gl)
+    acc_ms = statistics.mean(x["accumulate"] for x in stage_ms)
+    achieved = ops["accumulate_products"] / (acc_ms / 1e3)
+    rec, rec_any = recorded_traffic(mode)
+    kname = "k_accumulate<%s>" % ("ModelEdwards" if edw else "ModelXyzz")
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tprod/s", "frac": achieved / peak,
                 "peak_source": "of measured: msm377_imad_probe (mad.lo.cc/madc.hi.cc rows, all SMs)",
-                "algorithmic_products_per_launch": acc_products,
+                "algorithmic_products_per_launch": ops["accumulate_products"],
                 "traffic": (rec["bytes_per_launch_full"] if rec else None)}
+    padds = ops["madd"] + ops["bucket_running_sum_adds"] + ops["window_dbls"]
 
     result = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32 (12x32-bit limb Montgomery integer arithmetic)", "data": "synthetic",
-        "config": {"workload": f"msm_g1 BLS12-377 G1 n={n} signed digits c={c}, resident Montgomery points, "
-                               f"fresh scalars per step", "n": n, "c": c, "windows": W,
-                   "c_choice": ("autotuned on this GPU, ms by c: " + json.dumps(
-                       {str(cc): round(v, 3) for cc, v in tuning["timings"][int(np.log2(n))].items()})
-                                if tuning else "given"),
+        "config": {"workload": f"msm_g1 BLS12-377 G1 n={n}, mode {mode} (signed digits c={c}), resident "
+                               f"prepared points, fresh scalars per step", "n": n, "c": c, "mode": mode,
+                   "windows": ops["windows"],
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{world}"},
-        "padd_per_s": world * ops / (ms / 1e3),
-        "op_counts": {"madd": madds, "bucket_running_sum_adds": full_adds, "window_dbls": dbls},
-        "stages_ms": {k2: statistics.mean(s[k2] for s in stage_ms) for k2 in stage_ms[0]},
+        "padd_per_s": world * padds / (ms / 1e3),
+        "op_counts": ops,
+        "stages_ms": {k2: statistics.mean(x[k2] for x in stage_ms) for k2 in stage_ms[0]},
+        "modes": survey,
         "roofline": roofline,
         "gpu_launches": launches,
         "clocks": clk,
@@ -321,25 +378,26 @@ def run_ours(args):
         hp = pinned_pts.numpy().view(np.uint32)
         hsc = [torch.from_numpy(x.view(np.int32)).pin_memory().numpy().view(np.uint32)
                for x in sc_host[: min(4, nsets)]]
-        hws = torch.empty(pkg.msm_g1_host_workspace_bytes(n, c=c, scalar_bits=bits), dtype=torch.uint8,
-                          device=dev)
-        pkg.msm_g1_host(hp, hsc[0], workspace=hws, c=c, scalar_bits=bits)
+        hkw = dict(c=c, scalar_bits=bits, edwards=edw, glv=gl)
+        hws = torch.empty(pkg.msm_g1_host_workspace_bytes(n, **hkw), dtype=torch.uint8, device=dev)
+        pkg.msm_g1_host(hp, hsc[0], workspace=hws, **hkw)
         et = []
-        for k in range(args.steps):
+        for j in range(args.steps):
             t0 = time.perf_counter()
-            pkg.msm_g1_host(hp, hsc[k % len(hsc)], workspace=hws, c=c, scalar_bits=bits)
+            pkg.msm_g1_host(hp, hsc[j % len(hsc)], workspace=hws, **hkw)
             et.append(time.perf_counter() - t0)
         e2e_s = sum(et) / len(et)
         result["e2e"] = {"value": n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": n * (96 + 32),
                          "d2h_bytes_per_step": 96, "ms_per_step": 1e3 * e2e_s,
-                         "call": "msm_g1_host (pinned host points + scalars, synchronous)"}
+                         "call": f"msm_g1_host (pinned host points + scalars, synchronous; mode {mode}, "
+                                 f"points prepared inside the call)"}
         del hws
         # standalone batched arithmetic at 2^24 (Fq Montgomery multiplications, mixed PADDs)
         result["batch_ops"] = batch_ops(pkg, torch, dev, stream)
         # 64 MSMs of log-uniform n in [2^10, 2^20]: one graph launch vs 64 sequential calls
-        result["batched_msm"] = batched_msm(pkg, torch, dev)
+        result["batched_msm"] = batched_msm(pkg, torch, dev, edw, gl)
         # 2000 Poisson requests over 8 resident sets of 2^22 points
-        result["serving"] = serve(pkg, torch, dev)
+        result["serving"] = serve(pkg, torch, dev, edw, gl)
         result["cpu_baseline"] = cpu_baseline(1 << 16)
 
     if world > 1:
@@ -349,23 +407,24 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
 
 
-def batched_msm(pkg, torch, dev, njobs=64, reps=3):
+def batched_msm(pkg, torch, dev, edw=False, gl=False, njobs=64, reps=3):
     sizes = synth.workloads.batch_sizes(njobs=njobs, lo_log2=10, hi_log2=20, tag=3).tolist()
     pts, scs = [], []
     for i, n in enumerate(sizes):
         seeds = synth.scalars(synth.stream_seed(3, n, 1000 + i), n)
-        pts.append(pkg.msm_points_prepare(pkg.g1_generator_mul(pkg.to_device(seeds, dev))))
+        pts.append(pkg.msm_points_prepare(pkg.g1_generator_mul(pkg.to_device(seeds, dev)), edwards=edw, glv=gl))
         scs.append(pkg.to_device(synth.scalars(synth.stream_seed(3, n, 2000 + i), n), dev))
     bits = 253
+    mk = dict(edwards=edw, glv=gl)
     s = torch.cuda.Stream(dev)
-    ws = pkg.msm_g1_batched_workspace(pts, scalar_bits=bits, prepared=True, device=dev)
+    ws = pkg.msm_g1_batched_workspace(pts, scalar_bits=bits, prepared=True, device=dev, **mk)
     outs = [torch.empty(24, dtype=torch.int32, device=dev) for _ in sizes]
     with torch.cuda.stream(s):
-        pkg.msm_g1_batched(pts, scs, outs=outs, workspace=ws, scalar_bits=bits, prepared=True, stream=s)
+        pkg.msm_g1_batched(pts, scs, outs=outs, workspace=ws, scalar_bits=bits, prepared=True, stream=s, **mk)
     s.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        pkg.msm_g1_batched(pts, scs, outs=outs, workspace=ws, scalar_bits=bits, prepared=True, stream=s)
+        pkg.msm_g1_batched(pts, scs, outs=outs, workspace=ws, scalar_bits=bits, prepared=True, stream=s, **mk)
     g.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -378,12 +437,13 @@ def batched_msm(pkg, torch, dev, njobs=64, reps=3):
     batched_out = [pkg.to_host(o).copy() for o in outs]
     del g, ws
     # the same 64 MSMs as 64 msm_g1 calls on one stream (one shared workspace)
-    wseq = pkg.msm_g1_workspace(max(sizes), scalar_bits=bits, prepared=True, device=dev)
+    wseq = pkg.msm_g1_workspace(max(sizes), scalar_bits=bits, prepared=True, device=dev, **mk)
     seq_outs = [torch.empty(24, dtype=torch.int32, device=dev) for _ in sizes]
 
     def sequential():
         for i in range(len(sizes)):
-            pkg.msm_g1(pts[i], scs[i], out=seq_outs[i], workspace=wseq, scalar_bits=bits, prepared=True, stream=s)
+            pkg.msm_g1(pts[i], scs[i], out=seq_outs[i], workspace=wseq, scalar_bits=bits, prepared=True,
+                       stream=s, **mk)
 
     sequential()
     torch.cuda.synchronize()
@@ -399,14 +459,15 @@ def batched_msm(pkg, torch, dev, njobs=64, reps=3):
             "batched_graph_ms": batched_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batched_ms,
             "batched_points_per_s": total / (batched_ms / 1e3), "results_identical": bool(same),
             "form": "msm_g1_batched captured in one CUDA graph (persistent accumulation kernel over all "
-                    "jobs) vs 64 msm_g1 calls on one stream"}
+                    "jobs) vs 64 msm_g1 calls on one stream",
+            "mode": ("edwards" if edw else "xyzz") + ("+glv" if gl else "")}
 
 
-def serve(pkg, torch, dev, nreq=2000, nsets=8, set_size=1 << 22, load=0.8):
+def serve(pkg, torch, dev, edw=False, gl=False, nreq=2000, nsets=8, set_size=1 << 22, load=0.8):
     from paper_2502_11660_gb300 import serving
     seeds = [synth.scalars(synth.stream_seed(4, set_size, 700 + k), set_size) for k in range(nsets)]
     t0 = time.perf_counter()
-    rs = serving.ResidentSets(seeds, device=dev)
+    rs = serving.ResidentSets(seeds, device=dev, edwards=edw, glv=gl)
     setup_s = time.perf_counter() - t0
     srv = serving.MsmServer(rs, slots=8, device=dev)
     # sustained capacity from a back-to-back burst of the same size mix, then 0.8 of it
@@ -422,7 +483,9 @@ def serve(pkg, torch, dev, nreq=2000, nsets=8, set_size=1 << 22, load=0.8):
             "sustained_points_per_s": rep["points_per_s"], "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"],
             "mean_ms": rep["mean_ms"], "max_inflight": rep["max_inflight"], "slots": 8,
             "mem_budget_GB": rep["mem_budget_bytes"] / 1e9, "max_footprint_GB": rep["max_footprint_bytes"] / 1e9,
-            "resident_sets": f"{nsets} x {set_size} points ({nsets * set_size * 96 / 1e9:.1f} GB)",
+            "resident_sets": f"{nsets} x {set_size} points "
+                             f"({nsets * pkg.msm_points_prepared_bytes(set_size, edw, gl) / 1e9:.1f} GB stored)",
+            "mode": ("edwards" if edw else "xyzz") + ("+glv" if gl else ""),
             "setup_s": setup_s, "n": "log-uniform [2^12, 2^22]",
             "scalars": "fresh per request, drawn on the device from the request seed"}
 

@@ -100,8 +100,24 @@ int g1_generator_mul(const uint32_t *seeds, size_t n, uint32_t *out, void *strea
  */
 
 /* opts.flags */
-#define MSM377_POINTS_PREPARED 1u /* points are Montgomery-form (msm_points_prepare output) */
+#define MSM377_POINTS_PREPARED 1u /* points are in the stored form of msm_points_prepare_ex
+                                     for the same EDWARDS / GLV flags */
 #define MSM377_PROFILE 2u         /* record CUDA events between stages (see msm377_profile_last) */
+/* Curve model of the pipeline: the paper's twisted Edwards curve
+ * -x^2 + y^2 = 1 + (k/2) x^2 y^2 in extended coordinates (Sec. II-D): input points
+ * stored as (x, y, u = k x y) with Z = 1 (144 bytes each), buckets as (X, Y, Z, T);
+ * 7 multiplications per mixed addition instead of XYZZ's 10, no special cases.
+ * PRECONDITION: every point lies in the order-r subgroup of G1 (all points a
+ * BLS12-377 prover commits to do). For other points on y^2 = x^3 + 1 the result
+ * is unspecified (no fault: such points may become the identity). */
+#define MSM377_EDWARDS 4u
+/* GLV split (not in the paper): phi(x, y) = (beta x, y) acts on the order-r
+ * subgroup as multiplication by lambda = x0^2 - 1, lambda^2 + lambda + 1 = r. Each
+ * scalar is reduced mod r and split as k1 + lambda k2 with halves below 2^127;
+ * the MSM runs over the 2n points P_i, phi(P_i) with half the windows.
+ * PRECONDITION: every point lies in the order-r subgroup (same as MSM377_EDWARDS);
+ * scalars may be any 256-bit values (reduced mod r). */
+#define MSM377_GLV 8u
 
 typedef struct msm_opts {
     int32_t c;             /* window width in bits, 2..20; 0 = chosen from n */
@@ -110,29 +126,46 @@ typedef struct msm_opts {
     int32_t scalar_bits;   /* caller's bound: every scalar < 2^scalar_bits (1..256);
                               0 = 256. A larger scalar makes the call fail with
                               MSM377_ERANGE (reported through the workspace status). */
-    uint32_t flags;        /* MSM377_POINTS_PREPARED */
+    uint32_t flags;        /* MSM377_POINTS_PREPARED | MSM377_PROFILE | MSM377_EDWARDS | MSM377_GLV */
     void *stream;          /* cudaStream_t */
 } msm_opts;
 
 /* Workspace bytes msm_g1 needs for n points with these options (0 on bad options). */
 size_t msm_g1_workspace_bytes(size_t n, const msm_opts *opts);
 
-/* Window width msm_g1 uses for n points when opts.c == 0. */
-int msm_g1_default_c(size_t n, int signed_digits);
+/* Window width msm_g1 uses for n points when opts.c == 0 (flags: the options'
+ * MSM377_EDWARDS / MSM377_GLV bits). */
+int msm_g1_default_c(size_t n, int signed_digits, uint32_t flags);
 
 /* Installs measured window widths for signed digits: c_by_log2n[k] is used for
- * n in [2^k, 2^(k+1)) when opts.c == 0 (0 keeps the built-in rule). len <= 32;
- * len = 0 clears the table. Process-wide; written by the autotuner. */
-int msm_g1_set_window_table(const int32_t *c_by_log2n, int len);
+ * n in [2^k, 2^(k+1)) when opts.c == 0 (0 keeps the built-in rule). One table per
+ * combination of MSM377_EDWARDS and MSM377_GLV, chosen by flags (other bits:
+ * MSM377_EINVAL). len <= 32; len = 0 clears that table. Process-wide; written by
+ * the autotuner. */
+int msm_g1_set_window_table(const int32_t *c_by_log2n, int len, uint32_t flags);
+
+/* Bytes of the stored form of n points for flags (a combination of MSM377_EDWARDS
+ * and MSM377_GLV; 0 for other bits): XYZZ 96 per stored point, Edwards 144;
+ * n stored points, or 2n with GLV, interleaved: P_0, phi(P_0), P_1, phi(P_1), ...
+ * so the stored rows of input points [a, b) are rows [2a, 2b): a resident set can
+ * be sliced without copying. */
+size_t msm_points_prepared_bytes(size_t n, uint32_t flags);
 
 /* Converts n affine points in standard form (array-of-structures, 24 u32 per point,
- * 16-byte aligned) into the resident Montgomery form that msm_g1 reads with
- * MSM377_POINTS_PREPARED (same layout and size: 96 bytes per point). out may
- * alias in. */
+ * 16-byte aligned; (0, 0) = O) into the stored form that msm_g1 reads with
+ * MSM377_POINTS_PREPARED and the same EDWARDS / GLV flags: out (16-byte aligned)
+ * holds msm_points_prepared_bytes(n, flags). XYZZ: Montgomery affine (x, y).
+ * Edwards: (x, y, k x y) in Montgomery form, one inversion per 8 points
+ * (Montgomery's trick). out must not overlap points_std unless flags == 0. */
+int msm_points_prepare_ex(const uint32_t *points_std, size_t n, uint32_t *out, uint32_t flags,
+                          void *stream);
+
+/* msm_points_prepare_ex with flags = 0 (XYZZ, no GLV; 96 bytes per point). out
+ * may alias in. */
 int msm_points_prepare(const uint32_t *points_std, size_t n, uint32_t *out, void *stream);
 
-/* points: device, 24 u32 per point (standard form, or prepared with the flag),
- *   16-byte aligned. scalars: device, 8 u32 per scalar, 16-byte aligned.
+/* points: device, 24 u32 per point in standard form, or with MSM377_POINTS_PREPARED
+ *   the stored form of msm_points_prepare_ex for the same flags; 16-byte aligned. scalars: device, 8 u32 per scalar, 16-byte aligned.
  * out: device, 24 u32: the affine sum in standard form, (0, 0) for O.
  * workspace: device, >= msm_g1_workspace_bytes(n, opts), 256-byte aligned; the
  *   first 4 bytes hold the call's device status (0 or a negative code), readable

@@ -22,6 +22,8 @@ FORM_STANDARD = 0
 FORM_MONTGOMERY = 1
 POINTS_PREPARED = 1
 PROFILE = 2
+EDWARDS = 4   # the paper's twisted Edwards model; points of the order-r subgroup
+GLV = 8       # endomorphism split, half the windows; points of the order-r subgroup
 MSM_STAGES = ("head", "accumulate", "tail")
 
 __all__ = [
@@ -30,7 +32,8 @@ __all__ = [
     "padd_batch", "xyzz_to_affine_batch", "g1_generator_mul", "msm_points_prepare",
     "msm_g1", "msm_g1_workspace", "msm_g1_host", "msm_g1_status", "msm_g1_default_c",
     "imad_probe", "lib", "last_error", "profile_last", "launch_count", "MSM_STAGES", "PROFILE",
-    "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace",
+    "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace", "EDWARDS", "GLV",
+    "msm_points_prepared_bytes",
 ]
 
 
@@ -109,26 +112,44 @@ def g1_generator_mul(seeds: torch.Tensor, stream=None) -> torch.Tensor:
     return out
 
 
-def msm_points_prepare(points: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    out = torch.empty_like(points) if out is None else out
+def _model_flags(edwards: bool, glv: bool) -> int:
+    return (EDWARDS if edwards else 0) | (GLV if glv else 0)
+
+
+def msm_points_prepared_bytes(n: int, edwards: bool = False, glv: bool = False) -> int:
+    return int(lib().msm_points_prepared_bytes(n, _model_flags(edwards, glv)))
+
+
+def msm_points_prepare(points: torch.Tensor, out: torch.Tensor | None = None, stream=None,
+                       edwards: bool = False, glv: bool = False) -> torch.Tensor:
+    """Stored form of (n, 24) standard points for msm_g1(..., prepared=True) with the same
+    edwards / glv choice: (n', 24) int32 for XYZZ, (n', 36) for Edwards; n' = 2n with GLV."""
+    flags = _model_flags(edwards, glv)
+    n = points.shape[0]
+    words = lib().msm_points_prepared_bytes(n, flags) // 4
+    rows = 2 * n if glv else n
+    if out is None:
+        out = torch.empty((rows, words // rows if rows else 24), dtype=torch.int32, device=points.device)
     _check_dev(points, out)
-    check(lib().msm_points_prepare(_p(points), points.shape[0], _p(out), _s(stream)))
+    check(lib().msm_points_prepare_ex(_p(points), n, _p(out), flags, _s(stream)))
     return out
 
 
-def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0, profile=False) -> MsmOpts:
+def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0, profile=False, edwards=False,
+          glv=False) -> MsmOpts:
     """stream=0 for size queries (no CUDA context needed); None = torch's current stream."""
     sv = 0 if (isinstance(stream, int) and stream == 0) else _s(stream).value
-    flags = (POINTS_PREPARED if prepared else 0) | (PROFILE if profile else 0)
+    flags = (POINTS_PREPARED if prepared else 0) | (PROFILE if profile else 0) | _model_flags(edwards, glv)
     return MsmOpts(int(c), 1 if signed else 0, int(scalar_bits), flags, sv)
 
 
-def msm_g1_default_c(n: int, signed: bool = True) -> int:
-    return lib().msm_g1_default_c(n, 1 if signed else 0)
+def msm_g1_default_c(n: int, signed: bool = True, edwards: bool = False, glv: bool = False) -> int:
+    return lib().msm_g1_default_c(n, 1 if signed else 0, _model_flags(edwards, glv))
 
 
-def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, device="cuda") -> torch.Tensor:
-    o = _opts(c, signed, scalar_bits, prepared)
+def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, device="cuda",
+                     edwards: bool = False, glv: bool = False) -> torch.Tensor:
+    o = _opts(c, signed, scalar_bits, prepared, edwards=edwards, glv=glv)
     nbytes = lib().msm_g1_workspace_bytes(n, ctypes.byref(o))
     if nbytes == 0:
         raise MsmError(-1, "bad MSM options")
@@ -137,14 +158,15 @@ def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, de
 
 def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None = None,
            workspace: torch.Tensor | None = None, c: int = 0, signed: bool = True,
-           scalar_bits: int = 0, prepared: bool = False, stream=None, profile: bool = False) -> torch.Tensor:
-    """Enqueues sum_i scalars_i * points_i; returns the (24,) int32 device tensor it writes."""
-    n = points.shape[0]
-    if scalars.shape[0] != n:
-        raise ValueError("points and scalars differ in length")
-    o = _opts(c, signed, scalar_bits, prepared, None if stream is None else stream, profile)
+           scalar_bits: int = 0, prepared: bool = False, stream=None, profile: bool = False,
+           edwards: bool = False, glv: bool = False) -> torch.Tensor:
+    """Enqueues sum_i scalars_i * points_i; returns the (24,) int32 device tensor it writes.
+    With prepared=True, points is msm_points_prepare(..., edwards=, glv=) output."""
+    n = scalars.shape[0]
+    _check_points(points, n, prepared, edwards, glv)
+    o = _opts(c, signed, scalar_bits, prepared, None if stream is None else stream, profile, edwards, glv)
     if workspace is None:
-        workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared, points.device)
+        workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared, points.device, edwards, glv)
     out = torch.empty(24, dtype=torch.int32, device=points.device) if out is None else out
     _check_dev(points, scalars, out, workspace)
     check(lib().msm_g1(_p(points), _p(scalars), n, _p(out), _p(workspace), workspace.numel(),
@@ -152,24 +174,36 @@ def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None
     return out
 
 
+def _check_points(points: torch.Tensor, n: int, prepared: bool, edwards: bool, glv: bool) -> None:
+    """The points tensor must hold exactly what the call will read for n scalars."""
+    want = lib().msm_points_prepared_bytes(n, _model_flags(edwards, glv)) if prepared else 96 * n
+    if points.numel() * points.element_size() != want:
+        raise ValueError(f"points tensor holds {points.numel() * points.element_size()} bytes; "
+                         f"{want} expected for n = {n} ({'prepared' if prepared else 'standard'} form)")
+
+
+def _rows(pt: torch.Tensor, prepared: bool, glv: bool) -> int:
+    return pt.shape[0] // 2 if (prepared and glv) else pt.shape[0]
+
+
 def _jobs_array(points_list, scalars_list, outs, cs):
     arr = (MsmJob * len(points_list))()
     for i, (pt, sc, o) in enumerate(zip(points_list, scalars_list, outs)):
         arr[i].points = pt.data_ptr() if pt.shape[0] else 0
         arr[i].scalars = sc.data_ptr() if sc.shape[0] else 0
-        arr[i].n = pt.shape[0]
+        arr[i].n = sc.shape[0]
         arr[i].out = o.data_ptr()
         arr[i].c = int(cs[i]) if cs is not None else 0
     return arr
 
 
 def msm_g1_batched_workspace(points_list, c_list=None, signed=True, scalar_bits=0, prepared=False,
-                             device="cuda") -> torch.Tensor:
+                             device="cuda", edwards: bool = False, glv: bool = False) -> torch.Tensor:
     arr = (MsmJob * len(points_list))()
     for i, pt in enumerate(points_list):
-        arr[i].n = pt.shape[0]
+        arr[i].n = _rows(pt, prepared, glv)
         arr[i].c = int(c_list[i]) if c_list is not None else 0
-    o = _opts(0, signed, scalar_bits, prepared)
+    o = _opts(0, signed, scalar_bits, prepared, edwards=edwards, glv=glv)
     nbytes = lib().msm_g1_batched_workspace_bytes(arr, len(points_list), ctypes.byref(o))
     if nbytes == 0:
         raise MsmError(-1, "bad batched MSM options")
@@ -178,7 +212,7 @@ def msm_g1_batched_workspace(points_list, c_list=None, signed=True, scalar_bits=
 
 def msm_g1_batched(points_list, scalars_list, outs=None, workspace: torch.Tensor | None = None,
                    c_list=None, signed: bool = True, scalar_bits: int = 0, prepared: bool = False,
-                   stream=None):
+                   stream=None, edwards: bool = False, glv: bool = False):
     """Enqueues len(points_list) <= 128 independent MSMs; returns their (24,) output tensors."""
     if len(points_list) != len(scalars_list):
         raise ValueError("points and scalars lists differ in length")
@@ -186,13 +220,13 @@ def msm_g1_batched(points_list, scalars_list, outs=None, workspace: torch.Tensor
     if outs is None:
         outs = [torch.empty(24, dtype=torch.int32, device=dev) for _ in points_list]
     if workspace is None:
-        workspace = msm_g1_batched_workspace(points_list, c_list, signed, scalar_bits, prepared, dev)
+        workspace = msm_g1_batched_workspace(points_list, c_list, signed, scalar_bits, prepared, dev,
+                                             edwards, glv)
     for pt, sc in zip(points_list, scalars_list):
-        if pt.shape[0] != sc.shape[0]:
-            raise ValueError("points and scalars differ in length")
+        _check_points(pt, sc.shape[0], prepared, edwards, glv)
         _check_dev(pt, sc)
     arr = _jobs_array(points_list, scalars_list, outs, c_list)
-    o = _opts(0, signed, scalar_bits, prepared, None if stream is None else stream)
+    o = _opts(0, signed, scalar_bits, prepared, None if stream is None else stream, edwards=edwards, glv=glv)
     check(lib().msm_g1_batched(arr, len(points_list), _p(workspace), workspace.numel(), ctypes.byref(o)))
     return outs
 
@@ -203,12 +237,13 @@ def msm_g1_status(workspace: torch.Tensor, stream=None) -> int:
 
 
 def msm_g1_host(points: np.ndarray, scalars: np.ndarray, workspace: torch.Tensor | None = None,
-                c: int = 0, signed: bool = True, scalar_bits: int = 0, stream=None) -> np.ndarray:
+                c: int = 0, signed: bool = True, scalar_bits: int = 0, stream=None, edwards: bool = False,
+                glv: bool = False) -> np.ndarray:
     """Synchronous MSM on host arrays (copies in and out inside the call)."""
     pts = np.ascontiguousarray(points, dtype=np.uint32)
     sc = np.ascontiguousarray(scalars, dtype=np.uint32)
     n = pts.shape[0]
-    o = _opts(c, signed, scalar_bits, False, None if stream is None else stream)
+    o = _opts(c, signed, scalar_bits, False, None if stream is None else stream, edwards=edwards, glv=glv)
     need = lib().msm_g1_host_workspace_bytes(n, ctypes.byref(o))
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
@@ -219,8 +254,8 @@ def msm_g1_host(points: np.ndarray, scalars: np.ndarray, workspace: torch.Tensor
     return out
 
 
-def msm_g1_host_workspace_bytes(n: int, c=0, signed=True, scalar_bits=0) -> int:
-    o = _opts(c, signed, scalar_bits)
+def msm_g1_host_workspace_bytes(n: int, c=0, signed=True, scalar_bits=0, edwards=False, glv=False) -> int:
+    o = _opts(c, signed, scalar_bits, edwards=edwards, glv=glv)
     return lib().msm_g1_host_workspace_bytes(n, ctypes.byref(o))
 
 

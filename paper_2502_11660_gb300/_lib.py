@@ -51,9 +51,11 @@ SIGNATURES = {
     "xyzz_to_affine_batch": (c_int, [c_u32p, c_u32p, c_size, c_int, c_void]),
     "g1_generator_mul": (c_int, [c_u32p, c_size, c_u32p, c_void]),
     "msm_g1_workspace_bytes": (c_size, [c_size, ctypes.POINTER(MsmOpts)]),
-    "msm_g1_default_c": (c_int, [c_size, c_int]),
-    "msm_g1_set_window_table": (c_int, [ctypes.POINTER(ctypes.c_int32), c_int]),
+    "msm_g1_default_c": (c_int, [c_size, c_int, ctypes.c_uint32]),
+    "msm_g1_set_window_table": (c_int, [ctypes.POINTER(ctypes.c_int32), c_int, ctypes.c_uint32]),
     "msm_points_prepare": (c_int, [c_u32p, c_size, c_u32p, c_void]),
+    "msm_points_prepare_ex": (c_int, [c_u32p, c_size, c_u32p, ctypes.c_uint32, c_void]),
+    "msm_points_prepared_bytes": (c_size, [c_size, ctypes.c_uint32]),
     "msm_g1": (c_int, [c_u32p, c_u32p, c_size, c_u32p, c_void, c_size, ctypes.POINTER(MsmOpts)]),
     "msm_g1_status": (c_int, [c_void, ctypes.POINTER(MsmOpts)]),
     "msm_g1_host_workspace_bytes": (c_size, [c_size, ctypes.POINTER(MsmOpts)]),

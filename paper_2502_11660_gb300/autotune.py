@@ -3,8 +3,9 @@
 For each size n = 2^k it times msm_g1 on the device (resident prepared points,
 fresh scalars) for every candidate c, keeps the fastest, and installs the table
 into the library (msm_g1_set_window_table), so every later call with c = 0 --
-single, batched or served -- uses the measured choice. Tables can be saved to
-and loaded from a JSON file keyed by the device name.
+single, batched or served -- uses the measured choice. The library keeps one
+table per curve model / GLV combination; tune and install the one you run.
+Tables can be saved to and loaded from a JSON file keyed by the device name.
 """
 from __future__ import annotations
 
@@ -15,44 +16,49 @@ import os
 import numpy as np
 import torch
 
-from . import g1_generator_mul, lib, msm_g1, msm_g1_default_c, msm_g1_workspace, msm_points_prepare, to_device
+from . import (_model_flags, g1_generator_mul, lib, msm_g1, msm_g1_default_c, msm_g1_workspace,
+               msm_points_prepare, to_device)
 from ._lib import check
 
 
-def time_msm(n: int, c: int, reps: int = 3, device="cuda", seed: int = 11) -> float:
+def time_msm(n: int, c: int, reps: int = 3, device="cuda", seed: int = 11, edwards: bool = False,
+             glv: bool = False) -> float:
     """Median milliseconds of one msm_g1 call with window c at size n."""
     import synth
-    pts = msm_points_prepare(g1_generator_mul(to_device(synth.scalars(seed, n), device)))
+    pts = msm_points_prepare(g1_generator_mul(to_device(synth.scalars(seed, n), device)), edwards=edwards,
+                             glv=glv)
     sc = to_device(synth.scalars(seed + 1, n), device)
-    ws = msm_g1_workspace(n, c=c, scalar_bits=253, prepared=True, device=device)
+    kw = dict(c=c, scalar_bits=253, prepared=True, edwards=edwards, glv=glv)
+    ws = msm_g1_workspace(n, device=device, **kw)
     out = torch.empty(24, dtype=torch.int32, device=device)
-    msm_g1(pts, sc, out=out, workspace=ws, c=c, scalar_bits=253, prepared=True)
+    msm_g1(pts, sc, out=out, workspace=ws, **kw)
     times = []
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        msm_g1(pts, sc, out=out, workspace=ws, c=c, scalar_bits=253, prepared=True)
+        msm_g1(pts, sc, out=out, workspace=ws, **kw)
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     return float(np.median(times))
 
 
-def candidates(log2n: int) -> list[int]:
-    """Around the built-in rule; 12..17 for the large sizes."""
+def candidates(log2n: int, glv: bool = False) -> list[int]:
+    """Around the built-in rule; 12..17 for the large sizes (13..18 with GLV: 2n points per window)."""
     if log2n >= 16:
-        return list(range(12, 18))
+        return list(range(13, 19)) if glv else list(range(12, 18))
     base = max(4, log2n - 4)
     return sorted({max(3, base - 2), max(3, base - 1), base, base + 1, base + 2})
 
 
-def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda") -> dict:
+def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda", edwards: bool = False,
+         glv: bool = False) -> dict:
     """Returns {"table": [c by log2 n], "timings": {k: {c: ms}}}; fills gaps from neighbours."""
     timings = {}
     best = {}
     for k in log2_sizes:
         n = 1 << k
-        t = {c: time_msm(n, c, reps, device) for c in candidates(k)}
+        t = {c: time_msm(n, c, reps, device, edwards=edwards, glv=glv) for c in candidates(k, glv)}
         timings[k] = t
         best[k] = min(t, key=t.get)
     table = [0] * 32
@@ -62,16 +68,17 @@ def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda") -> dict:
             near = min(keys, key=lambda q: (abs(q - k), q))
             if abs(near - k) <= 2:
                 table[k] = best[near]
-    return {"table": table, "timings": timings, "device": torch.cuda.get_device_name(device)}
+    return {"table": table, "timings": timings, "device": torch.cuda.get_device_name(device),
+            "edwards": edwards, "glv": glv}
 
 
-def install(table) -> None:
+def install(table, edwards: bool = False, glv: bool = False) -> None:
     arr = (ctypes.c_int32 * len(table))(*[int(x) for x in table])
-    check(lib().msm_g1_set_window_table(arr, len(table)))
+    check(lib().msm_g1_set_window_table(arr, len(table), _model_flags(edwards, glv)))
 
 
-def clear() -> None:
-    check(lib().msm_g1_set_window_table(None, 0))
+def clear(edwards: bool = False, glv: bool = False) -> None:
+    check(lib().msm_g1_set_window_table(None, 0, _model_flags(edwards, glv)))
 
 
 def save(result: dict, path: str) -> None:
@@ -88,5 +95,5 @@ def load(path: str) -> dict | None:
         return json.load(f)
 
 
-def current_choice(n: int) -> int:
-    return msm_g1_default_c(n, True)
+def current_choice(n: int, edwards: bool = False, glv: bool = False) -> int:
+    return msm_g1_default_c(n, True, edwards, glv)

@@ -22,6 +22,14 @@
 //                 affine standard form
 //
 // Everything runs on the caller's stream, one launch per stage over all windows.
+//
+// Two curve models run the same pipeline (a template parameter of every point
+// kernel): short Weierstrass XYZZ (default; any points on the curve) and the
+// paper's twisted Edwards model in extended coordinates (MSM377_EDWARDS; 7M
+// mixed additions, points of the order-r subgroup). MSM377_GLV splits every
+// scalar k = k1 + lambda k2 (lambda = x0^2 - 1, 127-bit halves) and runs the
+// pipeline over the 2n points P_i, phi(P_i) = (beta x_i, y_i) with half the
+// windows (subgroup points); stored rows 2i and 2i + 1 are P_i and phi(P_i).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -29,6 +37,7 @@
 
 #include "common.cuh"
 #include "ec.cuh"
+#include "ed.cuh"
 
 namespace {
 
@@ -96,40 +105,192 @@ struct MemQ {
     __device__ __forceinline__ void all(xyzz& r) const { load_xyzz(r, p); }
 };
 
+// Second operand of ed::add_q() read from memory: (X, Y, Z, T) as 12 uint4.
+struct MemQE {
+    const uint4* p;
+    __device__ __forceinline__ void X(fe& r) const { load_fe(r, p); }
+    __device__ __forceinline__ void Y(fe& r) const { load_fe(r, p + 3); }
+    __device__ __forceinline__ void Z(fe& r) const { load_fe(r, p + 6); }
+    __device__ __forceinline__ void T(fe& r) const { load_fe(r, p + 9); }
+};
+
+// ---------------------------------------------------------------- curve models
+//
+// What the pipeline needs from a curve model: the stored form of an input point
+// (kStored uint4 per point), a mixed addition of a gathered stored point, a full
+// addition from memory or registers, a doubling, and the affine Weierstrass
+// result. Accumulators of both models are four 12-word coordinates, 12 uint4 in
+// memory. A bucket that received no point is all-zero words in memory: XYZZ
+// reads that as its identity (ZZ = 0); the Edwards loader skips it.
+
+struct ModelXyzz {
+    using acc = xyzz;
+    static constexpr int kStored = 6;  // affine (x, y)
+    static __device__ __forceinline__ void set_inf(acc& P) { ec::set_inf(P); }
+    static __device__ __forceinline__ void load(acc& P, const uint4* p) { load_xyzz(P, p); }
+    static __device__ __forceinline__ void store(uint4* p, const acc& P) { store_xyzz(p, P); }
+    static __device__ __forceinline__ void madd_at(acc& P, bool& inf, const uint4* pts, uint32_t idx, bool negate) {
+        affine Q;
+        load_affine(Q, pts, idx);
+        if (negate) ec::neg(Q);
+        ec::madd(P, inf, Q);
+    }
+    static __device__ __forceinline__ void add_mem(acc& P, const uint4* q) { ec::add_q(P, MemQ{q}); }
+    static __device__ __forceinline__ void add(acc& P, const acc& Q) { ec::add(P, Q); }
+    static __device__ __forceinline__ void dbl(acc& P) { ec::dbl(P); }
+    static __device__ __forceinline__ void to_affine(affine& A, const acc& P) { ec::to_affine(A, P); }
+};
+
+struct ModelEdwards {
+    using acc = ed::ext;
+    static constexpr int kStored = 9;  // (x, y, u = k x y), the paper's (X, Y, U) with Z = 1
+    static __device__ __forceinline__ void set_inf(acc& P) { ed::set_inf(P); }
+    static __device__ __forceinline__ void load(acc& P, const uint4* p) {
+        load_fe(P.X, p);
+        load_fe(P.Y, p + 3);
+        load_fe(P.Z, p + 6);
+        load_fe(P.T, p + 9);
+    }
+    static __device__ __forceinline__ void store(uint4* p, const acc& P) {
+        store_fe(p, P.X);
+        store_fe(p + 3, P.Y);
+        store_fe(p + 6, P.Z);
+        store_fe(p + 9, P.T);
+    }
+    static __device__ __forceinline__ void madd_at(acc& P, bool& inf, const uint4* pts, uint32_t idx, bool negate) {
+        ed::stored Q;
+        const uint4* q = pts + (size_t)kStored * idx;
+        load_fe(Q.x, q);
+        load_fe(Q.y, q + 3);
+        load_fe(Q.u, q + 6);
+        if (negate) ed::neg(Q);
+        ed::madd(P, inf, Q);
+    }
+    static __device__ __forceinline__ void add_mem(acc& P, const uint4* q) {
+        fe z;
+        load_fe(z, q + 6);
+        if (fq::is_zero_raw(z)) return;  // empty bucket
+        ed::add_q(P, MemQE{q});
+    }
+    static __device__ __forceinline__ void add(acc& P, const acc& Q) { ed::add(P, Q); }
+    static __device__ __forceinline__ void dbl(acc& P) { ed::dbl(P); }
+    static __device__ __forceinline__ void to_affine(affine& A, const acc& P) { ed::to_weierstrass(A, P); }
+};
+
 // ---------------------------------------------------------------- stage 1
 
-__global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    fe x, y;
-    load_fe(x, in + 6 * i);
-    load_fe(y, in + 6 * i + 3);
+// beta, a primitive cube root of unity in Fq with (beta x, y) = lambda (x, y) on
+// the order-r subgroup (Montgomery form).
+__device__ __constant__ static const uint32_t kBeta[fq::N] = {
+    0xa5847973u, 0xdacd106du, 0xbac2a79au, 0xd8fe2454u, 0xfd832edcu, 0x1ada4fd6u,
+    0x9d150908u, 0xfb986844u, 0xea32285eu, 0xd63eb8aeu, 0x6f873fd0u, 0x0167d6a3u};
+
+// Stored point i of np in Montgomery form: input point i when np = n; with GLV
+// (np = 2n) rows 2j and 2j + 1 are P_j and phi(P_j) = (beta x_j, y_j), so any
+// contiguous range of input points is a contiguous range of stored rows. The
+// affine identity (0, 0) stays (0, 0).
+__device__ __forceinline__ void glv_source(fe& x, fe& y, const uint4* __restrict__ in, size_t i, size_t n,
+                                           size_t np) {
+    const bool split = np != n;
+    const size_t src = split ? i >> 1 : i;
+    load_fe(x, in + 6 * src);
+    load_fe(y, in + 6 * src + 3);
     fq::to_mont(x, x);
     fq::to_mont(y, y);
+    if (split && (i & 1)) {
+        fe b;
+        ed::load_const(b, kBeta);
+        fq::mul(x, x, b);
+        fq::canon(x, x);
+    }
+}
+
+__global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n, size_t np) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    fe x, y;
+    glv_source(x, y, in, i, n, np);
     store_fe(out + 6 * i, x);
     store_fe(out + 6 * i + 3, y);
 }
 
+// Weierstrass -> Edwards stored form, kEdChunk points per thread sharing one
+// inversion (Montgomery's trick). For (x_w, y_w), with a = x_w + 1:
+//   D = y_w (a + s),  x = c1 a (a + s) / D,  y = (a - s) y_w / D,  u = k x y.
+// The affine identity, and points outside the map's domain (D = 0: order 2 or
+// 4, never in the subgroup), become the Edwards identity (0, 1, 0).
+constexpr int kEdChunk = 8;
+
+__device__ __forceinline__ bool ed_den(fe& a, fe& den, fe& x, fe& y, const uint4* __restrict__ in, size_t i,
+                                       size_t n, size_t np) {
+    glv_source(x, y, in, i, n, np);
+    if (fq::is_zero_raw(x) && fq::is_zero_raw(y)) return false;
+    fe one, sp;
+    fq::set_one(one);
+    fq::add(a, x, one);
+    ed::load_const(sp, ed::kS);
+    fq::add(sp, a, sp);
+    fq::mul(den, y, sp);
+    return !fq::is_zero(den);
+}
+
+__global__ void k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n, size_t np) {
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t i0 = t * kEdChunk;
+    if (i0 >= np) return;
+    const int m = (int)(np - i0 < (size_t)kEdChunk ? np - i0 : (size_t)kEdChunk);
+    fe pre[kEdChunk];
+    fe acc, a, den, x, y;
+    fq::set_one(acc);
+    for (int j = 0; j < m; ++j) {
+        if (ed_den(a, den, x, y, in, i0 + j, n, np)) fq::mul(acc, acc, den);
+        pre[j] = acc;  // product of the valid denominators 0..j
+    }
+    fe inv;
+    ec::inv(inv, acc);
+    for (int j = m - 1; j >= 0; --j) {
+        uint4* o = out + (size_t)ModelEdwards::kStored * (i0 + j);
+        if (!ed_den(a, den, x, y, in, i0 + j, n, np)) {
+            fe z, one;
+            fq::set_zero(z);
+            fq::set_one(one);
+            fq::canon(one, one);
+            store_fe(o, z);
+            store_fe(o + 3, one);
+            store_fe(o + 6, z);
+            continue;
+        }
+        fe dinv, c, sp, xe, ye, u;
+        if (j > 0) fq::mul(dinv, inv, pre[j - 1]);
+        else dinv = inv;
+        fq::mul(inv, inv, den);
+        ed::load_const(sp, ed::kS);
+        fq::add(c, a, sp);                  // a + s
+        fq::mul(xe, a, c);
+        ed::load_const(c, ed::kC1);
+        fq::mul(xe, xe, c);
+        fq::mul(xe, xe, dinv);              // c1 a (a + s) / D
+        fq::sub(c, a, sp);                  // a - s
+        fq::mul(ye, c, y);
+        fq::mul(ye, ye, dinv);              // (a - s) y / D
+        ed::load_const(c, ed::kK);
+        fq::mul(u, xe, ye);
+        fq::mul(u, u, c);
+        fq::canon(xe, xe);
+        fq::canon(ye, ye);
+        fq::canon(u, u);
+        store_fe(o, xe);
+        store_fe(o + 3, ye);
+        store_fe(o + 6, u);
+    }
+}
+
 // ---------------------------------------------------------------- stage 2
 
-__global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int W, int sgn,
-                         int bits, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                         int* __restrict__ status) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint4 lo = scalars[2 * i], hi = scalars[2 * i + 1];
-    uint32_t s[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
-    if (bits < 256) {
-        uint32_t over = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int lo_bit = 32 * k;
-            uint32_t m = lo_bit >= bits ? 0xffffffffu
-                         : (bits - lo_bit >= 32 ? 0u : ~((1u << (bits - lo_bit)) - 1u));
-            over |= s[k] & m;
-        }
-        if (over) atomicExch(status, MSM377_ERANGE);
-    }
+// Window digits of one scalar (8 words, little-endian) for point index `idx`:
+// key = |digit| (0 = no contribution), value = idx | sign << 31, window-major.
+__device__ __forceinline__ void emit_digits(const uint32_t (&s)[8], int c, int W, int sgn, size_t idx,
+                                            size_t np, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const uint32_t cmask = (1u << c) - 1u, half = 1u << (c - 1);
     uint32_t carry = 0;
     for (int j = 0; j < W; ++j) {
@@ -154,9 +315,140 @@ __global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int
         } else {
             key = raw;
         }
-        keys[(size_t)j * n + i] = key;
-        vals[(size_t)j * n + i] = (uint32_t)i | (neg << 31);
+        keys[(size_t)j * np + idx] = key;
+        vals[(size_t)j * np + idx] = (uint32_t)idx | (neg << 31);
     }
+}
+
+// GLV split of a scalar k < 2^256: k mod r = k1 + lambda k2 with 0 <= k1 < lambda
+// and k2 <= lambda + 1 (both below 2^127), lambda = x0^2 - 1 and
+// lambda^2 + lambda + 1 = r. k is first reduced below r by conditional
+// subtraction of 8r, 4r, 2r, r (2^256 < 16 r). Then q = floor(k mu / 2^256) with
+// mu = floor(2^256 / lambda) is k2 or k2 - 1 (k mu / 2^256 > k / lambda - 1 since
+// k < 2^256), fixed by one conditional subtraction of lambda.
+__device__ __constant__ static const uint32_t kR8[4][8] = {
+    {0x00000008u, 0x508c0000u, 0x80000008u, 0xcd53b7f6u, 0xe1bd800au, 0x05a268f2u, 0xd1652ab3u, 0x955b2af4u},
+    {0x00000004u, 0x28460000u, 0x40000004u, 0x66a9dbfbu, 0x70dec005u, 0x82d13479u, 0x68b29559u, 0x4aad957au},
+    {0x00000002u, 0x14230000u, 0xa0000002u, 0xb354edfdu, 0xb86f6002u, 0xc1689a3cu, 0x34594aacu, 0x2556cabdu},
+    {0x00000001u, 0x0a118000u, 0xd0000001u, 0x59aa76feu, 0x5c37b001u, 0x60b44d1eu, 0x9a2ca556u, 0x12ab655eu}};
+__device__ __constant__ static const uint32_t kLambda[4] = {0x00000000u, 0x0a118000u, 0x90000001u, 0x452217ccu};
+__device__ __constant__ static const uint32_t kMu[5] = {0xaf90182cu, 0x7f72ed32u, 0x9fd37160u, 0xb3f7aa96u,
+                                                        0x00000003u};
+
+__device__ __forceinline__ void glv_split(uint32_t (&k)[8], uint32_t (&k1)[8], uint32_t (&k2)[8]) {
+    for (int m = 0; m < 4; ++m) {  // k -= 8r, 4r, 2r, r where k is at least that
+        uint32_t d[8];
+        uint64_t borrow = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            uint64_t t = (uint64_t)k[w] - kR8[m][w] - borrow;
+            d[w] = (uint32_t)t;
+            borrow = (t >> 63) & 1u;
+        }
+        if (!borrow) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) k[w] = d[w];
+        }
+    }
+    // q = floor(k mu / 2^256): columns 8..12 of the 8 x 5 word product
+    uint32_t prod[13];
+#pragma unroll
+    for (int w = 0; w < 13; ++w) prod[w] = 0;
+    for (int i = 0; i < 8; ++i) {
+        uint64_t carry = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            uint64_t t = (uint64_t)k[i] * kMu[j] + prod[i + j] + carry;
+            prod[i + j] = (uint32_t)t;
+            carry = t >> 32;
+        }
+        for (int w = i + 5; w < 13 && carry; ++w) {
+            uint64_t t = (uint64_t)prod[w] + carry;
+            prod[w] = (uint32_t)t;
+            carry = t >> 32;
+        }
+    }
+    uint32_t q[4] = {prod[8], prod[9], prod[10], prod[11]};  // k mu < 2^383, so prod[12] = 0
+    // rem = k - q lambda (fits in 5 words: rem < 2 lambda < 2^128)
+    uint32_t ql[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) ql[w] = 0;
+    for (int i = 0; i < 4; ++i) {
+        uint64_t carry = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint64_t t = (uint64_t)q[i] * kLambda[j] + ql[i + j] + carry;
+            ql[i + j] = (uint32_t)t;
+            carry = t >> 32;
+        }
+        ql[i + 4] = (uint32_t)carry;
+    }
+    uint32_t rem[8];
+    uint64_t borrow = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        uint64_t t = (uint64_t)k[w] - ql[w] - borrow;
+        rem[w] = (uint32_t)t;
+        borrow = (t >> 63) & 1u;
+    }
+    // rem >= lambda ? (rem < 2^128 here, so words 4..7 are zero)
+    bool ge = true;
+    for (int w = 3; w >= 0; --w) {
+        if (rem[w] != kLambda[w]) {
+            ge = rem[w] > kLambda[w];
+            break;
+        }
+    }
+    if (rem[4] | rem[5] | rem[6] | rem[7]) ge = true;
+    if (ge) {
+        uint64_t br = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            uint64_t t = (uint64_t)rem[w] - (w < 4 ? kLambda[w] : 0u) - br;
+            rem[w] = (uint32_t)t;
+            br = (t >> 63) & 1u;
+        }
+        uint64_t cy = 1;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            uint64_t t = (uint64_t)q[w] + cy;
+            q[w] = (uint32_t)t;
+            cy = t >> 32;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        k1[w] = w < 4 ? rem[w] : 0u;
+        k2[w] = w < 4 ? q[w] : 0u;
+    }
+}
+
+__global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int W, int sgn,
+                         int bits, int glv, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                         int* __restrict__ status) {
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint4 lo = scalars[2 * i], hi = scalars[2 * i + 1];
+    uint32_t s[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    if (bits < 256) {
+        uint32_t over = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int lo_bit = 32 * k;
+            uint32_t m = lo_bit >= bits ? 0xffffffffu
+                         : (bits - lo_bit >= 32 ? 0u : ~((1u << (bits - lo_bit)) - 1u));
+            over |= s[k] & m;
+        }
+        if (over) atomicExch(status, MSM377_ERANGE);
+    }
+    if (!glv) {
+        emit_digits(s, c, W, sgn, i, n, keys, vals);
+        return;
+    }
+    uint32_t k1[8], k2[8];
+    glv_split(s, k1, k2);
+    emit_digits(k1, c, W, sgn, 2 * i, 2 * n, keys, vals);      // P_i
+    emit_digits(k2, c, W, sgn, 2 * i + 1, 2 * n, keys, vals);  // phi(P_i)
 }
 
 // ---------------------------------------------------------------- stage 3: radix sort
@@ -310,6 +602,7 @@ struct AccArgs {
 
 // Mixed additions of chunk t of window w. Flushes each run to its bucket, or to
 // the chunk's head / tail partial when it crosses a chunk edge.
+template <class M>
 __device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32_t t) {
     const size_t ci = (size_t)w * a.cpw + t;
     const uint32_t* keys = a.keys + (size_t)w * a.n;
@@ -320,8 +613,8 @@ __device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32
     const uint32_t next = end < a.n ? keys[end] : kNone;
     a.tailkey[ci] = kNone;
     a.headflag[ci] = 0;
-    xyzz acc;
-    ec::set_inf(acc);
+    typename M::acc acc;
+    M::set_inf(acc);
     bool inf = true;
     uint32_t cur = keys[start];
     bool first = true;
@@ -332,17 +625,17 @@ __device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32
                 const bool sb = first && prev == cur;
                 const bool ea = (g == end) && next == cur;
                 if (!sb && !ea) {
-                    store_xyzz(a.buckets + ((size_t)w * a.Bp + (cur - 1)) * kXyzzVec, acc);
+                    M::store(a.buckets + ((size_t)w * a.Bp + (cur - 1)) * kXyzzVec, acc);
                 } else if (sb) {
-                    store_xyzz(a.head + ci * kXyzzVec, acc);
+                    M::store(a.head + ci * kXyzzVec, acc);
                     a.headflag[ci] = ea ? 2u : 1u;
                 } else {
-                    store_xyzz(a.tail + ci * kXyzzVec, acc);
+                    M::store(a.tail + ci * kXyzzVec, acc);
                     a.tailkey[ci] = cur;
                 }
             }
             if (g == end) break;
-            ec::set_inf(acc);
+            M::set_inf(acc);
             inf = true;
             cur = key;
             first = false;
@@ -350,18 +643,16 @@ __device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32
         if (key != 0) {
             const uint32_t v = vals[g];
             if ((v & 0x7fffffffu) >= a.n) continue;  // cannot happen for sorted digit output
-            affine Q;
-            load_affine(Q, a.pts, v & 0x7fffffffu);
-            if (v >> 31) ec::neg(Q);
-            ec::madd(acc, inf, Q);
+            M::madd_at(acc, inf, a.pts, v & 0x7fffffffu, (v >> 31) != 0);
         }
     }
 }
 
+template <class M>
 __global__ void __launch_bounds__(128) k_accumulate(AccArgs a) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (uint32_t)a.nwin * a.cpw) return;
-    accumulate_chunk(a, a.w0 + (int)(id / a.cpw), id % a.cpw);
+    accumulate_chunk<M>(a, a.w0 + (int)(id / a.cpw), id % a.cpw);
 }
 
 // Batched MSMs: one persistent kernel drains a queue of (job, window, chunk)
@@ -374,6 +665,7 @@ struct BatchAcc {
     uint32_t* counter;
 };
 
+template <class M>
 __global__ void __launch_bounds__(128) k_accumulate_batched(const __grid_constant__ BatchAcc b) {
     const uint32_t total = b.prefix[b.njobs];
     const int lane = threadIdx.x & 31;
@@ -391,7 +683,7 @@ __global__ void __launch_bounds__(128) k_accumulate_batched(const __grid_constan
             }
             const AccArgs& a = b.job[lo];
             const uint32_t local = item - b.prefix[lo];
-            accumulate_chunk(a, (int)(local / a.cpw), local % a.cpw);
+            accumulate_chunk<M>(a, (int)(local / a.cpw), local % a.cpw);
         }
     }
 }
@@ -431,6 +723,7 @@ __global__ void __launch_bounds__(kScanThreads) k_merge_scan(AccArgs a, int32_t*
     }
 }
 
+template <class M>
 __global__ void k_merge_round(AccArgs a, const int32_t* __restrict__ start, uint32_t d) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (uint32_t)a.nwin * a.cpw) return;
@@ -444,12 +737,13 @@ __global__ void k_merge_round(AccArgs a, const int32_t* __restrict__ start, uint
     if (j % (2 * d) != 0) return;
     const uint32_t v = u + d;
     if (v >= a.cpw || a.headflag[base + v] == 0 || start[base + v] != t0) return;
-    xyzz acc;
-    load_xyzz(acc, a.head + (base + u) * kXyzzVec);
-    ec::add_q(acc, MemQ{a.head + (base + v) * kXyzzVec});
-    store_xyzz(a.head + (base + u) * kXyzzVec, acc);
+    typename M::acc acc;
+    M::load(acc, a.head + (base + u) * kXyzzVec);
+    M::add_mem(acc, a.head + (base + v) * kXyzzVec);
+    M::store(a.head + (base + u) * kXyzzVec, acc);
 }
 
+template <class M>
 __global__ void k_merge_final(AccArgs a) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (uint32_t)a.nwin * a.cpw) return;
@@ -458,34 +752,36 @@ __global__ void k_merge_final(AccArgs a) {
     const size_t ci = (size_t)w * a.cpw + t;
     const uint32_t key = a.tailkey[ci];
     if (key == kNone) return;
-    xyzz acc;
-    load_xyzz(acc, a.tail + ci * kXyzzVec);
-    if (t + 1 < a.cpw && a.headflag[ci + 1] != 0) ec::add_q(acc, MemQ{a.head + (ci + 1) * kXyzzVec});
-    store_xyzz(a.buckets + ((size_t)w * a.Bp + (key - 1)) * kXyzzVec, acc);
+    typename M::acc acc;
+    M::load(acc, a.tail + ci * kXyzzVec);
+    if (t + 1 < a.cpw && a.headflag[ci + 1] != 0) M::add_mem(acc, a.head + (ci + 1) * kXyzzVec);
+    M::store(a.buckets + ((size_t)w * a.Bp + (key - 1)) * kXyzzVec, acc);
 }
 
 // ---------------------------------------------------------------- stage 6
 
 // Thread (wi, g): Y = sum_{i=1..L} B[gL+i], V = sum_{i=1..L} i * B[gL+i] (bucket b at index b-1).
+template <class M>
 __global__ void k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, int w0, int nwin,
                                   uint32_t G, uint4* __restrict__ Y, uint4* __restrict__ V) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)nwin * G) return;
     const size_t wi = id / G, g = id % G;
     const uint4* seg = buckets + ((size_t)(w0 + wi) * Bp + g * L) * kXyzzVec;
-    xyzz T, S;
-    ec::set_inf(T);
-    ec::set_inf(S);
+    typename M::acc T, S;
+    M::set_inf(T);
+    M::set_inf(S);
     for (int i = (int)L; i >= 1; --i) {
-        ec::add_q(T, MemQ{seg + (size_t)(i - 1) * kXyzzVec});   // T += B
-        ec::add(S, T);                                          // S += T
+        M::add_mem(T, seg + (size_t)(i - 1) * kXyzzVec);   // T += B
+        M::add(S, T);                                       // S += T
     }
-    store_xyzz(Y + id * kXyzzVec, T);
-    store_xyzz(V + id * kXyzzVec, S);
+    M::store(Y + id * kXyzzVec, T);
+    M::store(V + id * kXyzzVec, S);
 }
 
 // Thread (wi, k, q): partial of Z_k = sum_{g in chunk q, bit k of g set} Y_g, or for
 // k == logG the partial of sum_{g in chunk q} V_g.
+template <class M>
 __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__ V, int nwin, uint32_t G,
                           int logG, uint32_t Q, uint4* __restrict__ P) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -495,45 +791,47 @@ __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__
     const int k = (int)((id % per_w) / Q);
     const uint32_t q = (uint32_t)(id % Q);
     const uint32_t span = G / Q, g0 = q * span;
-    xyzz acc;
-    ec::set_inf(acc);
+    typename M::acc acc;
+    M::set_inf(acc);
     for (uint32_t g = g0; g < g0 + span; ++g) {
         if (k == logG) {
-            ec::add_q(acc, MemQ{V + (wi * G + g) * kXyzzVec});
+            M::add_mem(acc, V + (wi * G + g) * kXyzzVec);
         } else if ((g >> k) & 1u) {
-            ec::add_q(acc, MemQ{Y + (wi * G + g) * kXyzzVec});
+            M::add_mem(acc, Y + (wi * G + g) * kXyzzVec);
         }
     }
-    store_xyzz(P + id * kXyzzVec, acc);
+    M::store(P + id * kXyzzVec, acc);
 }
 
 // out[s][i] = sum_{e < F} in[s][i F + e], segments of m points.
+template <class M>
 __global__ void k_sum_segments(const uint4* __restrict__ in, size_t nseg, uint32_t m, uint32_t F,
                                uint4* __restrict__ out) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const uint32_t mo = m / F;
     if (id >= nseg * mo) return;
     const size_t s = id / mo, i = id % mo;
-    xyzz acc;
-    ec::set_inf(acc);
-    for (uint32_t e = 0; e < F; ++e) ec::add_q(acc, MemQ{in + (s * m + i * F + e) * kXyzzVec});
-    store_xyzz(out + id * kXyzzVec, acc);
+    typename M::acc acc;
+    M::set_inf(acc);
+    for (uint32_t e = 0; e < F; ++e) M::add_mem(acc, in + (s * m + i * F + e) * kXyzzVec);
+    M::store(out + id * kXyzzVec, acc);
 }
 
 // Thread wi: S_w = Z_V + L * sum_k 2^k Z_k (Horner over k), Z laid out [nwin][logG + 1].
+template <class M>
 __global__ void k_window_horner(const uint4* __restrict__ Z, int nwin, int logG, int log2L, uint4* __restrict__ S) {
     const int wi = blockIdx.x * blockDim.x + threadIdx.x;
     if (wi >= nwin) return;
     const uint4* z = Z + (size_t)wi * (logG + 1) * kXyzzVec;
-    xyzz acc;
-    ec::set_inf(acc);
+    typename M::acc acc;
+    M::set_inf(acc);
     for (int k = logG - 1; k >= 0; --k) {
-        ec::dbl(acc);
-        ec::add_q(acc, MemQ{z + (size_t)k * kXyzzVec});
+        M::dbl(acc);
+        M::add_mem(acc, z + (size_t)k * kXyzzVec);
     }
-    for (int l = 0; l < log2L; ++l) ec::dbl(acc);
-    ec::add_q(acc, MemQ{z + (size_t)logG * kXyzzVec});
-    store_xyzz(S + (size_t)wi * kXyzzVec, acc);
+    for (int l = 0; l < log2L; ++l) M::dbl(acc);
+    M::add_mem(acc, z + (size_t)logG * kXyzzVec);
+    M::store(S + (size_t)wi * kXyzzVec, acc);
 }
 
 // ---------------------------------------------------------------- stage 7
@@ -541,24 +839,25 @@ __global__ void k_window_horner(const uint4* __restrict__ Z, int nwin, int logG,
 // One thread: acc = 2^(c) acc + S_w for w = w_hi - 1 down to w_lo (acc starts at
 // O for the top window of the MSM); when w_lo = 0 it normalises acc and writes
 // the affine result in standard form.
+template <class M>
 __global__ void k_chain(const uint4* __restrict__ S, int w_hi, int w_lo, int W, int c, uint4* __restrict__ accp,
                         uint32_t* __restrict__ out) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    xyzz acc;
+    typename M::acc acc;
     if (w_hi == W)
-        ec::set_inf(acc);
+        M::set_inf(acc);
     else
-        load_xyzz(acc, accp);
+        M::load(acc, accp);
     for (int w = w_hi - 1; w >= w_lo; --w) {
-        for (int k = 0; k < c; ++k) ec::dbl(acc);
-        ec::add_q(acc, MemQ{S + (size_t)w * kXyzzVec});
+        for (int k = 0; k < c; ++k) M::dbl(acc);
+        M::add_mem(acc, S + (size_t)w * kXyzzVec);
     }
     if (w_lo > 0) {
-        store_xyzz(accp, acc);
+        M::store(accp, acc);
         return;
     }
     affine A;
-    ec::to_affine(A, acc);
+    M::to_affine(A, acc);
     if (!ec::is_inf(A)) {
         fq::from_mont(A.x, A.x);
         fq::from_mont(A.y, A.y);
@@ -570,7 +869,11 @@ __global__ void k_chain(const uint4* __restrict__ S, int w_hi, int w_lo, int W, 
 // ---------------------------------------------------------------- planning
 
 struct Plan {
-    size_t n;
+    size_t n;        // scalars (and input points)
+    size_t np;       // stored points = items per window: n, or 2n with GLV
+    int edw, glv;    // curve model (0 XYZZ, 1 Edwards); GLV split
+    int stored_vec;  // uint4 per stored point
+    int user_bits;   // scalar range checked against opts.scalar_bits
     int c, sgn, bits, W;
     uint32_t B, Bp;
     int passes;
@@ -592,16 +895,22 @@ int ilog2(uint64_t v) {
     return r;
 }
 
-// Tuned window widths for signed digits by floor(log2 n) (0 = not tuned), set by
-// msm_g1_set_window_table from a measured table.
-std::atomic<int> g_ctable[32];
+// Tuned window widths for signed digits by floor(log2 n) (0 = not tuned), one
+// table per mode (Edwards, GLV), set by msm_g1_set_window_table from a measured
+// table.
+std::atomic<int> g_ctable[4][32];
 
-int default_c(size_t n, int sgn) {
+int table_mode(uint32_t flags) {
+    return ((flags & MSM377_EDWARDS) ? 1 : 0) | ((flags & MSM377_GLV) ? 2 : 0);
+}
+
+int default_c(size_t n, int sgn, uint32_t flags) {
     int lg = n > 1 ? ilog2(n) : 0;
     if (sgn && lg < 32) {
-        const int t = g_ctable[lg].load(std::memory_order_relaxed);
+        const int t = g_ctable[table_mode(flags)][lg].load(std::memory_order_relaxed);
         if (t > 0) return t;
     }
+    if (flags & MSM377_GLV) ++lg;  // 2n points per window
     int c = lg - 4;
     if (!sgn) c = lg - 3;
     if (c < 4) c = 4;
@@ -612,23 +921,29 @@ int default_c(size_t n, int sgn) {
 bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     if (!o) return false;
     p->n = n;
+    p->edw = (o->flags & MSM377_EDWARDS) ? 1 : 0;
+    p->glv = (o->flags & MSM377_GLV) ? 1 : 0;
+    p->stored_vec = p->edw ? ModelEdwards::kStored : ModelXyzz::kStored;
     p->sgn = o->signed_digits ? 1 : 0;
-    p->bits = o->scalar_bits ? o->scalar_bits : 256;
-    if (p->bits < 1 || p->bits > 256) return false;
-    p->c = o->c ? o->c : default_c(n, p->sgn);
+    p->user_bits = o->scalar_bits ? o->scalar_bits : 256;
+    if (p->user_bits < 1 || p->user_bits > 256) return false;
+    p->bits = p->glv ? 127 : p->user_bits;  // GLV halves are below 2^127
+    p->c = o->c ? o->c : default_c(n, p->sgn, o->flags);
     if (p->c < 2 || p->c > 20) return false;
-    if (n >= (1ull << 31)) return false;
+    if (n >= (1ull << 30)) return false;
+    const size_t np = p->glv ? 2 * n : n;
+    p->np = np;
     p->W = p->sgn ? (p->bits + 1 + p->c - 1) / p->c : (p->bits + p->c - 1) / p->c;
     p->B = p->sgn ? (1u << (p->c - 1)) : ((1u << p->c) - 1u);
     p->Bp = p->sgn ? p->B : (1u << p->c);
     p->passes = (p->c + 7) / 8;
-    p->tiles = (n + kSortTile - 1) / kSortTile;
+    p->tiles = (np + kSortTile - 1) / kSortTile;
     // about 150 resident threads x 512 per SM worth of chunks over all windows
-    size_t K = ((size_t)p->W * n) / (152 * 512);
+    size_t K = ((size_t)p->W * np) / (152 * 512);
     if (K < 2) K = 2;
     if (K > 64) K = 64;
     p->K = (int)K;
-    p->cpw = (uint32_t)((n + K - 1) / K);
+    p->cpw = (uint32_t)((np + K - 1) / K);
     if (p->cpw == 0) p->cpw = 1;
     p->gw = p->W;
     p->ngroups = 1;
@@ -652,11 +967,11 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     const size_t XY = kXyzzBytes;
     const size_t chunks = (size_t)p->W * p->cpw;
     p->off_status = take(256);
-    p->off_points = take(o->flags & MSM377_POINTS_PREPARED ? 0 : n * 96);
-    p->off_keys0 = take((size_t)p->W * n * 4);
-    p->off_vals0 = take((size_t)p->W * n * 4);
-    p->off_keys1 = take((size_t)p->W * n * 4);
-    p->off_vals1 = take((size_t)p->W * n * 4);
+    p->off_points = take(o->flags & MSM377_POINTS_PREPARED ? 0 : np * 16 * (size_t)p->stored_vec);
+    p->off_keys0 = take((size_t)p->W * np * 4);
+    p->off_vals0 = take((size_t)p->W * np * 4);
+    p->off_keys1 = take((size_t)p->W * np * 4);
+    p->off_vals1 = take((size_t)p->W * np * 4);
     p->off_hist = take((size_t)p->W * kRadix * (p->tiles ? p->tiles : 1) * 4);
     p->off_dtot = take((size_t)p->W * kRadix * 4);
     p->off_buckets = take((size_t)p->W * p->Bp * XY);
@@ -676,6 +991,23 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     return true;
 }
 
+// Stored points of a set: the form the pipeline gathers from (XYZZ: Montgomery
+// affine, 96 B; Edwards: (x, y, k x y), 144 B), for n input points or, with GLV,
+// for the 2n points P_0, phi(P_0), P_1, phi(P_1), ...
+size_t stored_count(size_t n, uint32_t flags) { return (flags & MSM377_GLV) ? 2 * n : n; }
+int stored_vec(uint32_t flags) { return (flags & MSM377_EDWARDS) ? ModelEdwards::kStored : ModelXyzz::kStored; }
+
+void launch_prepare(const uint4* in, uint4* out, size_t n, uint32_t flags, cudaStream_t s) {
+    const size_t np = stored_count(n, flags);
+    if (flags & MSM377_EDWARDS) {
+        const size_t threads = (np + kEdChunk - 1) / kEdChunk;
+        k_prepare_ed<<<msm377::grid_for(threads, 128), 128, 0, s>>>(in, out, n, np);
+    } else {
+        k_prepare<<<msm377::grid_for(np, 256), 256, 0, s>>>(in, out, n, np);
+    }
+    msm377::note_launches(1);
+}
+
 template <typename T>
 T* at(void* ws, size_t off) {
     return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
@@ -685,15 +1017,22 @@ T* at(void* ws, size_t off) {
 
 using namespace msm377;
 
-extern "C" int msm_g1_default_c(size_t n, int signed_digits) { return default_c(n, signed_digits ? 1 : 0); }
+extern "C" int msm_g1_default_c(size_t n, int signed_digits, uint32_t flags) {
+    return default_c(n, signed_digits ? 1 : 0, flags);
+}
 
-extern "C" int msm_g1_set_window_table(const int32_t* c_by_log2n, int len) {
+extern "C" int msm_g1_set_window_table(const int32_t* c_by_log2n, int len, uint32_t flags) {
     if (len < 0 || len > 32 || (len > 0 && !c_by_log2n))
         return set_error(MSM377_EINVAL, "msm_g1_set_window_table: bad table (len %d)", len);
+    if (flags & ~(MSM377_EDWARDS | MSM377_GLV))
+        return set_error(MSM377_EINVAL, "msm_g1_set_window_table: flags 0x%x (only EDWARDS and GLV select a table)",
+                         flags);
     for (int k = 0; k < len; ++k)
         if (c_by_log2n[k] != 0 && (c_by_log2n[k] < 2 || c_by_log2n[k] > 20))
             return set_error(MSM377_EINVAL, "msm_g1_set_window_table: c = %d at log2 n = %d", c_by_log2n[k], k);
-    for (int k = 0; k < 32; ++k) g_ctable[k].store(k < len ? c_by_log2n[k] : 0, std::memory_order_relaxed);
+    const int mode = table_mode(flags);
+    for (int k = 0; k < 32; ++k)
+        g_ctable[mode][k].store(k < len ? c_by_log2n[k] : 0, std::memory_order_relaxed);
     return MSM377_OK;
 }
 
@@ -703,14 +1042,27 @@ extern "C" size_t msm_g1_workspace_bytes(size_t n, const msm_opts* opts) {
     return p.total;
 }
 
-extern "C" int msm_points_prepare(const uint32_t* points_std, size_t n, uint32_t* out, void* stream) {
+extern "C" size_t msm_points_prepared_bytes(size_t n, uint32_t flags) {
+    if (flags & ~(MSM377_EDWARDS | MSM377_GLV)) return 0;
+    if (n >= (1ull << 30)) return 0;
+    return stored_count(n, flags) * 16 * (size_t)stored_vec(flags);
+}
+
+extern "C" int msm_points_prepare_ex(const uint32_t* points_std, size_t n, uint32_t* out, uint32_t flags,
+                                     void* stream) {
+    if (flags & ~(MSM377_EDWARDS | MSM377_GLV))
+        return set_error(MSM377_EINVAL, "msm_points_prepare_ex: flags 0x%x (only EDWARDS and GLV)", flags);
+    if (n >= (1ull << 30)) return set_error(MSM377_EINVAL, "msm_points_prepare_ex: n = %zu too large", n);
     if (n == 0) return MSM377_OK;
     if (!points_std || !out || !aligned(points_std, 16) || !aligned(out, 16))
-        return set_error(MSM377_EINVAL, "msm_points_prepare: null or non-16-byte-aligned pointer");
-    k_prepare<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(
-        reinterpret_cast<const uint4*>(points_std), reinterpret_cast<uint4*>(out), n);
-    note_launches(1);
-    return check_launch("msm_points_prepare");
+        return set_error(MSM377_EINVAL, "msm_points_prepare_ex: null or non-16-byte-aligned pointer");
+    launch_prepare(reinterpret_cast<const uint4*>(points_std), reinterpret_cast<uint4*>(out), n, flags,
+                   as_stream(stream));
+    return check_launch("msm_points_prepare_ex");
+}
+
+extern "C" int msm_points_prepare(const uint32_t* points_std, size_t n, uint32_t* out, void* stream) {
+    return msm_points_prepare_ex(points_std, n, out, 0, stream);
 }
 
 namespace {
@@ -725,14 +1077,14 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     const uint4* pts = reinterpret_cast<const uint4*>(points);
     if (!(opts->flags & MSM377_POINTS_PREPARED)) {
         uint4* prep = at<uint4>(workspace, p.off_points);
-        k_prepare<<<grid_for(n, 256), 256, 0, s>>>(pts, prep, n);
-        note_launches(1);
+        launch_prepare(pts, prep, n, opts->flags, s);
         pts = prep;
     }
+    const size_t np = p.np;
     uint32_t* keys[2] = {at<uint32_t>(workspace, p.off_keys0), at<uint32_t>(workspace, p.off_keys1)};
     uint32_t* vals[2] = {at<uint32_t>(workspace, p.off_vals0), at<uint32_t>(workspace, p.off_vals1)};
     k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.W,
-                                              p.sgn, p.bits, keys[0], vals[0], status);
+                                              p.sgn, p.user_bits, p.glv, keys[0], vals[0], status);
     note_launches(1);
     uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
     uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
@@ -740,10 +1092,10 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     for (int pass = 0; pass < p.passes; ++pass) {
         int shift = 8 * pass;
         dim3 g((unsigned)p.tiles, (unsigned)p.W);
-        k_sort_hist<<<g, kSortThreads, 0, s>>>(keys[cur], n, shift, p.tiles, hist);
+        k_sort_hist<<<g, kSortThreads, 0, s>>>(keys[cur], np, shift, p.tiles, hist);
         k_sort_scan_tiles<<<dim3(kRadix, p.W), kSortThreads, 0, s>>>(hist, p.tiles, dtot);
         k_sort_scan_digits<<<p.W, kSortThreads, 0, s>>>(dtot);
-        k_sort_scatter<<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n,
+        k_sort_scatter<<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np,
                                                   shift, p.tiles, hist, dtot);
         note_launches(4);
         cur ^= 1;
@@ -759,7 +1111,7 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     a.tail = at<uint4>(workspace, p.off_tail);
     a.headflag = at<uint32_t>(workspace, p.off_headflag);
     a.tailkey = at<uint32_t>(workspace, p.off_tailkey);
-    a.n = n;
+    a.n = np;
     a.cpw = p.cpw;
     a.Bp = p.Bp;
     a.K = p.K;
@@ -770,7 +1122,8 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
 
 // Phase 5-7 of one MSM on stream s: partial merges, bucket reduction, window
 // combination and normalisation into out.
-int enqueue_tail(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s) {
+template <class M>
+int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s) {
     uint4* Y = at<uint4>(workspace, p.off_Y);
     uint4* V = at<uint4>(workspace, p.off_V);
     uint4* P0 = at<uint4>(workspace, p.off_P0);
@@ -783,35 +1136,50 @@ int enqueue_tail(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out
     k_merge_scan<<<p.W, kScanThreads, 0, s>>>(a, start);
     note_launches(1);
     for (uint32_t d = 1; d < p.cpw; d <<= 1) {
-        k_merge_round<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d);
+        k_merge_round<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d);
         note_launches(1);
     }
-    k_merge_final<<<grid_for(nchunks, 128), 128, 0, s>>>(a);
+    k_merge_final<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a);
     note_launches(1);
     // 6. bucket reduction, all windows
     const size_t WG = (size_t)p.W * p.G;
-    k_reduce_segments<<<grid_for(WG, 128), 128, 0, s>>>(a.buckets, p.Bp, p.L, 0, p.W, p.G, Y, V);
+    k_reduce_segments<M><<<grid_for(WG, 128), 128, 0, s>>>(a.buckets, p.Bp, p.L, 0, p.W, p.G, Y, V);
     const size_t nseg = (size_t)p.W * (p.logG + 1);
-    k_bitsums<<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, p.W, p.G, p.logG, p.Q, P0);
+    k_bitsums<M><<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, p.W, p.G, p.logG, p.Q, P0);
     note_launches(2);
     uint32_t m = p.Q;
     uint4* zin = P0;
     uint4* zout = P1;
     while (m > 1) {
         const uint32_t F = m >= 8 ? 8 : m;
-        k_sum_segments<<<grid_for(nseg * (m / F), 128), 128, 0, s>>>(zin, nseg, m, F, zout);
+        k_sum_segments<M><<<grid_for(nseg * (m / F), 128), 128, 0, s>>>(zin, nseg, m, F, zout);
         note_launches(1);
         m /= F;
         uint4* tmp = zin;
         zin = zout;
         zout = tmp;
     }
-    k_window_horner<<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+    k_window_horner<M><<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
     note_launches(1);
     // 7. window combination and normalisation
-    k_chain<<<1, 32, 0, s>>>(S, p.W, 0, p.W, p.c, accp, out);
+    k_chain<M><<<1, 32, 0, s>>>(S, p.W, 0, p.W, p.c, accp, out);
     note_launches(1);
     return check_launch("msm tail");
+}
+
+int enqueue_tail(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s) {
+    return p.edw ? enqueue_tail_m<ModelEdwards>(p, a, workspace, out, s)
+                 : enqueue_tail_m<ModelXyzz>(p, a, workspace, out, s);
+}
+
+int enqueue_accumulate(const Plan& p, const AccArgs& a, cudaStream_t s) {
+    const unsigned grid = grid_for((size_t)p.W * p.cpw, 128);
+    if (p.edw)
+        k_accumulate<ModelEdwards><<<grid, 128, 0, s>>>(a);
+    else
+        k_accumulate<ModelXyzz><<<grid, 128, 0, s>>>(a);
+    note_launches(1);
+    return check_launch("msm accumulate");
 }
 
 // Library-owned helper streams for batched calls, per device, created once.
@@ -819,7 +1187,7 @@ constexpr int kMaxDevices = 64;
 constexpr int kAuxStreams = 16;
 struct DeviceAux {
     bool ready = false;
-    int sms = 0, acc_blocks_per_sm = 0;
+    int sms = 0, acc_blocks_per_sm[2] = {0, 0};  // k_accumulate_batched per model
     cudaStream_t st[kAuxStreams];
     cudaEvent_t fork, done[kAuxStreams];
 };
@@ -834,8 +1202,12 @@ int device_aux(DeviceAux** out) {
     DeviceAux& a = g_aux[dev];
     if (!a.ready) {
         MSM_CUDA_TRY(cudaDeviceGetAttribute(&a.sms, cudaDevAttrMultiProcessorCount, dev));
-        MSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a.acc_blocks_per_sm, k_accumulate_batched, 128, 0));
-        if (a.acc_blocks_per_sm < 1) a.acc_blocks_per_sm = 1;
+        MSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a.acc_blocks_per_sm[0],
+                                                                   k_accumulate_batched<ModelXyzz>, 128, 0));
+        MSM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a.acc_blocks_per_sm[1],
+                                                                   k_accumulate_batched<ModelEdwards>, 128, 0));
+        for (int m = 0; m < 2; ++m)
+            if (a.acc_blocks_per_sm[m] < 1) a.acc_blocks_per_sm[m] = 1;
         for (int i = 0; i < kAuxStreams; ++i) {
             MSM_CUDA_TRY(cudaStreamCreateWithFlags(&a.st[i], cudaStreamNonBlocking));
             MSM_CUDA_TRY(cudaEventCreateWithFlags(&a.done[i], cudaEventDisableTiming));
@@ -892,9 +1264,7 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     int r = enqueue_head(p, points, scalars, workspace, opts, s, &a);
     if (r) return r;
     if (prof) profile_mark(s);
-    k_accumulate<<<grid_for((size_t)p.W * p.cpw, 128), 128, 0, s>>>(a);
-    note_launches(1);
-    r = check_launch("msm_g1 accumulate");
+    r = enqueue_accumulate(p, a, s);
     if (r) return r;
     if (prof) profile_mark(s);
     r = enqueue_tail(p, a, workspace, out, s);
@@ -985,8 +1355,12 @@ extern "C" int msm_g1_batched(const msm_job* jobs, size_t njobs, void* workspace
     // every job's bucket accumulation in one persistent launch
     if (b.njobs > 0) {
         b.counter = counter;
-        const unsigned grid = (unsigned)(aux->sms * aux->acc_blocks_per_sm);
-        k_accumulate_batched<<<grid, 128, 0, s>>>(b);
+        const int edw = (opts->flags & MSM377_EDWARDS) ? 1 : 0;
+        const unsigned grid = (unsigned)(aux->sms * aux->acc_blocks_per_sm[edw]);
+        if (edw)
+            k_accumulate_batched<ModelEdwards><<<grid, 128, 0, s>>>(b);
+        else
+            k_accumulate_batched<ModelXyzz><<<grid, 128, 0, s>>>(b);
         note_launches(1);
         r = check_launch("msm_g1_batched accumulate");
         if (r) return r;

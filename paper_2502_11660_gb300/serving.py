@@ -11,7 +11,8 @@ a request's arrival to the host seeing its completion event.
 
 Scalars are drawn on the device per request from the request's own seed (like
 witness-derived scalars that already live on the GPU in a prover); every GPU
-step is a call into libmsm377.
+step is a call into libmsm377. With GLV the stored set interleaves P_i and
+phi(P_i), so a request's slice is still one contiguous range of rows.
 """
 from __future__ import annotations
 
@@ -53,18 +54,23 @@ def device_scalars(n: int, seed: int, device) -> torch.Tensor:
 
 
 class ResidentSets:
-    """Resident point sets P_i = s_i G in prepared (Montgomery) form on the device."""
+    """Resident point sets P_i = s_i G in prepared form on the device (XYZZ Montgomery
+    affine, or the Edwards stored form; with GLV interleaved with phi(P_i))."""
 
-    def __init__(self, seeds: list[np.ndarray], device="cuda"):
+    def __init__(self, seeds: list[np.ndarray], device="cuda", edwards: bool = False, glv: bool = False):
+        self.edwards, self.glv = edwards, glv
         self.sets = []
         for s in seeds:
             pts = g1_generator_mul(to_device(s, device))
-            self.sets.append(msm_points_prepare(pts))
+            self.sets.append(msm_points_prepare(pts, edwards=edwards, glv=glv))
             del pts
         torch.cuda.synchronize(device)
 
     def slice(self, set_id: int, offset: int, n: int) -> torch.Tensor:
-        return self.sets[set_id][offset:offset + n]
+        st = self.sets[set_id]
+        if not self.glv:
+            return st[offset:offset + n]
+        return st[2 * offset:2 * (offset + n)]   # rows P_i, phi(P_i) interleaved
 
 
 class MsmServer:
@@ -82,17 +88,20 @@ class MsmServer:
     def footprint(self, n: int) -> int:
         from . import _opts, lib
         import ctypes
-        o = _opts(self.c, True, 253, True)
+        o = _opts(self.c, True, 253, True, edwards=self.sets.edwards, glv=self.sets.glv)
         return int(lib().msm_g1_workspace_bytes(n, ctypes.byref(o))) + 32 * n + 96
 
     def _launch(self, req: Request, slot: int):
         st = self.streams[slot]
         with torch.cuda.stream(st):
             sc = device_scalars(req.n, req.seed, self.device)
-            ws = msm_g1_workspace(req.n, c=self.c, scalar_bits=253, prepared=True, device=self.device)
+            ed, gl = self.sets.edwards, self.sets.glv
+            ws = msm_g1_workspace(req.n, c=self.c, scalar_bits=253, prepared=True, device=self.device,
+                                  edwards=ed, glv=gl)
             out = torch.empty(24, dtype=torch.int32, device=self.device)
-            msm_g1(self.sets.slice(req.set_id, req.offset, req.n), sc, out=out, workspace=ws, c=self.c,
-                   scalar_bits=253, prepared=True, stream=st)
+            pts = self.sets.slice(req.set_id, req.offset, req.n)
+            msm_g1(pts, sc, out=out, workspace=ws, c=self.c, scalar_bits=253, prepared=True, stream=st,
+                   edwards=ed, glv=gl)
             ev = torch.cuda.Event()
             ev.record(st)
         return {"req": req, "slot": slot, "event": ev, "out": out, "tensors": (sc, ws),

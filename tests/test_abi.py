@@ -95,3 +95,64 @@ def test_window_table_install_and_reject():
     finally:
         autotune.clear()
     assert pkg.msm_g1_default_c(1 << 20) == base
+
+
+def _const_limbs(src, name):
+    m = re.search(name + r"\[[^\]]*\] = \{([^}]*)\}", src)
+    words = [w.strip().rstrip("u") for w in m.group(1).split(",") if w.strip()]
+    return sum(int(w, 16) << (32 * k) for k, w in enumerate(words))
+
+
+def test_edwards_and_glv_constants_match_the_oracle():
+    """The Edwards map constants (ed.cuh) and the GLV constants (msm.cu) agree with
+    the oracle's own derivations (Montgomery form x 2^384 mod p for field elements)."""
+    from oracle import edwards, fq, glv
+    R = 1 << 384
+    ed_src = open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", "ed.cuh")).read()
+    assert _const_limbs(ed_src, "kK") == edwards.K * R % fq.P
+    assert _const_limbs(ed_src, "kS") == edwards.S * R % fq.P
+    assert _const_limbs(ed_src, "kGamma") == edwards.GAMMA * R % fq.P
+    assert _const_limbs(ed_src, "kC1") == edwards.GAMMA * fq.inv(edwards.S) % fq.P * R % fq.P
+    msm_src = open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", "msm.cu")).read()
+    assert _const_limbs(msm_src, "kBeta") == glv.BETA * R % fq.P
+    assert _const_limbs(msm_src, "kLambda") == glv.LAMBDA
+    assert _const_limbs(msm_src, "kMu") == (1 << 256) // glv.LAMBDA
+    rows = re.search(r"kR8\[4\]\[8\] = \{(.*?)\};", msm_src, flags=re.S).group(1)
+    mults = [sum(int(w.strip().rstrip("u"), 16) << (32 * k) for k, w in enumerate(r.split(",")))
+             for r in re.findall(r"\{([^}]*)\}", rows)]
+    assert mults == [8 * fq.R, 4 * fq.R, 2 * fq.R, fq.R]
+
+
+def test_stored_point_sizes_and_mode_flags():
+    import paper_2502_11660_gb300 as pkg
+    L = pkg.lib()
+    n = 1000
+    assert L.msm_points_prepared_bytes(n, 0) == 96 * n
+    assert L.msm_points_prepared_bytes(n, pkg.EDWARDS) == 144 * n
+    assert L.msm_points_prepared_bytes(n, pkg.GLV) == 2 * 96 * n
+    assert L.msm_points_prepared_bytes(n, pkg.EDWARDS | pkg.GLV) == 2 * 144 * n
+    assert L.msm_points_prepared_bytes(n, pkg.PROFILE) == 0
+    assert L.msm_points_prepare_ex(None, 10, None, pkg.PROFILE, None) == -1
+    assert L.msm_points_prepare_ex(None, 0, None, pkg.GLV, None) == 0
+    # GLV halves the windows: key/value buffers of 2n items x W/2 windows, plus 2n stored points
+    plain = L.msm_g1_workspace_bytes(1 << 16, ctypes.byref(pkg._opts(c=12, scalar_bits=253)))
+    split = L.msm_g1_workspace_bytes(1 << 16, ctypes.byref(pkg._opts(c=12, scalar_bits=253, glv=True)))
+    assert plain > 0 and split > 0
+    assert pkg.msm_g1_default_c(1 << 20, glv=True) == pkg.msm_g1_default_c(1 << 21)
+
+
+def test_window_tables_are_per_mode():
+    import paper_2502_11660_gb300 as pkg
+    from paper_2502_11660_gb300 import autotune
+    base = pkg.msm_g1_default_c(1 << 20)
+    base_e = pkg.msm_g1_default_c(1 << 20, edwards=True, glv=True)
+    try:
+        autotune.install([0] * 20 + [11], edwards=True, glv=True)
+        assert pkg.msm_g1_default_c(1 << 20, edwards=True, glv=True) == 11
+        assert pkg.msm_g1_default_c(1 << 20) == base
+        assert pkg.msm_g1_default_c(1 << 20, edwards=True) != 11 or base == 11
+        arr = (ctypes.c_int32 * 1)(5)
+        assert pkg.lib().msm_g1_set_window_table(arr, 1, pkg.PROFILE) == -1
+    finally:
+        autotune.clear(edwards=True, glv=True)
+    assert pkg.msm_g1_default_c(1 << 20, edwards=True, glv=True) == base_e

@@ -1,0 +1,183 @@
+"""GPU parity of the two alternative schedules of msm_g1 against the closed form and
+the oracle: the paper's twisted Edwards model (MSM377_EDWARDS, Sec. II-D) and the
+GLV split (MSM377_GLV), alone and together, for single, prepared, host-buffer and
+batched calls. Results are exact affine points, compared bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import edwards, fq, g1, glv
+from tests.util import closed_form_limbs, msm_inputs
+
+pytestmark = pytest.mark.gpu
+
+pkg = pytest.importorskip("paper_2502_11660_gb300")
+
+MODES = [(True, False), (False, True), (True, True)]
+MODE_IDS = ["edwards", "glv", "edwards+glv"]
+R384 = 1 << 384
+
+
+def run(pts, sc, **kw):
+    out = pkg.msm_g1(pkg.to_device(pts), pkg.to_device(sc), **kw)
+    torch.cuda.synchronize()
+    return g1.from_limbs(pkg.to_host(out))
+
+
+@pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 255, 1000, 2049])
+@pytest.mark.parametrize("c,signed", [(4, True), (8, True), (7, False)])
+def test_small_n(edw, split, n, c, signed):
+    a, s, pts = msm_inputs(n, tag=100 + n)
+    want = closed_form_limbs(s, a)
+    assert run(pts, a, c=c, signed=signed, scalar_bits=253, edwards=edw, glv=split) == want
+
+
+@pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)
+def test_edge_scalars_identity_points_duplicates(edw, split):
+    n = 700
+    a, s, pts = msm_inputs(n, tag=7)
+    a, s, pts = a.copy(), s.copy(), pts.copy()
+    lam = glv.LAMBDA
+    a[0:10] = 0
+    for i, v in enumerate([fq.R - 1, 1, lam - 1, lam, lam + 1, lam * lam, fq.R - lam, 2 ** 127 - 1]):
+        a[10 + i] = synth.int_to_limbs(v, 8)
+    pts[20] = pts[21]
+    s[20] = s[21]
+    pts[30] = pts[31]
+    pts[30, 12:] = synth.int_to_limbs((fq.P - synth.limbs_to_int(pts[31, 12:])) % fq.P, 12)
+    s[30] = synth.int_to_limbs((fq.R - synth.limbs_to_int(s[31])) % fq.R, 8)
+    a[30] = a[31]
+    pts[40] = 0            # the identity, encoded (0, 0): its seed is 0
+    s[40] = 0
+    want = closed_form_limbs(s, a)
+    for c, sg in [(5, True), (9, False), (12, True)]:
+        assert run(pts, a, c=c, signed=sg, scalar_bits=253, edwards=edw, glv=split) == want
+
+
+@pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)
+def test_full_width_scalars_reduce_mod_r(edw, split):
+    """Scalars up to 2^256 - 1: on subgroup points the sum equals the one with scalars mod r."""
+    n = 300
+    _, s, pts = msm_inputs(n, tag=9)
+    a = synth.scalars_full(55, n)
+    a[0] = 0xFFFFFFFF
+    want = closed_form_limbs(s, a)
+    for sg in (True, False):
+        assert run(pts, a, c=9, signed=sg, edwards=edw, glv=split) == want
+
+
+@pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)
+def test_heavy_bucket(edw, split):
+    n = 5000
+    a, s, pts = msm_inputs(n, tag=8)
+    a = np.tile(a[:1], (n, 1))
+    want = closed_form_limbs(s, a)
+    for c in (6, 16):
+        assert run(pts, a, c=c, signed=True, scalar_bits=253, edwards=edw, glv=split) == want
+
+
+@pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)
+def test_prepared_host_and_range_check(edw, split):
+    n = 3000
+    a, s, pts = msm_inputs(n, tag=12)
+    want = closed_form_limbs(s, a)
+    prep = pkg.msm_points_prepare(pkg.to_device(pts), edwards=edw, glv=split)
+    assert prep.numel() * 4 == pkg.msm_points_prepared_bytes(n, edw, split)
+    out = pkg.msm_g1(prep, pkg.to_device(a), c=10, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == want
+    host = pkg.msm_g1_host(pts, a, c=10, scalar_bits=253, edwards=edw, glv=split)
+    assert g1.from_limbs(host) == want
+    bad = a.copy()
+    bad[3, 7] = 0x80000000
+    ws = pkg.msm_g1_workspace(n, c=5, scalar_bits=253, edwards=edw, glv=split)
+    pkg.msm_g1(pkg.to_device(pts), pkg.to_device(bad), workspace=ws, c=5, scalar_bits=253, edwards=edw,
+               glv=split)
+    assert pkg.msm_g1_status(ws) == -5
+
+
+def _mont_ints(block: np.ndarray) -> list[int]:
+    """Rows of 12 u32 (Montgomery form) -> standard-form ints."""
+    rinv = pow(R384, -1, fq.P)
+    return [synth.limbs_to_int(row) * rinv % fq.P for row in block]
+
+
+def test_stored_forms_match_the_oracle_maps():
+    """The prepared points themselves: Edwards (x, y, k x y) of the oracle's map, and
+    the GLV half phi(P) = (beta x, y), element by element."""
+    n = 257
+    _, s, pts = msm_inputs(n, tag=13)
+    pts = pts.copy()
+    pts[5] = 0                                    # identity -> Edwards (0, 1, 0)
+    dp = pkg.to_device(pts)
+    ed_st = pkg.to_host(pkg.msm_points_prepare(dp, edwards=True)).reshape(n, 36)
+    gl_st = pkg.to_host(pkg.msm_points_prepare(dp, glv=True)).reshape(2 * n, 24)
+    both = pkg.to_host(pkg.msm_points_prepare(dp, edwards=True, glv=True)).reshape(2 * n, 36)
+    torch.cuda.synchronize()
+    for i in range(n):
+        P = None if i == 5 else g1.from_limbs(pts[i])
+        e = edwards.from_weierstrass(P)
+        want = list(edwards.stored_point(e))
+        assert _mont_ints(ed_st[i].reshape(3, 12)) == want
+        ph = glv.phi(P)
+        assert _mont_ints(gl_st[2 * i].reshape(2, 12)) == ([0, 0] if P is None else list(P))
+        assert _mont_ints(gl_st[2 * i + 1].reshape(2, 12)) == ([0, 0] if ph is None else list(ph))
+        assert _mont_ints(both[2 * i].reshape(3, 12)) == want
+        assert _mont_ints(both[2 * i + 1].reshape(3, 12)) == list(
+            edwards.stored_point(edwards.from_weierstrass(ph)))
+
+
+@pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)
+def test_full_size_2e20(edw, split):
+    n = 1 << 20
+    a, s, pts = msm_inputs(n, tag=2)
+    want = closed_form_limbs(s, a)
+    prep = pkg.msm_points_prepare(pkg.to_device(pts), edwards=edw, glv=split)
+    da = pkg.to_device(a)
+    ws = pkg.msm_g1_workspace(n, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+    for _ in range(2):
+        out = pkg.msm_g1(prep, da, workspace=ws, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+        torch.cuda.synchronize()
+        assert g1.from_limbs(pkg.to_host(out)) == want
+    assert pkg.msm_g1_status(ws) == 0
+
+
+def test_full_size_2e22_edwards_glv():
+    n = 1 << 22
+    a, s, pts = msm_inputs(n, tag=2)
+    want = closed_form_limbs(s, a)
+    prep = pkg.msm_points_prepare(pkg.to_device(pts), edwards=True, glv=True)
+    out = pkg.msm_g1(prep, pkg.to_device(a), scalar_bits=253, prepared=True, edwards=True, glv=True)
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == want
+
+
+@pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)
+def test_batched_and_graph(edw, split):
+    sizes = [0, 1, 7, 333, 2049, 5000, 64]
+    cs = [0, 0, 5, 0, 10, 12, 3]
+    data = [msm_inputs(n, tag=77000 + i) for i, n in enumerate(sizes)]
+    prep = [pkg.msm_points_prepare(pkg.to_device(p), edwards=edw, glv=split) for _, _, p in data]
+    scs = [pkg.to_device(a) for a, _, _ in data]
+    kw = dict(c_list=cs, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+    outs = pkg.msm_g1_batched(prep, scs, **kw)
+    torch.cuda.synchronize()
+    for i, o in enumerate(outs):
+        assert g1.from_limbs(pkg.to_host(o)) == closed_form_limbs(data[i][1], data[i][0]), f"job {i}"
+    ws = pkg.msm_g1_batched_workspace(prep, c_list=cs, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        pkg.msm_g1_batched(prep, scs, outs=outs, workspace=ws, stream=st, **kw)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        pkg.msm_g1_batched(prep, scs, outs=outs, workspace=ws, stream=st, **kw)
+    new = [synth.scalars(900 + i, n) for i, n in enumerate(sizes)]
+    for d, h in zip(scs, new):
+        d.copy_(pkg.to_device(h))
+    g.replay()
+    torch.cuda.synchronize()
+    for i, o in enumerate(outs):
+        assert g1.from_limbs(pkg.to_host(o)) == closed_form_limbs(data[i][1], new[i]), f"job {i}"

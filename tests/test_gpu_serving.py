@@ -60,3 +60,15 @@ def test_poisson_stream_and_footprint_admission(sets):
     assert rep2["requests"] == 10 and rep2["max_footprint_bytes"] <= tight.mem_budget
     for r in reqs[:10]:
         assert np.array_equal(rep2["results"][r.rid], rep["results"][r.rid])
+
+
+def test_edwards_glv_sets_serve_the_same_results(sets):
+    """Resident sets in the Edwards stored form with the GLV rows interleaved: slices
+    of them give the same exact results as the XYZZ sets."""
+    seeds, rs = sets
+    rs2 = serving.ResidentSets(seeds, edwards=True, glv=True)
+    reqs = _requests(12, tag=73)
+    a = serving.MsmServer(rs, slots=4).run(reqs, realtime=False)
+    b = serving.MsmServer(rs2, slots=4).run(reqs, realtime=False)
+    for r in reqs:
+        assert np.array_equal(a["results"][r.rid], b["results"][r.rid]), f"request {r.rid}"
