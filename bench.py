@@ -160,10 +160,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# The source the bucket-accumulation kernel is compiled from: the field and curve
+# headers and three sections of msm.cu (memory I/O, curve models, stages 4-5).
+ACC_SECTIONS = (("// ---------------------------------------------------------------- memory I/O",
+                 "// Second operand of ec::add_q()"),
+                ("// ---------------------------------------------------------------- curve models",
+                 "// ---------------------------------------------------------------- stage 1"),
+                ("// ---------------------------------------------------------------- stages 4-5",
+                 "// Batched MSMs:"))
+
+
 def kernel_hash() -> str:
+    csrc = os.path.join(ROOT, "paper_2502_11660_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("fq.cuh", "ec.cuh", "ed.cuh", "msm.cu"):
-        h.update(open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", f), "rb").read())
+    for f in ("fq.cuh", "ec.cuh", "ed.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    src = open(os.path.join(csrc, "msm.cu")).read()
+    for start, end in ACC_SECTIONS:
+        a = src.index(start)
+        h.update(src[a:src.index(end, a)].encode())
     return h.hexdigest()[:16]
 
 
