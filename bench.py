@@ -409,6 +409,8 @@ def run_ours(args):
         del hws
         # standalone batched arithmetic at 2^24 (Fq Montgomery multiplications, mixed PADDs)
         result["batch_ops"] = batch_ops(pkg, torch, dev, stream)
+        # the paper's dependent-chain experiment: 2^18 points summed in order
+        result["latency"] = latency_chain(pkg, torch, dev, stream, pts_std)
         # 64 MSMs of log-uniform n in [2^10, 2^20]: one graph launch vs 64 sequential calls
         result["batched_msm"] = batched_msm(pkg, torch, dev, edw, gl)
         # 2000 Poisson requests over 8 resident sets of 2^22 points
@@ -505,6 +507,25 @@ def serve(pkg, torch, dev, edw=False, gl=False, nreq=2000, nsets=8, set_size=1 <
             "scalars": "fresh per request, drawn on the device from the request seed"}
 
 
+def latency_chain(pkg, torch, dev, stream, pts_std, n=1 << 18):
+    """Microseconds per mixed PADD of a dependent chain (each addition waits for the
+    previous one) over the first n resident points, per model and lane count."""
+    src = pts_std[:n]
+    res = {"n": n, "paper_context_us": {"AIE med-ind (VCK190)": 1.05, "VCK190 CPU (GMP)": 9.69}}
+    for name, edw, lanes in (("xyzz_1_lane", False, 1), ("edwards_1_lane", True, 1), ("edwards_4_lanes", True, 4)):
+        st = pkg.msm_points_prepare(src, edwards=edw)
+        out = torch.empty(24, dtype=torch.int32, device=dev)
+        pkg.padd_chain(st[:1024], 1024, edwards=edw, lanes=lanes, out=out, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.padd_chain(st, n, edwards=edw, lanes=lanes, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name + "_us_per_padd"] = 1e3 * e0.elapsed_time(e1) / n
+    return res
+
+
 def batch_ops(pkg, torch, dev, stream):
     n = 1 << 24
     a, b = synth.workloads.fq_pairs(n, tag=1)
@@ -524,6 +545,13 @@ def batch_ops(pkg, torch, dev, stream):
         return e0.elapsed_time(e1) / reps
 
     ms_mul = timed(lambda: pkg.fq_mul_batch(mA, mB, out=out, form=pkg.FORM_MONTGOMERY))
+    # the alternative multiplications on the same operands (variants: Sec. III-C Barrett,
+    # Karatsuba top level, radix-2^24 carry-save), one kernel each
+    variants = {}
+    for name, v in (("cios", pkg.FQMUL_CIOS), ("barrett", pkg.FQMUL_BARRETT),
+                    ("karatsuba", pkg.FQMUL_KARATSUBA), ("carrysave", pkg.FQMUL_CARRYSAVE)):
+        ms_v = timed(lambda v=v: pkg.fq_mul_batch_variant(mA, mB, v, out=out))
+        variants[name] = {"ms_2^24": ms_v, "mul_per_s": n / (ms_v / 1e3)}
     del mA, mB, out
     # mixed PADDs on a pool of 2^16 device-generated points, XYZZ accumulators with ZZ = ZZZ = R
     pool = pkg.g1_generator_mul(pkg.to_device(synth.scalars(3, 1 << 16), dev))
@@ -542,7 +570,7 @@ def batch_ops(pkg, torch, dev, stream):
     del P, Q, i1, i2
     outp = torch.empty_like(acc)
     ms_padd = timed(lambda: pkg.padd_batch(acc, q, out=outp, form=pkg.FORM_MONTGOMERY), reps=3)
-    return {"fq_mul_per_s": n / (ms_mul / 1e3), "fq_mul_ms_2^24": ms_mul,
+    return {"fq_mul_per_s": n / (ms_mul / 1e3), "fq_mul_ms_2^24": ms_mul, "fq_mul_variants": variants,
             "fq_mul_hbm_GBps": n * 144 / (ms_mul / 1e3) / 1e9,
             "padd_per_s": n / (ms_padd / 1e3), "padd_ms_2^24": ms_padd,
             "padd_products_per_s": n * PRODUCTS["madd"] / (ms_padd / 1e3)}

@@ -67,6 +67,26 @@ int fq_mul_batch(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, 
 
 /* Standard <-> Montgomery conversion of n elements, SoA [12][n]; out may alias in. */
 int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
+/* Alternative multiplications, for comparison with fq_mul_batch's Montgomery CIOS
+ * (same layout: structure-of-arrays [12][n], 16-byte aligned device arrays,
+ * operands in [0, p), result canonical in [0, p)). The MSM does not use them.
+ *   MSM377_FQMUL_CIOS      a b 2^-384 mod p, word-serial Montgomery (the library's)
+ *   MSM377_FQMUL_BARRETT   a b mod p on standard-form operands: the paper's Barrett
+ *                          reduction (Sec. III-C), k = 377, mu = floor(2^754 / p),
+ *                          remainder in [0, 3p) then at most two subtractions of p
+ *   MSM377_FQMUL_KARATSUBA a b 2^-384 mod p, a b by one Karatsuba level over 192-bit
+ *                          halves with schoolbook leaves (Sec. V-C), then
+ *                          word-by-word Montgomery reduction
+ *   MSM377_FQMUL_CARRYSAVE a b 2^-384 mod p on 16 digits of 24 bits with 64-bit
+ *                          column sums and deferred carries (Sec. III-B, III-D)
+ * MSM377_EINVAL for another variant. */
+#define MSM377_FQMUL_CIOS 0
+#define MSM377_FQMUL_BARRETT 1
+#define MSM377_FQMUL_KARATSUBA 2
+#define MSM377_FQMUL_CARRYSAVE 3
+int fq_mul_batch_variant(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, int variant,
+                         void *stream);
+
 int fq_from_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
 
 /* ------------------------------------------------------------------------
@@ -243,6 +263,19 @@ int msm_g1_host(const uint32_t *points_host, const uint32_t *scalars_host, size_
 #define MSM377_NOALLOC_SCRATCH_BYTES (64u << 20)
 int msm_g1_noalloc(const uint32_t *points, const uint32_t *scalars, size_t n, uint32_t *out,
                    const msm_opts *opts);
+
+/* ------------------------------------------------------------------------
+ * Dependent-chain latency (Sec. V-A, the sequential sum of a point stream):
+ * out = P_0 + P_1 + ... + P_{n-1} added strictly in order, each mixed PADD waiting
+ * for the previous one, so time / n is the latency of one PADD.
+ * points: device, the stored form of msm_points_prepare_ex(points, n, ., flags)
+ *   with flags = 0 (XYZZ model, Montgomery affine) or MSM377_EDWARDS (no GLV).
+ * lanes: 1 (one thread performs every multiplication) or 4 (Edwards only: the
+ *   independent multiplications of each addition run on four lanes of a warp, the
+ *   analogue of the paper's multi-tile med-ind mapping).
+ * out: device, 24 u32, affine standard form, (0, 0) for O. Asynchronous on stream.
+ * MSM377_EINVAL for other flags or lanes. The Edwards model needs subgroup points. */
+int padd_chain(const uint32_t *points, size_t n, uint32_t *out, uint32_t flags, int lanes, void *stream);
 
 /* Stage timings of the most recent msm_g1 call made with MSM377_PROFILE, in
  * milliseconds, from CUDA events recorded on the caller's stream:

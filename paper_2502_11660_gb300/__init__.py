@@ -33,7 +33,8 @@ __all__ = [
     "msm_g1", "msm_g1_workspace", "msm_g1_host", "msm_g1_status", "msm_g1_default_c",
     "imad_probe", "lib", "last_error", "profile_last", "launch_count", "MSM_STAGES", "PROFILE",
     "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace", "EDWARDS", "GLV",
-    "msm_points_prepared_bytes",
+    "msm_points_prepared_bytes", "padd_chain", "fq_mul_batch_variant", "FQMUL_CIOS", "FQMUL_BARRETT",
+    "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE",
 ]
 
 
@@ -69,6 +70,19 @@ def fq_mul_batch(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = No
     out = torch.empty_like(a) if out is None else out
     _check_dev(a, b, out)
     check(lib().fq_mul_batch(_p(a), _p(b), _p(out), n, form, _s(stream)))
+    return out
+
+
+FQMUL_CIOS, FQMUL_BARRETT, FQMUL_KARATSUBA, FQMUL_CARRYSAVE = 0, 1, 2, 3
+
+
+def fq_mul_batch_variant(a: torch.Tensor, b: torch.Tensor, variant: int, out: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """[12][n] operands in [0, p): BARRETT gives a b mod p, the others a b 2^-384 mod p."""
+    n = a.shape[-1]
+    out = torch.empty_like(a) if out is None else out
+    _check_dev(a, b, out)
+    check(lib().fq_mul_batch_variant(_p(a), _p(b), _p(out), n, int(variant), _s(stream)))
     return out
 
 
@@ -270,6 +284,17 @@ def profile_last() -> dict:
 
 def launch_count() -> int:
     return int(lib().msm377_launch_count())
+
+
+def padd_chain(stored: torch.Tensor, n: int, edwards: bool = False, lanes: int = 1, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """P_0 + ... + P_{n-1} as one dependent chain of mixed PADDs over stored points
+    (msm_points_prepare(..., edwards=edwards)); lanes = 4 spreads each Edwards PADD over four lanes."""
+    out = torch.empty(24, dtype=torch.int32, device=stored.device) if out is None else out
+    _check_points(stored, n, True, edwards, False)
+    _check_dev(stored, out)
+    check(lib().padd_chain(_p(stored), n, _p(out), EDWARDS if edwards else 0, int(lanes), _s(stream)))
+    return out
 
 
 def imad_probe(iters: int = 20000, stream=None) -> float:

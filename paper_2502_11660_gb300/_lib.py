@@ -46,6 +46,7 @@ SIGNATURES = {
     "msm377_version": (c_int, []),
     "fq_mul_batch": (c_int, [c_u32p, c_u32p, c_u32p, c_size, c_int, c_void]),
     "fq_to_montgomery": (c_int, [c_u32p, c_u32p, c_size, c_void]),
+    "fq_mul_batch_variant": (c_int, [c_u32p, c_u32p, c_u32p, c_size, c_int, c_void]),
     "fq_from_montgomery": (c_int, [c_u32p, c_u32p, c_size, c_void]),
     "padd_batch": (c_int, [c_u32p, c_u32p, c_u32p, c_size, c_int, c_void]),
     "xyzz_to_affine_batch": (c_int, [c_u32p, c_u32p, c_size, c_int, c_void]),
@@ -64,6 +65,7 @@ SIGNATURES = {
     "msm377_profile_last": (c_int, [ctypes.POINTER(ctypes.c_float), c_int]),
     "msm377_launch_count": (ctypes.c_uint64, []),
     "msm_g1_noalloc": (c_int, [c_u32p, c_u32p, c_size, c_u32p, ctypes.POINTER(MsmOpts)]),
+    "padd_chain": (c_int, [c_u32p, c_size, c_u32p, ctypes.c_uint32, c_int, c_void]),
     "msm_g1_batched_workspace_bytes": (c_size, [ctypes.POINTER(MsmJob), c_size, ctypes.POINTER(MsmOpts)]),
     "msm_g1_batched": (c_int, [ctypes.POINTER(MsmJob), c_size, c_void, c_size, ctypes.POINTER(MsmOpts)]),
 }

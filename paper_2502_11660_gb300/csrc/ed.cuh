@@ -177,6 +177,123 @@ __device__ __forceinline__ void dbl(ext& P) {
     fq::mul(P.Y, P.Y, A);           // G H
 }
 
+// ---- four lanes per point operation (latency-bound chains)
+//
+// A dependent chain of point operations (the window combination, the per-window
+// Horner sums) runs at the latency of one thread's multiplications. The
+// multiplications inside one Edwards formula fall into two or three levels of
+// independent products, so four lanes of a warp that hold the same point each
+// compute one product of a level and exchange the results through shared memory:
+// a doubling costs two multiplication latencies instead of eight. Every lane of
+// the warp calls these functions (lanes of the same group of four hold the same
+// values); `sh` is the group's four-element shared slot and `l` = lane % 4.
+
+__device__ __forceinline__ void xchg4(fe (&v)[4], const fe& mine, fe* sh, int l, bool writer) {
+    if (writer) sh[l] = mine;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = sh[k];
+    __syncwarp();
+}
+
+// Word-wise select by lane role (no addresses taken, so everything stays in registers).
+__device__ __forceinline__ fe pick4(int l, const fe& a, const fe& b, const fe& c, const fe& d) {
+    fe r;
+#pragma unroll
+    for (int k = 0; k < fq::N; ++k)
+        r.v[k] = l == 0 ? a.v[k] : (l == 1 ? b.v[k] : (l == 2 ? c.v[k] : d.v[k]));
+    return r;
+}
+
+// P = 2P: level 1 {X^2, Y^2, Z^2, (X + Y)^2}, level 2 {E F, G H, E H, F G}.
+__device__ __forceinline__ void dbl4(ext& P, fe* sh, int l, bool writer) {
+    fe s, r, v[4];
+    fq::add(s, P.X, P.Y);
+    const fe x = pick4(l, P.X, P.Y, P.Z, s);
+    fq::sqr(r, x);
+    xchg4(v, r, sh, l, writer);     // A, B, Z^2, (X + Y)^2
+    fe E, G, H, F;
+    fq::sub(E, v[3], v[0]);
+    fq::sub(E, E, v[1]);            // E = (X + Y)^2 - A - B
+    fq::sub(G, v[1], v[0]);         // G = B - A
+    fq::neg(H, v[0]);
+    fq::sub(H, H, v[1]);            // H = -A - B
+    fq::dbl(F, v[2]);
+    fq::sub(F, G, F);               // F = G - 2 Z^2
+    const fe a = pick4(l, E, G, E, F);
+    const fe b = pick4(l, F, H, H, G);
+    fq::mul(r, a, b);
+    xchg4(v, r, sh, l, writer);     // X3, Y3, T3, Z3
+    P.X = v[0];
+    P.Y = v[1];
+    P.T = v[2];
+    P.Z = v[3];
+}
+
+// P += Q (extended, Q read through `q`): level 1 {A, B, T1 T2, Z1 Z2}, level 2
+// {k T1 T2} (one lane), level 3 {E F, G H, E H, F G}.
+template <class QL>
+__device__ __forceinline__ void add4(ext& P, const QL& q, fe* sh, int l, bool writer) {
+    fe X2, Y2, Z2, T2, u, w, r, v[4];
+    q.X(X2);
+    q.Y(Y2);
+    q.Z(Z2);
+    q.T(T2);
+    fe a0, b0, a1, b1;
+    fq::sub(a0, P.Y, P.X);
+    fq::sub(b0, Y2, X2);
+    fq::add(a1, P.Y, P.X);
+    fq::add(b1, Y2, X2);
+    const fe x = pick4(l, a0, a1, P.T, P.Z);
+    const fe y = pick4(l, b0, b1, T2, Z2);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // A, B, T1 T2, Z1 Z2
+    load_const(u, kK);
+    fq::mul(w, v[2], u);            // C = k T1 T2 (every lane; one latency)
+    fe E, F, G, H, D;
+    fq::dbl(D, v[3]);
+    fq::sub(E, v[1], v[0]);
+    fq::add(H, v[1], v[0]);
+    fq::sub(F, D, w);
+    fq::add(G, D, w);
+    const fe a = pick4(l, E, G, E, F);
+    const fe b = pick4(l, F, H, H, G);
+    fq::mul(r, a, b);
+    xchg4(v, r, sh, l, writer);
+    P.X = v[0];
+    P.Y = v[1];
+    P.T = v[2];
+    P.Z = v[3];
+}
+
+// P += Q (stored): level 1 {A, B, C = T1 u2} (the fourth lane repeats C), level 2
+// {E F, G H, E H, F G}: two multiplication latencies per mixed addition.
+__device__ __forceinline__ void madd4(ext& P, const stored& Q, fe* sh, int l, bool writer) {
+    fe a0, b0, a1, b1, r, v[4];
+    fq::sub(a0, P.Y, P.X);
+    fq::sub(b0, Q.y, Q.x);
+    fq::add(a1, P.Y, P.X);
+    fq::add(b1, Q.y, Q.x);
+    const fe x = pick4(l, a0, a1, P.T, P.T);
+    const fe y = pick4(l, b0, b1, Q.u, Q.u);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // A, B, C, C
+    fe E, F, G, H, D;
+    fq::dbl(D, P.Z);
+    fq::sub(E, v[1], v[0]);
+    fq::add(H, v[1], v[0]);
+    fq::sub(F, D, v[2]);
+    fq::add(G, D, v[2]);
+    const fe a = pick4(l, E, G, E, F);
+    const fe b = pick4(l, F, H, H, G);
+    fq::mul(r, a, b);
+    xchg4(v, r, sh, l, writer);
+    P.X = v[0];
+    P.Y = v[1];
+    P.T = v[2];
+    P.Z = v[3];
+}
+
 // Weierstrass affine point (Montgomery form, [0, 2p)) of P, canonical [0, p);
 // the identity gives (0, 0). One inversion of (Z - Y) X.
 __device__ __forceinline__ void to_weierstrass(ec::affine& A, const ext& P) {

@@ -1,0 +1,382 @@
+// Alternative Fq multiplications, measured against the library's Montgomery CIOS
+// (fq_mul_batch_variant). None of them is used by the MSM; they exist to compare
+// the designs the paper uses or proposes with the one this library chose:
+//
+//  * BARRETT   -- the paper's modular multiplication (Sec. III-C): the 754-bit
+//                 product a*b, then Barrett reduction by three multiplications with
+//                 k = bitlen(p) = 377, mu = floor(2^754 / p): q1 = x >> (k - 1),
+//                 q3 = (q1 mu) >> (k + 1), r = x - q3 p mod 2^(k + 1) in [0, 3p),
+//                 then at most two subtractions of p. Standard-form operands.
+//  * KARATSUBA -- Montgomery, with a*b by one Karatsuba level over 192-bit halves
+//                 and schoolbook leaves (Sec. V-C proposes Karatsuba at the top
+//                 level); then word-by-word Montgomery reduction of the 24-word product.
+//  * CARRYSAVE -- Montgomery on 16 digits of 24 bits in 32-bit registers, 64-bit
+//                 column sums and two rounds of coarse carry propagation (the
+//                 element format of Sec. III-B / III-D carried to the GPU).
+//
+// Every variant reads 12 x 32-bit limbs in structure-of-arrays layout and writes the
+// canonical result in [0, p), so all four are bit-comparable.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fq.cuh"
+
+namespace {
+
+using fq::fe;
+constexpr int N = 12;
+
+__device__ __constant__ static const uint32_t kPv[N] = {FQ_P_LIMBS};
+// mu = floor(2^754 / p), 378 bits
+__device__ __constant__ static const uint32_t kMuB[N] = {
+    0x5e4daffcu, 0x1f9fd58cu, 0x89c42a59u, 0xd0ed6877u, 0xd85a6d02u, 0x6af2d488u,
+    0x6776b1a0u, 0x3bbad0deu, 0x582ef4f7u, 0x976c3ca0u, 0x0cc4060eu, 0x0261508du};
+
+// acc[0..12] += ai * b[0..11]: low halves at acc[j], high halves at acc[j + 1];
+// the final carry lands in acc[12] (the caller bounds the window so none leaves it).
+__device__ __forceinline__ void row(uint32_t& t0, uint32_t& t1, uint32_t& t2, uint32_t& t3, uint32_t& t4,
+                                    uint32_t& t5, uint32_t& t6, uint32_t& t7, uint32_t& t8, uint32_t& t9,
+                                    uint32_t& t10, uint32_t& t11, uint32_t& t12, uint32_t ai, const uint32_t* b) {
+    asm("mad.lo.cc.u32 %0, %13, %14, %0;\n\t"
+        "madc.lo.cc.u32 %1, %13, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, %16, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, %17, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, %18, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, %19, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, %20, %6;\n\t"
+        "madc.lo.cc.u32 %7, %13, %21, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, %22, %8;\n\t"
+        "madc.lo.cc.u32 %9, %13, %23, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, %24, %10;\n\t"
+        "madc.lo.cc.u32 %11, %13, %25, %11;\n\t"
+        "addc.u32 %12, %12, 0;\n\t"
+        "mad.hi.cc.u32 %1, %13, %14, %1;\n\t"
+        "madc.hi.cc.u32 %2, %13, %15, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, %16, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, %18, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, %19, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, %20, %7;\n\t"
+        "madc.hi.cc.u32 %8, %13, %21, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, %22, %9;\n\t"
+        "madc.hi.cc.u32 %10, %13, %23, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, %24, %11;\n\t"
+        "madc.hi.u32 %12, %13, %25, %12;"
+        : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9),
+          "+r"(t10), "+r"(t11), "+r"(t12)
+        : "r"(ai), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]),
+          "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
+}
+
+#define ROW_AT(x, i, ai, b)                                                                                  \
+    row(x[(i) + 0], x[(i) + 1], x[(i) + 2], x[(i) + 3], x[(i) + 4], x[(i) + 5], x[(i) + 6], x[(i) + 7],      \
+        x[(i) + 8], x[(i) + 9], x[(i) + 10], x[(i) + 11], x[(i) + 12], ai, b)
+
+// x[0..23] = a * b (x has 25 words; x[24] stays 0).
+__device__ __forceinline__ void mul_wide(uint32_t (&x)[25], const uint32_t* a, const uint32_t* b) {
+#pragma unroll
+    for (int k = 0; k < 25; ++k) x[k] = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) ROW_AT(x, i, a[i], b);
+}
+
+// a - b over n words; returns the borrow.
+template <int W>
+__device__ __forceinline__ uint32_t sub_words(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t borrow = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        uint64_t t = (uint64_t)a[k] - b[k] - borrow;
+        r[k] = (uint32_t)t;
+        borrow = (uint32_t)(t >> 63);
+    }
+    return borrow;
+}
+
+// r in [0, 2^384) -> r - p while r >= p (at most `times` subtractions)
+template <int TIMES>
+__device__ __forceinline__ void reduce_p(uint32_t* r) {
+#pragma unroll
+    for (int s = 0; s < TIMES; ++s) {
+        uint32_t d[N];
+        const uint32_t borrow = sub_words<N>(d, r, kPv);
+        if (!borrow) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) r[k] = d[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Barrett (Sec. III-C)
+
+__device__ __forceinline__ void mul_barrett(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    uint32_t x[25];
+    mul_wide(x, a, b);  // x < p^2 < 2^754
+    // q1 = x >> 376: words 11.. shifted by 24 bits (x < 2^754, so q1 < 2^378)
+    uint32_t q1[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) q1[i] = (x[11 + i] >> 24) | (x[12 + i] << 8);
+    // q2 = q1 * mu, q3 = q2 >> 378: words 11.. shifted by 26 bits
+    uint32_t q2[25];
+    mul_wide(q2, q1, kMuB);
+    uint32_t q3[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) q3[i] = (q2[11 + i] >> 26) | (q2[12 + i] << 6);
+    // r2 = q3 * p mod 2^378 (only the 12 low words are needed)
+    uint32_t r2[25];
+#pragma unroll
+    for (int k = 0; k < 25; ++k) r2[k] = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) ROW_AT(r2, i, q3[i], kPv);
+    // r = (x - r2) mod 2^378, in [0, 3p)
+    uint32_t rr[N];
+    sub_words<N>(rr, x, r2);
+    rr[N - 1] &= (1u << 26) - 1u;
+    reduce_p<2>(rr);
+#pragma unroll
+    for (int k = 0; k < N; ++k) r[k] = rr[k];
+}
+
+// ---------------------------------------------------------------- Karatsuba + Montgomery
+
+// x[0..12] = a[0..5] * b[0..5] (6 x 6 words; x has 13 words, x[12] = 0)
+__device__ __forceinline__ void mul6(uint32_t (&x)[13], const uint32_t* a, const uint32_t* b) {
+#pragma unroll
+    for (int k = 0; k < 13; ++k) x[k] = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        uint64_t carry = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            uint64_t t = (uint64_t)a[i] * b[j] + x[i + j] + carry;
+            x[i + j] = (uint32_t)t;
+            carry = t >> 32;
+        }
+        x[i + 6] = (uint32_t)carry;
+    }
+}
+
+__device__ __forceinline__ void mul_karatsuba(uint32_t* r, const uint32_t* a, const uint32_t* b) {
+    // a = a0 + a1 2^192, b = b0 + b1 2^192
+    uint32_t z0[13], z2[13], z1[13];
+    mul6(z0, a, b);
+    mul6(z2, a + 6, b + 6);
+    uint32_t sa[6], sb[6];
+    uint32_t ca = 0, cb = 0;
+    {
+        uint64_t c1 = 0, c2 = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            uint64_t t = (uint64_t)a[k] + a[k + 6] + c1;
+            sa[k] = (uint32_t)t;
+            c1 = t >> 32;
+            uint64_t u = (uint64_t)b[k] + b[k + 6] + c2;
+            sb[k] = (uint32_t)u;
+            c2 = u >> 32;
+        }
+        ca = (uint32_t)c1;
+        cb = (uint32_t)c2;
+    }
+    mul6(z1, sa, sb);
+    // (sa + ca 2^192)(sb + cb 2^192) = sa sb + (ca sb + cb sa) 2^192 + ca cb 2^384
+    uint32_t mid[14];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) mid[k] = z1[k];
+    mid[13] = 0;
+    {
+        uint64_t c = 0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            uint64_t t = (uint64_t)mid[6 + k] + (ca ? sb[k] : 0u) + (cb ? sa[k] : 0u) + c;
+            mid[6 + k] = (uint32_t)t;
+            c = t >> 32;
+        }
+        uint64_t t = (uint64_t)mid[12] + c + (ca & cb);
+        mid[12] = (uint32_t)t;
+        mid[13] = (uint32_t)(t >> 32);
+    }
+    // mid -= z0 + z2 (mid >= z0 + z2, the middle Karatsuba term is non-negative)
+    {
+        uint64_t borrow = 0;
+#pragma unroll
+        for (int k = 0; k < 14; ++k) {
+            uint64_t t = (uint64_t)mid[k] - (k < 13 ? z0[k] : 0u) - (k < 13 ? z2[k] : 0u) - borrow;
+            mid[k] = (uint32_t)t;
+            borrow = (uint32_t)(0u - (uint32_t)(t >> 32));  // 0, 1 or 2
+        }
+    }
+    // x = z0 + mid 2^192 + z2 2^384 (25 words)
+    uint32_t x[26];
+#pragma unroll
+    for (int k = 0; k < 26; ++k) x[k] = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x[k] = z0[k];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x[12 + k] = z2[k];
+    {
+        uint64_t c = 0;
+#pragma unroll
+        for (int k = 0; k < 20; ++k) {
+            uint64_t t = (uint64_t)x[6 + k] + (k < 14 ? mid[k] : 0u) + c;
+            x[6 + k] = (uint32_t)t;
+            c = t >> 32;
+        }
+    }
+    // Montgomery reduction, word by word: m = -x_i (since -p^-1 = 0xffffffff mod 2^32)
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const uint32_t m = 0u - x[i];
+        uint32_t top = 0;
+        row(x[i + 0], x[i + 1], x[i + 2], x[i + 3], x[i + 4], x[i + 5], x[i + 6], x[i + 7], x[i + 8], x[i + 9],
+            x[i + 10], x[i + 11], top, m, kPv);
+        // top holds the carry into word i + 12 (< 2^32); add it with a full carry chain
+        uint64_t c = top;
+#pragma unroll
+        for (int k = i + 12; k < 26; ++k) {
+            uint64_t t = (uint64_t)x[k] + c;
+            x[k] = (uint32_t)t;
+            c = t >> 32;
+        }
+    }
+    // result = x >> 384 < 2p
+    uint32_t rr[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) rr[k] = x[12 + k];
+    reduce_p<1>(rr);
+#pragma unroll
+    for (int k = 0; k < N; ++k) r[k] = rr[k];
+}
+
+// ---------------------------------------------------------------- carry-save radix 2^24 Montgomery
+
+constexpr int ND = 16;  // digits of 24 bits
+constexpr uint32_t DMASK = (1u << 24) - 1u;
+
+__host__ __device__ constexpr uint32_t pdig(int i) {
+    return i == 0 ? 0x1u : i == 1 ? 0xc00000u : i == 2 ? 0x8508u : i == 3 ? 0x300000u : i == 4 ? 0xb5d44u
+         : i == 5 ? 0x480017u : i == 6 ? 0x2fba09u : i == 7 ? 0x1ef362u : i == 8 ? 0xf5138fu
+         : i == 9 ? 0xd9f300u : i == 10 ? 0x3b1a22u : i == 11 ? 0x6ca149u : i == 12 ? 0x3b05c0u
+         : i == 13 ? 0x10eac6u : i == 14 ? 0x4617c5u : 0x1ae3au;
+}
+
+__device__ __forceinline__ void unpack24(uint32_t (&d)[ND], const uint32_t* w) {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const uint32_t w0 = w[3 * g], w1 = w[3 * g + 1], w2 = w[3 * g + 2];
+        d[4 * g + 0] = w0 & DMASK;
+        d[4 * g + 1] = ((w0 >> 24) | (w1 << 8)) & DMASK;
+        d[4 * g + 2] = ((w1 >> 16) | (w2 << 16)) & DMASK;
+        d[4 * g + 3] = w2 >> 8;
+    }
+}
+
+// r = a b 2^-384 mod p on 24-bit digits: row i adds a_i b into 64-bit column sums;
+// column i is then complete, m_i = -c_i mod 2^24 (p = 1 mod 2^24) zeroes its low
+// 24 bits and m_i p is added the same way; the column's high part carries into
+// column i + 1. Two rounds of coarse carries settle the result columns.
+__device__ __forceinline__ void mul_carrysave(uint32_t* r, const uint32_t* aw, const uint32_t* bw) {
+    uint32_t a[ND], b[ND];
+    unpack24(a, aw);
+    unpack24(b, bw);
+    uint64_t c[2 * ND];
+#pragma unroll
+    for (int k = 0; k < 2 * ND; ++k) c[k] = 0;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+#pragma unroll
+        for (int j = 0; j < ND; ++j) c[i + j] += (uint64_t)a[i] * b[j];
+        const uint32_t m = (0u - (uint32_t)c[i]) & DMASK;
+        c[i] += m;
+#pragma unroll
+        for (int j = 1; j < ND; ++j) c[i + j] += (uint64_t)m * pdig(j);
+        c[i + 1] += c[i] >> 24;
+    }
+    // exact digits of the result columns c[16..31] by one serial carry pass
+    uint32_t d[ND];
+    uint64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+        uint64_t t = c[ND + k] + carry;
+        d[k] = k < ND - 1 ? (uint32_t)(t & DMASK) : (uint32_t)t;
+        carry = t >> 24;
+    }
+    uint32_t w[N];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        w[3 * g] = d[4 * g] | (d[4 * g + 1] << 24);
+        w[3 * g + 1] = (d[4 * g + 1] >> 8) | (d[4 * g + 2] << 16);
+        w[3 * g + 2] = (d[4 * g + 2] >> 16) | (d[4 * g + 3] << 8);
+    }
+    reduce_p<1>(w);
+#pragma unroll
+    for (int k = 0; k < N; ++k) r[k] = w[k];
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int V>
+__global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                                 uint32_t* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x[N], y[N], r[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            x[k] = a[k * n + i];
+            y[k] = b[k * n + i];
+        }
+        if (V == MSM377_FQMUL_CIOS) {
+            fe fa, fb, fr;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                fa.v[k] = x[k];
+                fb.v[k] = y[k];
+            }
+            fq::mul_inl(fr, fa, fb);
+            fq::canon(fr, fr);
+#pragma unroll
+            for (int k = 0; k < N; ++k) r[k] = fr.v[k];
+        } else if (V == MSM377_FQMUL_BARRETT) {
+            mul_barrett(r, x, y);
+        } else if (V == MSM377_FQMUL_KARATSUBA) {
+            mul_karatsuba(r, x, y);
+        } else {
+            mul_carrysave(r, x, y);
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) out[k * n + i] = r[k];
+    }
+}
+
+}  // namespace
+
+using namespace msm377;
+
+extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n, int variant,
+                                    void* stream) {
+    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_CARRYSAVE)
+        return set_error(MSM377_EINVAL, "fq_mul_batch_variant: unknown variant %d", variant);
+    if (n == 0) return MSM377_OK;
+    if (!a || !b || !out) return set_error(MSM377_EINVAL, "fq_mul_batch_variant: NULL pointer");
+    cudaStream_t s = as_stream(stream);
+    int sms = 0, dev = 0;
+    MSM_CUDA_TRY(cudaGetDevice(&dev));
+    MSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    size_t blocks = (n + 255) / 256;
+    const size_t cap = (size_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    switch (variant) {
+        case MSM377_FQMUL_CIOS:
+            k_fq_mul_variant<MSM377_FQMUL_CIOS><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        case MSM377_FQMUL_BARRETT:
+            k_fq_mul_variant<MSM377_FQMUL_BARRETT><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        case MSM377_FQMUL_KARATSUBA:
+            k_fq_mul_variant<MSM377_FQMUL_KARATSUBA><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        default:
+            k_fq_mul_variant<MSM377_FQMUL_CARRYSAVE><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+    }
+    note_launches(1);
+    return check_launch("fq_mul_batch_variant");
+}

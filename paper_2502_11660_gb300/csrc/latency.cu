@@ -1,0 +1,119 @@
+// The dependent-chain latency experiment of the paper (Sec. V-A): the points of a
+// stream are summed strictly in order, P_0 + P_1 + ... + P_{n-1}, so every mixed
+// PADD waits for the previous one and the time per PADD is its latency, not a
+// throughput. The paper lowers that latency by spreading one PADD over several
+// AIE tiles (its med-ind mapping); here the analogue is spreading the independent
+// multiplications of one Edwards PADD over four lanes of a warp (ed::madd4: two
+// multiplication latencies per addition instead of seven).
+//
+// Variants (padd_chain): XYZZ on one thread (10 multiplications in sequence per
+// mixed addition, with the special-case branches), Edwards on one thread, and
+// Edwards on four lanes. Inputs are stored points (msm_points_prepare_ex), so the
+// timed kernel is the chain alone.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "ec.cuh"
+#include "ed.cuh"
+
+namespace {
+
+using ec::affine;
+using fq::fe;
+
+__device__ __forceinline__ void load_fe16(fe& a, const uint4* p) {
+    uint4 u0 = p[0], u1 = p[1], u2 = p[2];
+    a.v[0] = u0.x; a.v[1] = u0.y; a.v[2] = u0.z; a.v[3] = u0.w;
+    a.v[4] = u1.x; a.v[5] = u1.y; a.v[6] = u1.z; a.v[7] = u1.w;
+    a.v[8] = u2.x; a.v[9] = u2.y; a.v[10] = u2.z; a.v[11] = u2.w;
+}
+
+__device__ __forceinline__ void store_affine_std(uint32_t* out, affine A) {
+    if (!ec::is_inf(A)) {
+        fq::from_mont(A.x, A.x);
+        fq::from_mont(A.y, A.y);
+    }
+    fq::store(out, A.x);
+    fq::store(out + 12, A.y);
+}
+
+// One thread: XYZZ accumulator += Montgomery affine points in order.
+__global__ void k_chain_xyzz1(const uint4* __restrict__ pts, size_t n, uint32_t* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    ec::xyzz acc;
+    ec::set_inf(acc);
+    bool inf = true;
+    for (size_t i = 0; i < n; ++i) {
+        affine Q;
+        load_fe16(Q.x, pts + 6 * i);
+        load_fe16(Q.y, pts + 6 * i + 3);
+        ec::madd(acc, inf, Q);
+    }
+    affine A;
+    ec::to_affine(A, acc);
+    store_affine_std(out, A);
+}
+
+// One thread: Edwards accumulator += stored points (x, y, k x y) in order.
+__global__ void k_chain_ed1(const uint4* __restrict__ pts, size_t n, uint32_t* __restrict__ out) {
+    if (threadIdx.x != 0) return;
+    ed::ext acc;
+    ed::set_inf(acc);
+    for (size_t i = 0; i < n; ++i) {
+        ed::stored Q;
+        load_fe16(Q.x, pts + 9 * i);
+        load_fe16(Q.y, pts + 9 * i + 3);
+        load_fe16(Q.u, pts + 9 * i + 6);
+        ed::madd(acc, Q);
+    }
+    affine A;
+    ed::to_weierstrass(A, acc);
+    store_affine_std(out, A);
+}
+
+// Four lanes per addition; the eight groups of a warp compute the same chain (so
+// every __syncwarp is warp-wide) and lane 0 writes the result.
+__global__ void __launch_bounds__(32) k_chain_ed4(const uint4* __restrict__ pts, size_t n, uint32_t* __restrict__ out) {
+    __shared__ fe sh[8][4];
+    const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
+    ed::ext acc;
+    ed::set_inf(acc);
+    for (size_t i = 0; i < n; ++i) {
+        ed::stored Q;
+        load_fe16(Q.x, pts + 9 * i);
+        load_fe16(Q.y, pts + 9 * i + 3);
+        load_fe16(Q.u, pts + 9 * i + 6);
+        ed::madd4(acc, Q, sh[g], l, true);
+    }
+    if (lane != 0) return;
+    affine A;
+    ed::to_weierstrass(A, acc);
+    store_affine_std(out, A);
+}
+
+}  // namespace
+
+using namespace msm377;
+
+extern "C" int padd_chain(const uint32_t* points, size_t n, uint32_t* out, uint32_t flags, int lanes, void* stream) {
+    if (flags & ~(uint32_t)MSM377_EDWARDS)
+        return set_error(MSM377_EINVAL, "padd_chain: flags 0x%x (0 or MSM377_EDWARDS)", flags);
+    if (lanes != 1 && lanes != 4)
+        return set_error(MSM377_EINVAL, "padd_chain: lanes = %d (1 or 4)", lanes);
+    if (lanes == 4 && !(flags & MSM377_EDWARDS))
+        return set_error(MSM377_EINVAL, "padd_chain: four lanes need the Edwards model");
+    if (!out || (n && (!points || !aligned(points, 16))))
+        return set_error(MSM377_EINVAL, "padd_chain: NULL or non-16-byte-aligned pointer");
+    cudaStream_t s = as_stream(stream);
+    const uint4* p = reinterpret_cast<const uint4*>(points);
+    if (flags & MSM377_EDWARDS) {
+        if (lanes == 4)
+            k_chain_ed4<<<1, 32, 0, s>>>(p, n, out);
+        else
+            k_chain_ed1<<<1, 32, 0, s>>>(p, n, out);
+    } else {
+        k_chain_xyzz1<<<1, 32, 0, s>>>(p, n, out);
+    }
+    note_launches(1);
+    return check_launch("padd_chain");
+}

@@ -214,64 +214,116 @@ __global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out,
     store_fe(out + 6 * i + 3, y);
 }
 
-// Weierstrass -> Edwards stored form, kEdChunk points per thread sharing one
-// inversion (Montgomery's trick). For (x_w, y_w), with a = x_w + 1:
+// Weierstrass -> Edwards stored form. For (x_w, y_w), with a = x_w + 1:
 //   D = y_w (a + s),  x = c1 a (a + s) / D,  y = (a - s) y_w / D,  u = k x y.
-// The affine identity, and points outside the map's domain (D = 0: order 2 or
-// 4, never in the subgroup), become the Edwards identity (0, 1, 0).
+// The inverses of D come from one inversion per warp (Montgomery's trick twice:
+// each thread multiplies the D of its kEdChunk points, a warp scan multiplies the
+// threads' products, lane 0 inverts the warp's total, and prefix and suffix
+// products hand every thread the inverse of its own product, from which it walks
+// back through its chunk). The affine identity, and points outside the map's
+// domain (D = 0: order 2 or 4, never in the subgroup), become the Edwards
+// identity (0, 1, 0).
 constexpr int kEdChunk = 8;
 
-__device__ __forceinline__ bool ed_den(fe& a, fe& den, fe& x, fe& y, const uint4* __restrict__ in, size_t i,
-                                       size_t n, size_t np) {
-    glv_source(x, y, in, i, n, np);
-    if (fq::is_zero_raw(x) && fq::is_zero_raw(y)) return false;
-    fe one, sp;
-    fq::set_one(one);
-    fq::add(a, x, one);
-    ed::load_const(sp, ed::kS);
-    fq::add(sp, a, sp);
-    fq::mul(den, y, sp);
-    return !fq::is_zero(den);
+__device__ __forceinline__ fe shfl_fe_up(const fe& a, int off) {
+    fe r;
+#pragma unroll
+    for (int k = 0; k < fq::N; ++k) r.v[k] = __shfl_up_sync(0xffffffffu, a.v[k], off);
+    return r;
 }
 
-__global__ void k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n, size_t np) {
+__device__ __forceinline__ fe shfl_fe_down(const fe& a, int off) {
+    fe r;
+#pragma unroll
+    for (int k = 0; k < fq::N; ++k) r.v[k] = __shfl_down_sync(0xffffffffu, a.v[k], off);
+    return r;
+}
+
+__device__ __forceinline__ fe shfl_fe(const fe& a, int src) {
+    fe r;
+#pragma unroll
+    for (int k = 0; k < fq::N; ++k) r.v[k] = __shfl_sync(0xffffffffu, a.v[k], src);
+    return r;
+}
+
+// One warp covers 32 * kEdChunk consecutive stored points; every lane of every
+// launched warp takes part in the shuffles (lanes past np carry the product 1).
+__global__ void __launch_bounds__(128) k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n,
+                                                    size_t np) {
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const size_t i0 = t * kEdChunk;
-    if (i0 >= np) return;
-    const int m = (int)(np - i0 < (size_t)kEdChunk ? np - i0 : (size_t)kEdChunk);
-    fe pre[kEdChunk];
-    fe acc, a, den, x, y;
-    fq::set_one(acc);
+    const int m = i0 >= np ? 0 : (int)(np - i0 < (size_t)kEdChunk ? np - i0 : (size_t)kEdChunk);
+    fe xs[kEdChunk], ys[kEdChunk], den[kEdChunk];
+    bool ok[kEdChunk];
+    fe one, sp;
+    fq::set_one(one);
+    ed::load_const(sp, ed::kS);
+    fe acc = one;
     for (int j = 0; j < m; ++j) {
-        if (ed_den(a, den, x, y, in, i0 + j, n, np)) fq::mul(acc, acc, den);
-        pre[j] = acc;  // product of the valid denominators 0..j
+        glv_source(xs[j], ys[j], in, i0 + j, n, np);
+        ok[j] = !(fq::is_zero_raw(xs[j]) && fq::is_zero_raw(ys[j]));
+        fe a, apl;
+        fq::add(a, xs[j], one);
+        fq::add(apl, a, sp);
+        fq::mul(den[j], ys[j], apl);
+        ok[j] = ok[j] && !fq::is_zero(den[j]);
+        if (ok[j]) fq::mul(acc, acc, den[j]);
     }
+    // warp prefix products P_l = acc_0 ... acc_l and suffix products S_l = acc_{l+1} ... acc_31
+    fe pre = acc, suf = one, y;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        y = shfl_fe_up(pre, off);
+        if (lane >= off) fq::mul(pre, pre, y);
+    }
+    fe sacc = acc;                         // inclusive suffix, then shifted
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        y = shfl_fe_down(sacc, off);
+        if (lane + off < 32) fq::mul(sacc, sacc, y);
+    }
+    suf = shfl_fe_down(sacc, 1);
+    if (lane == 31) suf = one;
+    fe total = shfl_fe(pre, 31);
+    fe tinv = one;
+    if (lane == 0) ec::inv(tinv, total);
+    tinv = shfl_fe(tinv, 0);
+    fe before = shfl_fe_up(pre, 1);        // P_{l-1}
+    if (lane == 0) before = one;
+    // inverse of this thread's product: acc^-1 = total^-1 * P_{l-1} * S_l
     fe inv;
-    ec::inv(inv, acc);
+    fq::mul(inv, tinv, before);
+    fq::mul(inv, inv, suf);
+    // walk back through the chunk: inverse of den[j] = inv * (product of den[0..j-1])
+    fe prefix[kEdChunk];
+    fe run = one;
+    for (int j = 0; j < m; ++j) {
+        prefix[j] = run;
+        if (ok[j]) fq::mul(run, run, den[j]);
+    }
     for (int j = m - 1; j >= 0; --j) {
         uint4* o = out + (size_t)ModelEdwards::kStored * (i0 + j);
-        if (!ed_den(a, den, x, y, in, i0 + j, n, np)) {
-            fe z, one;
+        if (!ok[j]) {
+            fe z, o1;
             fq::set_zero(z);
-            fq::set_one(one);
-            fq::canon(one, one);
+            fq::canon(o1, one);
             store_fe(o, z);
-            store_fe(o + 3, one);
+            store_fe(o + 3, o1);
             store_fe(o + 6, z);
             continue;
         }
-        fe dinv, c, sp, xe, ye, u;
-        if (j > 0) fq::mul(dinv, inv, pre[j - 1]);
-        else dinv = inv;
-        fq::mul(inv, inv, den);
-        ed::load_const(sp, ed::kS);
+        fe dinv, c, a, xe, ye, u;
+        fq::mul(dinv, inv, prefix[j]);
+        fq::mul(inv, inv, den[j]);
+        fq::add(a, xs[j], one);
         fq::add(c, a, sp);                  // a + s
         fq::mul(xe, a, c);
         ed::load_const(c, ed::kC1);
         fq::mul(xe, xe, c);
         fq::mul(xe, xe, dinv);              // c1 a (a + s) / D
         fq::sub(c, a, sp);                  // a - s
-        fq::mul(ye, c, y);
+        fq::mul(ye, c, ys[j]);
         fq::mul(ye, ye, dinv);              // (a - s) y / D
         ed::load_const(c, ed::kK);
         fq::mul(u, xe, ye);
@@ -866,6 +918,53 @@ __global__ void k_chain(const uint4* __restrict__ S, int w_hi, int w_lo, int W, 
     fq::store(out + 12, A.y);
 }
 
+// Edwards versions of the two latency-bound chains with four lanes per point
+// operation (ed::dbl4 / ed::add4): each group of four lanes of a warp holds one
+// accumulator; all 32 lanes take part (every __syncwarp is warp-wide).
+constexpr int kGroups = 8;  // groups of four lanes per warp
+
+// Group g of warp b: S_w for window w = 8 b + g (windows past nwin recompute the
+// last window and store nothing).
+__global__ void __launch_bounds__(32) k_window_horner4(const uint4* __restrict__ Z, int nwin, int logG, int log2L,
+                                                       uint4* __restrict__ S) {
+    __shared__ fe sh[kGroups][4];
+    const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
+    const int w = blockIdx.x * kGroups + g;
+    const int wi = w < nwin ? w : nwin - 1;
+    const uint4* z = Z + (size_t)wi * (logG + 1) * kXyzzVec;
+    ed::ext acc;
+    ed::set_inf(acc);
+    for (int k = logG - 1; k >= 0; --k) {
+        ed::dbl4(acc, sh[g], l, true);
+        ed::add4(acc, MemQE{z + (size_t)k * kXyzzVec}, sh[g], l, true);
+    }
+    for (int t = 0; t < log2L; ++t) ed::dbl4(acc, sh[g], l, true);
+    ed::add4(acc, MemQE{z + (size_t)logG * kXyzzVec}, sh[g], l, true);
+    if (w < nwin && l == 0) ModelEdwards::store(S + (size_t)w * kXyzzVec, acc);
+}
+
+// sum_w 2^(c w) S_w from the top window, then the affine result in standard form.
+// Every group computes the same chain; lane 0 writes the result.
+__global__ void __launch_bounds__(32) k_chain4(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
+    __shared__ fe sh[kGroups][4];
+    const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
+    ed::ext acc;
+    ed::set_inf(acc);
+    for (int w = W - 1; w >= 0; --w) {
+        for (int k = 0; k < c; ++k) ed::dbl4(acc, sh[g], l, true);
+        ed::add4(acc, MemQE{S + (size_t)w * kXyzzVec}, sh[g], l, true);
+    }
+    if (lane != 0) return;
+    affine A;
+    ModelEdwards::to_affine(A, acc);
+    if (!ec::is_inf(A)) {
+        fq::from_mont(A.x, A.x);
+        fq::from_mont(A.y, A.y);
+    }
+    fq::store(out, A.x);
+    fq::store(out + 12, A.y);
+}
+
 // ---------------------------------------------------------------- planning
 
 struct Plan {
@@ -1000,7 +1099,7 @@ int stored_vec(uint32_t flags) { return (flags & MSM377_EDWARDS) ? ModelEdwards:
 void launch_prepare(const uint4* in, uint4* out, size_t n, uint32_t flags, cudaStream_t s) {
     const size_t np = stored_count(n, flags);
     if (flags & MSM377_EDWARDS) {
-        const size_t threads = (np + kEdChunk - 1) / kEdChunk;
+        const size_t threads = (np + kEdChunk - 1) / kEdChunk;  // whole warps: grid_for rounds up to 128
         k_prepare_ed<<<msm377::grid_for(threads, 128), 128, 0, s>>>(in, out, n, np);
     } else {
         k_prepare<<<msm377::grid_for(np, 256), 256, 0, s>>>(in, out, n, np);
@@ -1159,11 +1258,15 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
         zin = zout;
         zout = tmp;
     }
-    k_window_horner<M><<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
-    note_launches(1);
     // 7. window combination and normalisation
-    k_chain<M><<<1, 32, 0, s>>>(S, p.W, 0, p.W, p.c, accp, out);
-    note_launches(1);
+    if (p.edw) {
+        k_window_horner4<<<grid_for(p.W, kGroups), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+        k_chain4<<<1, 32, 0, s>>>(S, p.W, p.c, out);
+    } else {
+        k_window_horner<M><<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+        k_chain<M><<<1, 32, 0, s>>>(S, p.W, 0, p.W, p.c, accp, out);
+    }
+    note_launches(2);
     return check_launch("msm tail");
 }
 

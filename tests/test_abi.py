@@ -156,3 +156,11 @@ def test_window_tables_are_per_mode():
     finally:
         autotune.clear(edwards=True, glv=True)
     assert pkg.msm_g1_default_c(1 << 20, edwards=True, glv=True) == base_e
+
+
+def test_barrett_constant_matches_the_oracle():
+    from oracle import barrett, fq
+    src = open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", "fqvar.cu")).read()
+    k, mu = barrett.barrett_params(fq.P)
+    assert k == 377
+    assert _const_limbs(src, "kMuB") == mu
