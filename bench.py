@@ -1,14 +1,16 @@
 """Benchmark: BLS12-377 G1 MSM points/s at n = 2^20 (one step = one msm_g1 call).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n N] [--c C]
-                [--mode xyzz|edwards|glv|edwards+glv|best]
+                [--mode xyzz|edwards|glv|edwards+glv|edwards+precomputed|edwards+glv+precomputed|best]
 
 Our arm: resident prepared points (prepared once), fresh seeded scalars per
 step already in HBM, L2 flushed (256 MB write) between timed steps, per-step
-CUDA events on the launch stream. Every curve-model / GLV mode is autotuned and
-timed; the headline (`value`) is the fastest mode unless --mode names one (the
-workload's points P_i = s_i G lie in the order-r subgroup, which the Edwards and
-GLV modes require). Prints one JSON line (rank 0).
+CUDA events on the launch stream. Every curve-model / GLV / fixed-base mode is
+autotuned and timed; the headline (`value`) is the fastest mode unless --mode
+names one (the workload's points P_i = s_i G lie in the order-r subgroup, which
+the Edwards and GLV modes require; the fixed-base modes store 2^(cj) P_i for every
+window once per resident set, outside the timed region). Prints one JSON line
+(rank 0).
 Reference arm (--impl reference): the CPU oracle's Pippenger (plain C, all host
 cores) on a bounded sample of the same workload; rank 0 only.
 For N > 1 (torchrun) every rank runs its own MSMs on its own GPU (replicas, no
@@ -41,7 +43,10 @@ PRODUCTS["dbl"] = 6 * PRODUCTS["fq_mul"] + 3 * PRODUCTS["fq_sqr"]      # 2286
 PRODUCTS["ed_madd"] = 7 * PRODUCTS["fq_mul"]                            # 1932
 PRODUCTS["ed_add"] = 9 * PRODUCTS["fq_mul"]                             # 2484
 PRODUCTS["ed_dbl"] = 4 * PRODUCTS["fq_mul"] + 4 * PRODUCTS["fq_sqr"]    # 1944
-MODES = {"xyzz": (False, False), "edwards": (True, False), "glv": (False, True), "edwards+glv": (True, True)}
+# mode -> (edwards, glv, precomputed)
+MODES = {"xyzz": (False, False, False), "edwards": (True, False, False), "glv": (False, True, False),
+         "edwards+glv": (True, True, False), "edwards+precomputed": (True, False, True),
+         "edwards+glv+precomputed": (True, True, True)}
 X0 = 0x8508C00000000001
 R_ORDER = X0 ** 4 - X0 ** 2 + 1
 GLV_LAMBDA = X0 * X0 - 1
@@ -59,6 +64,39 @@ def parse():
     ap.add_argument("--mode", default="best", choices=["best"] + list(MODES))
     ap.add_argument("--no-extras", action="store_true", help="skip the e2e, cpu and batch-op extras")
     return ap.parse_args()
+
+
+def agree_on(value, world: int):
+    """Rank 0's value on every rank (the headline mode, so every rank times the same work)."""
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    obj = [value]
+    dist.broadcast_object_list(obj, src=0)
+    return obj[0]
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time: the whole job finishes when its last rank does."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_points_per_s(n: int, world: int, ms: float) -> float:
+    """Weak scaling: every rank runs its own n-point MSM per step."""
+    return world * n / (ms / 1e3)
+
+
+def rank_workload(n: int, rank: int, nsets: int):
+    """Seeds of rank `rank`'s resident point set and its per-step scalar sets (disjoint streams per rank)."""
+    seeds = synth.scalars(synth.stream_seed(2, n, 2 + 1000 * rank), n)
+    scal = [synth.scalars(synth.stream_seed(2, n, 100 + j + 1000 * rank), n) for j in range(nsets)]
+    return seeds, scal
 
 
 def dist_env():
@@ -84,13 +122,15 @@ def glv_halves(scalars: np.ndarray) -> np.ndarray:
     return out
 
 
-def digit_counts(scalars: np.ndarray, c: int, signed: bool, bits: int):
-    """Nonzero digits and distinct nonzero buckets per window (host numpy, for op counts)."""
+def digit_counts(scalars: np.ndarray, c: int, signed: bool, bits: int, shared: bool = False):
+    """Nonzero digits and distinct nonzero buckets, per window or (shared) over one
+    bucket set for all windows (host numpy, for op counts)."""
     words = scalars.astype(np.uint64)
     W = -(-(bits + (1 if signed else 0)) // c)
     carry = np.zeros(scalars.shape[0], dtype=np.int64)
     nonzero = 0
     runs = 0
+    seen = np.zeros(1 << c, dtype=bool)
     half = 1 << (c - 1)
     for j in range(W):
         b0 = j * c
@@ -109,7 +149,12 @@ def digit_counts(scalars: np.ndarray, c: int, signed: bool, bits: int):
             key = raw
         nz = key[key != 0]
         nonzero += nz.size
-        runs += np.unique(nz).size
+        if shared:
+            seen[np.unique(nz)] = True
+        else:
+            runs += np.unique(nz).size
+    if shared:
+        runs = int(seen.sum())
     return W, nonzero, runs
 
 
@@ -250,13 +295,14 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def op_counts(sc_host: np.ndarray, c: int, bits: int, edwards: bool, glv: bool):
+def op_counts(sc_host: np.ndarray, c: int, bits: int, edwards: bool, glv: bool, pre: bool = False):
     """Additions and doublings of one MSM, and the textbook products of its accumulation."""
     sc = glv_halves(sc_host) if glv else sc_host
-    W, nonzero, runs = digit_counts(sc, c, True, 127 if glv else bits)
+    W, nonzero, runs = digit_counts(sc, c, True, 127 if glv else bits, shared=pre)
     madds = nonzero - runs            # the first point of each run is an assignment
-    full_adds = 2 * W * (1 << (c - 1))  # running sums of the bucket reduction
-    dbls = W * c
+    sets = 1 if pre else W            # bucket sets
+    full_adds = 2 * sets * (1 << (c - 1))  # running sums of the bucket reduction
+    dbls = 0 if pre else (W - 1) * c
     pm = PRODUCTS["ed_madd" if edwards else "madd"]
     return {"windows": W, "madd": madds, "bucket_running_sum_adds": full_adds, "window_dbls": dbls,
             "products_per_madd": pm, "accumulate_products": madds * pm}
@@ -279,23 +325,22 @@ def run_ours(args):
     k = int(np.log2(n))
 
     # resident point set P_i = s_i G, built on the device and prepared per mode (not timed)
-    seeds = synth.scalars(synth.stream_seed(2, n, 2 + 1000 * rank), n)
-    pts_std = pkg.g1_generator_mul(pkg.to_device(seeds, dev))
     nsets = args.steps + args.warmup
-    sc_host = [synth.scalars(synth.stream_seed(2, n, 100 + j + 1000 * rank), n) for j in range(nsets)]
+    seeds, sc_host = rank_workload(n, rank, nsets)
+    pts_std = pkg.g1_generator_mul(pkg.to_device(seeds, dev))
     sc_dev = [pkg.to_device(x, dev) for x in sc_host]
     out = torch.empty(24, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def timed_steps(prep, ws, c, edw, gl, steps, offset, profile):
+    def timed_steps(prep, ws, c, edw, gl, pre, steps, offset, profile):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         stages = []
         for j in range(steps):
             flush.fill_(j & 0xFF)                 # L2 flush between timed steps (outside the events)
             ev[j][0].record(stream)
             pkg.msm_g1(prep, sc_dev[(offset + j) % nsets], out=out, workspace=ws, c=c, scalar_bits=bits,
-                       prepared=True, stream=stream, profile=profile, edwards=edw, glv=gl)
+                       prepared=True, stream=stream, profile=profile, edwards=edw, glv=gl, precomputed=pre)
             ev[j][1].record(stream)
             if profile:
                 stages.append(pkg.profile_last())   # synchronises on the step's last event
@@ -305,31 +350,42 @@ def run_ours(args):
     # every mode: window width measured on this GPU (the autotuner) unless --c, then a short timing
     survey = {}
     preps = {}
-    for name, (edw, gl) in MODES.items():
+    for name, (edw, gl, pre) in MODES.items():
         if args.mode != "best" and name != args.mode:
             continue
         tuning = None
         if args.c:
             c = args.c
         else:
-            tuning = autotune.tune(log2_sizes=[k], reps=3, device=dev, edwards=edw, glv=gl)
-            autotune.install(tuning["table"], edwards=edw, glv=gl)
-            c = pkg.msm_g1_default_c(n, True, edw, gl)
-        prep = pkg.msm_points_prepare(pts_std, edwards=edw, glv=gl)
-        ws = pkg.msm_g1_workspace(n, c=c, scalar_bits=bits, prepared=True, device=dev, edwards=edw, glv=gl)
+            tuning = autotune.tune(log2_sizes=[k], reps=3, device=dev, edwards=edw, glv=gl, precomputed=pre)
+            autotune.install(tuning["table"], edwards=edw, glv=gl, precomputed=pre)
+            c = pkg.msm_g1_default_c(n, True, edw, gl, pre)
+        t_prep = time.perf_counter()
+        if pre:
+            prep = pkg.msm_points_precompute(pts_std, c=c, scalar_bits=bits, glv=gl)
+        else:
+            prep = pkg.msm_points_prepare(pts_std, edwards=edw, glv=gl)
+        torch.cuda.synchronize()
+        t_prep = time.perf_counter() - t_prep
+        ws = pkg.msm_g1_workspace(n, c=c, scalar_bits=bits, prepared=True, device=dev, edwards=edw, glv=gl,
+                                  precomputed=pre)
         for j in range(args.warmup):
             pkg.msm_g1(prep, sc_dev[j], out=out, workspace=ws, c=c, scalar_bits=bits, prepared=True,
-                       stream=stream, edwards=edw, glv=gl)
+                       stream=stream, edwards=edw, glv=gl, precomputed=pre)
         torch.cuda.synchronize()
-        ms, st = timed_steps(prep, ws, c, edw, gl, 10, args.warmup, True)
+        ms, st = timed_steps(prep, ws, c, edw, gl, pre, 10, args.warmup, True)
         survey[name] = {"c": c, "ms_per_step": statistics.mean(ms),
                         "points_per_s": world * n / (statistics.mean(ms) / 1e3),
+                        "resident_set": {"GB": prep.numel() * 4 / 1e9, "setup_s": t_prep},
                         "stages_ms": {s2: statistics.mean(x[s2] for x in st) for s2 in st[0]},
                         "c_by_autotuner": ({str(cc): round(v, 3) for cc, v in tuning["timings"][k].items()}
                                            if tuning else "given")}
-        preps[name] = (prep, ws, c, edw, gl)
-    mode = min(survey, key=lambda m: survey[m]["ms_per_step"])
-    prep, ws, c, edw, gl = preps[mode]
+        preps[name] = (prep, ws, c, edw, gl, pre)
+    mode = agree_on(min(survey, key=lambda m: survey[m]["ms_per_step"]), world)
+    prep, ws, c, edw, gl, pre = preps[mode]
+    # the host-buffer path prepares points inside every call: the fastest mode without precomputation
+    e2e_mode = min((m for m in survey if not MODES[m][2]), key=lambda m: survey[m]["ms_per_step"], default=None)
+    e2e_c = survey[e2e_mode]["c"] if e2e_mode else None
     for other in list(preps):
         if other != mode:
             del preps[other]
@@ -343,20 +399,16 @@ def run_ours(args):
     clocks.start()
     launches0 = pkg.launch_count()
     t_wall = time.perf_counter()
-    step_ms, stage_ms = timed_steps(prep, ws, c, edw, gl, args.steps, args.warmup, True)
+    step_ms, stage_ms = timed_steps(prep, ws, c, edw, gl, pre, args.steps, args.warmup, True)
     wall = time.perf_counter() - t_wall
     launches = pkg.launch_count() - launches0
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms / 1e3)
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+    value = job_points_per_s(n, world, ms)
 
-    ops = op_counts(sc_host[args.warmup], c, bits, edw, gl)
+    ops = op_counts(sc_host[args.warmup], c, bits, edw, gl, pre)
     acc_ms = statistics.mean(x["accumulate"] for x in stage_ms)
     achieved = ops["accumulate_products"] / (acc_ms / 1e3)
     rec, rec_any = recorded_traffic(mode)
@@ -373,7 +425,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32 (12x32-bit limb Montgomery integer arithmetic)", "data": "synthetic",
         "config": {"workload": f"msm_g1 BLS12-377 G1 n={n}, mode {mode} (signed digits c={c}), resident "
-                               f"prepared points, fresh scalars per step", "n": n, "c": c, "mode": mode,
+                               f"prepared points{' with per-window shifted copies made once per set' if pre else ''}, "
+                               f"fresh scalars per step", "n": n, "c": c, "mode": mode,
                    "windows": ops["windows"],
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "parallelism": f"replicas x{world}"},
@@ -388,6 +441,9 @@ def run_ours(args):
     }
 
     if rank == 0 and not args.no_extras:
+        # extras run in the fastest mode without precomputation (every call prepares its points)
+        edw, gl, _ = MODES[e2e_mode] if e2e_mode else (True, True, False)
+        c = e2e_c or pkg.msm_g1_default_c(n, True, edw, gl)
         # end to end through the host-buffer C-ABI call: H2D of points and scalars, D2H of the result
         pinned_pts = torch.from_numpy(pkg.to_host(pts_std).view(np.int32)).pin_memory()
         hp = pinned_pts.numpy().view(np.uint32)
@@ -404,7 +460,7 @@ def run_ours(args):
         e2e_s = sum(et) / len(et)
         result["e2e"] = {"value": n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": n * (96 + 32),
                          "d2h_bytes_per_step": 96, "ms_per_step": 1e3 * e2e_s,
-                         "call": f"msm_g1_host (pinned host points + scalars, synchronous; mode {mode}, "
+                         "call": f"msm_g1_host (pinned host points + scalars, synchronous; mode {e2e_mode}, "
                                  f"points prepared inside the call)"}
         del hws
         # standalone batched arithmetic at 2^24 (Fq Montgomery multiplications, mixed PADDs)

@@ -138,6 +138,13 @@ int g1_generator_mul(const uint32_t *seeds, size_t n, uint32_t *out, void *strea
  * PRECONDITION: every point lies in the order-r subgroup (same as MSM377_EDWARDS);
  * scalars may be any 256-bit values (reduced mod r). */
 #define MSM377_GLV 8u
+/* Fixed-base precomputation for resident sets (with MSM377_EDWARDS and
+ * MSM377_POINTS_PREPARED, GLV optional): points is msm_points_precompute output,
+ * the stored forms of 2^(c j) P_i for every digit window j, made for this same c
+ * (explicit, nonzero), scalar_bits, signed_digits and GLV choice. All windows then
+ * add into one bucket set: the bucket reduction shrinks by the window count and the
+ * window chain has no doublings; the mixed additions are the same in number. */
+#define MSM377_PRECOMPUTED 16u
 
 typedef struct msm_opts {
     int32_t c;             /* window width in bits, 2..20; 0 = chosen from n */
@@ -146,7 +153,8 @@ typedef struct msm_opts {
     int32_t scalar_bits;   /* caller's bound: every scalar < 2^scalar_bits (1..256);
                               0 = 256. A larger scalar makes the call fail with
                               MSM377_ERANGE (reported through the workspace status). */
-    uint32_t flags;        /* MSM377_POINTS_PREPARED | MSM377_PROFILE | MSM377_EDWARDS | MSM377_GLV */
+    uint32_t flags;        /* MSM377_POINTS_PREPARED | MSM377_PROFILE | MSM377_EDWARDS | MSM377_GLV |
+                              MSM377_PRECOMPUTED */
     void *stream;          /* cudaStream_t */
 } msm_opts;
 
@@ -159,8 +167,9 @@ int msm_g1_default_c(size_t n, int signed_digits, uint32_t flags);
 
 /* Installs measured window widths for signed digits: c_by_log2n[k] is used for
  * n in [2^k, 2^(k+1)) when opts.c == 0 (0 keeps the built-in rule). One table per
- * combination of MSM377_EDWARDS and MSM377_GLV, chosen by flags (other bits:
- * MSM377_EINVAL). len <= 32; len = 0 clears that table. Process-wide; written by
+ * combination of MSM377_EDWARDS, MSM377_GLV and MSM377_PRECOMPUTED, chosen by flags
+ * (other bits: MSM377_EINVAL; with PRECOMPUTED the table only advises which c to
+ * precompute for, since those calls need an explicit c). len <= 32; len = 0 clears that table. Process-wide; written by
  * the autotuner. */
 int msm_g1_set_window_table(const int32_t *c_by_log2n, int len, uint32_t flags);
 
@@ -183,6 +192,21 @@ int msm_points_prepare_ex(const uint32_t *points_std, size_t n, uint32_t *out, u
 /* msm_points_prepare_ex with flags = 0 (XYZZ, no GLV; 96 bytes per point). out
  * may alias in. */
 int msm_points_prepare(const uint32_t *points_std, size_t n, uint32_t *out, void *stream);
+
+/* Bytes of the precomputed set for n points and these options (flags must hold
+ * MSM377_EDWARDS | MSM377_PRECOMPUTED, GLV optional; c explicit): Wd * n' stored
+ * points of 144 bytes, Wd = the digit windows of scalar_bits at width c, n' = n or
+ * 2n with GLV. 0 on other options. */
+size_t msm_points_precomputed_bytes(size_t n, const msm_opts *opts);
+
+/* Fills out (device, 16-byte aligned, msm_points_precomputed_bytes; it must not
+ * overlap points_std) from n affine standard-form points: row i Wd + j is the
+ * Edwards stored form of 2^(c j) P'_i, P' the (GLV-interleaved) stored points, so
+ * the rows of input points [a, b) are rows [a Wd', b Wd') (Wd' = Wd, or 2 Wd with
+ * GLV) and a resident set slices without copies. Asynchronous on opts->stream;
+ * one-time work per resident set (c doublings per point and window, one inversion
+ * per 256 points and window). Subgroup points only, as MSM377_EDWARDS. */
+int msm_points_precompute(const uint32_t *points_std, size_t n, uint32_t *out, const msm_opts *opts);
 
 /* points: device, 24 u32 per point in standard form, or with MSM377_POINTS_PREPARED
  *   the stored form of msm_points_prepare_ex for the same flags; 16-byte aligned. scalars: device, 8 u32 per scalar, 16-byte aligned.

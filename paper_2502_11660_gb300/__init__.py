@@ -24,6 +24,7 @@ POINTS_PREPARED = 1
 PROFILE = 2
 EDWARDS = 4   # the paper's twisted Edwards model; points of the order-r subgroup
 GLV = 8       # endomorphism split, half the windows; points of the order-r subgroup
+PRECOMPUTED = 16  # fixed-base shifted copies 2^(cj) P (Edwards resident sets, explicit c)
 MSM_STAGES = ("head", "accumulate", "tail")
 
 __all__ = [
@@ -34,7 +35,8 @@ __all__ = [
     "imad_probe", "lib", "last_error", "profile_last", "launch_count", "MSM_STAGES", "PROFILE",
     "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace", "EDWARDS", "GLV",
     "msm_points_prepared_bytes", "padd_chain", "fq_mul_batch_variant", "FQMUL_CIOS", "FQMUL_BARRETT",
-    "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE",
+    "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE", "PRECOMPUTED", "msm_points_precompute",
+    "msm_points_precomputed_bytes",
 ]
 
 
@@ -150,20 +152,46 @@ def msm_points_prepare(points: torch.Tensor, out: torch.Tensor | None = None, st
 
 
 def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0, profile=False, edwards=False,
-          glv=False) -> MsmOpts:
+          glv=False, precomputed=False) -> MsmOpts:
     """stream=0 for size queries (no CUDA context needed); None = torch's current stream."""
     sv = 0 if (isinstance(stream, int) and stream == 0) else _s(stream).value
     flags = (POINTS_PREPARED if prepared else 0) | (PROFILE if profile else 0) | _model_flags(edwards, glv)
+    flags |= PRECOMPUTED if precomputed else 0
     return MsmOpts(int(c), 1 if signed else 0, int(scalar_bits), flags, sv)
 
 
-def msm_g1_default_c(n: int, signed: bool = True, edwards: bool = False, glv: bool = False) -> int:
-    return lib().msm_g1_default_c(n, 1 if signed else 0, _model_flags(edwards, glv))
+def msm_points_precomputed_bytes(n: int, c: int, scalar_bits: int = 0, signed: bool = True,
+                                 glv: bool = False) -> int:
+    o = _opts(c, signed, scalar_bits, True, edwards=True, glv=glv, precomputed=True)
+    return int(lib().msm_points_precomputed_bytes(n, ctypes.byref(o)))
+
+
+def msm_points_precompute(points: torch.Tensor, c: int, scalar_bits: int = 0, signed: bool = True,
+                          glv: bool = False, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Fixed-base set for msm_g1(..., edwards=True, precomputed=True) with the same c, scalar_bits,
+    signed and glv: rows j n' + i = stored 2^(c j) P'_i, as an (rows, 36) int32 tensor."""
+    n = points.shape[0]
+    nbytes = msm_points_precomputed_bytes(n, c, scalar_bits, signed, glv)
+    if msm_points_precomputed_bytes(max(n, 1), c, scalar_bits, signed, glv) == 0:
+        raise MsmError(-1, "bad precompute options (explicit c needed)")
+    if out is None:
+        out = torch.empty((nbytes // 144, 36), dtype=torch.int32, device=points.device)
+    _check_dev(points, out)
+    o = _opts(c, signed, scalar_bits, True, None if stream is None else stream, edwards=True, glv=glv,
+              precomputed=True)
+    check(lib().msm_points_precompute(_p(points), n, _p(out), ctypes.byref(o)))
+    return out
+
+
+def msm_g1_default_c(n: int, signed: bool = True, edwards: bool = False, glv: bool = False,
+                     precomputed: bool = False) -> int:
+    return lib().msm_g1_default_c(n, 1 if signed else 0,
+                                  _model_flags(edwards, glv) | (PRECOMPUTED if precomputed else 0))
 
 
 def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, device="cuda",
-                     edwards: bool = False, glv: bool = False) -> torch.Tensor:
-    o = _opts(c, signed, scalar_bits, prepared, edwards=edwards, glv=glv)
+                     edwards: bool = False, glv: bool = False, precomputed: bool = False) -> torch.Tensor:
+    o = _opts(c, signed, scalar_bits, prepared or precomputed, edwards=edwards, glv=glv, precomputed=precomputed)
     nbytes = lib().msm_g1_workspace_bytes(n, ctypes.byref(o))
     if nbytes == 0:
         raise MsmError(-1, "bad MSM options")
@@ -173,14 +201,17 @@ def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, de
 def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None = None,
            workspace: torch.Tensor | None = None, c: int = 0, signed: bool = True,
            scalar_bits: int = 0, prepared: bool = False, stream=None, profile: bool = False,
-           edwards: bool = False, glv: bool = False) -> torch.Tensor:
+           edwards: bool = False, glv: bool = False, precomputed: bool = False) -> torch.Tensor:
     """Enqueues sum_i scalars_i * points_i; returns the (24,) int32 device tensor it writes.
-    With prepared=True, points is msm_points_prepare(..., edwards=, glv=) output."""
+    With prepared=True, points is msm_points_prepare(..., edwards=, glv=) output; with
+    precomputed=True (Edwards, explicit c) msm_points_precompute output for the same options."""
     n = scalars.shape[0]
-    _check_points(points, n, prepared, edwards, glv)
-    o = _opts(c, signed, scalar_bits, prepared, None if stream is None else stream, profile, edwards, glv)
+    o = _opts(c, signed, scalar_bits, prepared or precomputed, None if stream is None else stream, profile,
+              edwards, glv, precomputed)
+    _check_points(points, n, prepared or precomputed, edwards, glv, o)
     if workspace is None:
-        workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared, points.device, edwards, glv)
+        workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared or precomputed, points.device, edwards,
+                                     glv, precomputed)
     out = torch.empty(24, dtype=torch.int32, device=points.device) if out is None else out
     _check_dev(points, scalars, out, workspace)
     check(lib().msm_g1(_p(points), _p(scalars), n, _p(out), _p(workspace), workspace.numel(),
@@ -188,9 +219,12 @@ def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None
     return out
 
 
-def _check_points(points: torch.Tensor, n: int, prepared: bool, edwards: bool, glv: bool) -> None:
+def _check_points(points: torch.Tensor, n: int, prepared: bool, edwards: bool, glv: bool, o=None) -> None:
     """The points tensor must hold exactly what the call will read for n scalars."""
-    want = lib().msm_points_prepared_bytes(n, _model_flags(edwards, glv)) if prepared else 96 * n
+    if o is not None and o.flags & PRECOMPUTED:
+        want = lib().msm_points_precomputed_bytes(n, ctypes.byref(o))
+    else:
+        want = lib().msm_points_prepared_bytes(n, _model_flags(edwards, glv)) if prepared else 96 * n
     if points.numel() * points.element_size() != want:
         raise ValueError(f"points tensor holds {points.numel() * points.element_size()} bytes; "
                          f"{want} expected for n = {n} ({'prepared' if prepared else 'standard'} form)")
@@ -212,12 +246,13 @@ def _jobs_array(points_list, scalars_list, outs, cs):
 
 
 def msm_g1_batched_workspace(points_list, c_list=None, signed=True, scalar_bits=0, prepared=False,
-                             device="cuda", edwards: bool = False, glv: bool = False) -> torch.Tensor:
+                             device="cuda", edwards: bool = False, glv: bool = False, precomputed: bool = False,
+                             n_list=None) -> torch.Tensor:
     arr = (MsmJob * len(points_list))()
     for i, pt in enumerate(points_list):
-        arr[i].n = _rows(pt, prepared, glv)
+        arr[i].n = int(n_list[i]) if n_list is not None else _rows(pt, prepared, glv)
         arr[i].c = int(c_list[i]) if c_list is not None else 0
-    o = _opts(0, signed, scalar_bits, prepared, edwards=edwards, glv=glv)
+    o = _opts(0, signed, scalar_bits, prepared or precomputed, edwards=edwards, glv=glv, precomputed=precomputed)
     nbytes = lib().msm_g1_batched_workspace_bytes(arr, len(points_list), ctypes.byref(o))
     if nbytes == 0:
         raise MsmError(-1, "bad batched MSM options")
@@ -226,7 +261,7 @@ def msm_g1_batched_workspace(points_list, c_list=None, signed=True, scalar_bits=
 
 def msm_g1_batched(points_list, scalars_list, outs=None, workspace: torch.Tensor | None = None,
                    c_list=None, signed: bool = True, scalar_bits: int = 0, prepared: bool = False,
-                   stream=None, edwards: bool = False, glv: bool = False):
+                   stream=None, edwards: bool = False, glv: bool = False, precomputed: bool = False):
     """Enqueues len(points_list) <= 128 independent MSMs; returns their (24,) output tensors."""
     if len(points_list) != len(scalars_list):
         raise ValueError("points and scalars lists differ in length")
@@ -235,12 +270,15 @@ def msm_g1_batched(points_list, scalars_list, outs=None, workspace: torch.Tensor
         outs = [torch.empty(24, dtype=torch.int32, device=dev) for _ in points_list]
     if workspace is None:
         workspace = msm_g1_batched_workspace(points_list, c_list, signed, scalar_bits, prepared, dev,
-                                             edwards, glv)
-    for pt, sc in zip(points_list, scalars_list):
-        _check_points(pt, sc.shape[0], prepared, edwards, glv)
+                                             edwards, glv, precomputed, [sc.shape[0] for sc in scalars_list])
+    for i, (pt, sc) in enumerate(zip(points_list, scalars_list)):
+        oj = _opts(int(c_list[i]) if c_list is not None else 0, signed, scalar_bits, prepared or precomputed,
+                   edwards=edwards, glv=glv, precomputed=precomputed)
+        _check_points(pt, sc.shape[0], prepared or precomputed, edwards, glv, oj)
         _check_dev(pt, sc)
     arr = _jobs_array(points_list, scalars_list, outs, c_list)
-    o = _opts(0, signed, scalar_bits, prepared, None if stream is None else stream, edwards=edwards, glv=glv)
+    o = _opts(0, signed, scalar_bits, prepared or precomputed, None if stream is None else stream,
+              edwards=edwards, glv=glv, precomputed=precomputed)
     check(lib().msm_g1_batched(arr, len(points_list), _p(workspace), workspace.numel(), ctypes.byref(o)))
     return outs
 

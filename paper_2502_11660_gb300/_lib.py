@@ -57,6 +57,8 @@ SIGNATURES = {
     "msm_points_prepare": (c_int, [c_u32p, c_size, c_u32p, c_void]),
     "msm_points_prepare_ex": (c_int, [c_u32p, c_size, c_u32p, ctypes.c_uint32, c_void]),
     "msm_points_prepared_bytes": (c_size, [c_size, ctypes.c_uint32]),
+    "msm_points_precomputed_bytes": (c_size, [c_size, ctypes.POINTER(MsmOpts)]),
+    "msm_points_precompute": (c_int, [c_u32p, c_size, c_u32p, ctypes.POINTER(MsmOpts)]),
     "msm_g1": (c_int, [c_u32p, c_u32p, c_size, c_u32p, c_void, c_size, ctypes.POINTER(MsmOpts)]),
     "msm_g1_status": (c_int, [c_void, ctypes.POINTER(MsmOpts)]),
     "msm_g1_host_workspace_bytes": (c_size, [c_size, ctypes.POINTER(MsmOpts)]),

@@ -16,19 +16,25 @@ import os
 import numpy as np
 import torch
 
-from . import (_model_flags, g1_generator_mul, lib, msm_g1, msm_g1_default_c, msm_g1_workspace,
-               msm_points_prepare, to_device)
+from . import (PRECOMPUTED, _model_flags, g1_generator_mul, lib, msm_g1, msm_g1_default_c, msm_g1_workspace,
+               msm_points_precompute, msm_points_prepare, to_device)
 from ._lib import check
 
 
 def time_msm(n: int, c: int, reps: int = 3, device="cuda", seed: int = 11, edwards: bool = False,
-             glv: bool = False) -> float:
-    """Median milliseconds of one msm_g1 call with window c at size n."""
+             glv: bool = False, precomputed: bool = False) -> float:
+    """Median milliseconds of one msm_g1 call with window c at size n (a precomputed
+    set is built for each c, outside the timing)."""
     import synth
-    pts = msm_points_prepare(g1_generator_mul(to_device(synth.scalars(seed, n), device)), edwards=edwards,
-                             glv=glv)
+    std = g1_generator_mul(to_device(synth.scalars(seed, n), device))
+    if precomputed:
+        pts = msm_points_precompute(std, c=c, scalar_bits=253, glv=glv)
+    else:
+        pts = msm_points_prepare(std, edwards=edwards, glv=glv)
+    del std
     sc = to_device(synth.scalars(seed + 1, n), device)
-    kw = dict(c=c, scalar_bits=253, prepared=True, edwards=edwards, glv=glv)
+    kw = dict(c=c, scalar_bits=253, prepared=True, edwards=edwards or precomputed, glv=glv,
+              precomputed=precomputed)
     ws = msm_g1_workspace(n, device=device, **kw)
     out = torch.empty(24, dtype=torch.int32, device=device)
     msm_g1(pts, sc, out=out, workspace=ws, **kw)
@@ -43,22 +49,26 @@ def time_msm(n: int, c: int, reps: int = 3, device="cuda", seed: int = 11, edwar
     return float(np.median(times))
 
 
-def candidates(log2n: int, glv: bool = False) -> list[int]:
-    """Around the built-in rule; 12..17 for the large sizes (13..18 with GLV: 2n points per window)."""
+def candidates(log2n: int, glv: bool = False, precomputed: bool = False) -> list[int]:
+    """Around the built-in rule; 12..17 for the large sizes (13..18 with GLV: 2n points per window;
+    15..20 precomputed: all windows share one bucket set, so wider windows pay)."""
     if log2n >= 16:
+        if precomputed:
+            return list(range(15, 21))
         return list(range(13, 19)) if glv else list(range(12, 18))
     base = max(4, log2n - 4)
     return sorted({max(3, base - 2), max(3, base - 1), base, base + 1, base + 2})
 
 
 def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda", edwards: bool = False,
-         glv: bool = False) -> dict:
+         glv: bool = False, precomputed: bool = False) -> dict:
     """Returns {"table": [c by log2 n], "timings": {k: {c: ms}}}; fills gaps from neighbours."""
     timings = {}
     best = {}
     for k in log2_sizes:
         n = 1 << k
-        t = {c: time_msm(n, c, reps, device, edwards=edwards, glv=glv) for c in candidates(k, glv)}
+        t = {c: time_msm(n, c, reps, device, edwards=edwards, glv=glv, precomputed=precomputed)
+             for c in candidates(k, glv, precomputed)}
         timings[k] = t
         best[k] = min(t, key=t.get)
     table = [0] * 32
@@ -69,16 +79,20 @@ def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda", edwards: boo
             if abs(near - k) <= 2:
                 table[k] = best[near]
     return {"table": table, "timings": timings, "device": torch.cuda.get_device_name(device),
-            "edwards": edwards, "glv": glv}
+            "edwards": edwards, "glv": glv, "precomputed": precomputed}
 
 
-def install(table, edwards: bool = False, glv: bool = False) -> None:
+def _flags(edwards: bool, glv: bool, precomputed: bool) -> int:
+    return _model_flags(edwards or precomputed, glv) | (PRECOMPUTED if precomputed else 0)
+
+
+def install(table, edwards: bool = False, glv: bool = False, precomputed: bool = False) -> None:
     arr = (ctypes.c_int32 * len(table))(*[int(x) for x in table])
-    check(lib().msm_g1_set_window_table(arr, len(table), _model_flags(edwards, glv)))
+    check(lib().msm_g1_set_window_table(arr, len(table), _flags(edwards, glv, precomputed)))
 
 
-def clear(edwards: bool = False, glv: bool = False) -> None:
-    check(lib().msm_g1_set_window_table(None, 0, _model_flags(edwards, glv)))
+def clear(edwards: bool = False, glv: bool = False, precomputed: bool = False) -> None:
+    check(lib().msm_g1_set_window_table(None, 0, _flags(edwards, glv, precomputed)))
 
 
 def save(result: dict, path: str) -> None:
@@ -95,5 +109,5 @@ def load(path: str) -> dict | None:
         return json.load(f)
 
 
-def current_choice(n: int, edwards: bool = False, glv: bool = False) -> int:
-    return msm_g1_default_c(n, True, edwards, glv)
+def current_choice(n: int, edwards: bool = False, glv: bool = False, precomputed: bool = False) -> int:
+    return msm_g1_default_c(n, True, edwards or precomputed, glv, precomputed)

@@ -246,20 +246,72 @@ __device__ __forceinline__ fe shfl_fe(const fe& a, int src) {
     return r;
 }
 
-// One warp covers 32 * kEdChunk consecutive stored points; every lane of every
-// launched warp takes part in the shuffles (lanes past np carry the product 1).
-__global__ void __launch_bounds__(128) k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n,
-                                                    size_t np) {
-    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+// Replaces den[j] (j < m, where ok[j]) by its inverse, with one inversion for
+// the whole warp: prefix and suffix products over the lanes' chunk products hand
+// every lane the inverse of its own product, from which it walks back through its
+// chunk. Every lane of the warp must call it (m may be 0; lanes carry 1 then).
+__device__ __forceinline__ void warp_batch_inverse(fe (&den)[kEdChunk], const bool (&ok)[kEdChunk], int m) {
     const int lane = threadIdx.x & 31;
-    const size_t i0 = t * kEdChunk;
-    const int m = i0 >= np ? 0 : (int)(np - i0 < (size_t)kEdChunk ? np - i0 : (size_t)kEdChunk);
+    fe one;
+    fq::set_one(one);
+    fe prefix[kEdChunk];
+    fe acc = one;
+    for (int j = 0; j < m; ++j) {
+        prefix[j] = acc;                   // product of the valid den[0..j-1]
+        if (ok[j]) fq::mul(acc, acc, den[j]);
+    }
+    fe pre = acc, y;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {  // P_l = acc_0 ... acc_l
+        y = shfl_fe_up(pre, off);
+        if (lane >= off) fq::mul(pre, pre, y);
+    }
+    fe sacc = acc;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {  // acc_l ... acc_31
+        y = shfl_fe_down(sacc, off);
+        if (lane + off < 32) fq::mul(sacc, sacc, y);
+    }
+    fe suf = shfl_fe_down(sacc, 1);           // S_l = acc_{l+1} ... acc_31
+    if (lane == 31) suf = one;
+    const fe total = shfl_fe(pre, 31);
+    fe tinv = one;
+    if (lane == 0) ec::inv(tinv, total);
+    tinv = shfl_fe(tinv, 0);
+    fe before = shfl_fe_up(pre, 1);           // P_{l-1}
+    if (lane == 0) before = one;
+    fe inv;                                   // acc^-1 = total^-1 P_{l-1} S_l
+    fq::mul(inv, tinv, before);
+    fq::mul(inv, inv, suf);
+    for (int j = m - 1; j >= 0; --j) {
+        if (!ok[j]) continue;
+        fe dj;
+        fq::mul(dj, inv, prefix[j]);
+        fq::mul(inv, inv, den[j]);
+        den[j] = dj;
+    }
+}
+
+__device__ __forceinline__ void store_ed_identity(uint4* o) {
+    fe z, one;
+    fq::set_zero(z);
+    fq::set_one(one);
+    fq::canon(one, one);
+    store_fe(o, z);
+    store_fe(o + 3, one);
+    store_fe(o + 6, z);
+}
+
+// Edwards affine (x, y) of the chunk's stored points i0 .. i0 + m - 1 (from the
+// standard-form input, GLV rows included); ok[j] is false for the affine identity
+// and points outside the map's domain, whose (x, y) is then left unset. Every lane
+// of the warp must call it (one inversion per warp).
+__device__ __forceinline__ void ed_affine_chunk(const uint4* __restrict__ in, size_t n, size_t np, size_t i0, int m,
+                                                fe (&xe)[kEdChunk], fe (&ye)[kEdChunk], bool (&ok)[kEdChunk]) {
     fe xs[kEdChunk], ys[kEdChunk], den[kEdChunk];
-    bool ok[kEdChunk];
     fe one, sp;
     fq::set_one(one);
     ed::load_const(sp, ed::kS);
-    fe acc = one;
     for (int j = 0; j < m; ++j) {
         glv_source(xs[j], ys[j], in, i0 + j, n, np);
         ok[j] = !(fq::is_zero_raw(xs[j]) && fq::is_zero_raw(ys[j]));
@@ -268,81 +320,117 @@ __global__ void __launch_bounds__(128) k_prepare_ed(const uint4* __restrict__ in
         fq::add(apl, a, sp);
         fq::mul(den[j], ys[j], apl);
         ok[j] = ok[j] && !fq::is_zero(den[j]);
-        if (ok[j]) fq::mul(acc, acc, den[j]);
     }
-    // warp prefix products P_l = acc_0 ... acc_l and suffix products S_l = acc_{l+1} ... acc_31
-    fe pre = acc, suf = one, y;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        y = shfl_fe_up(pre, off);
-        if (lane >= off) fq::mul(pre, pre, y);
-    }
-    fe sacc = acc;                         // inclusive suffix, then shifted
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        y = shfl_fe_down(sacc, off);
-        if (lane + off < 32) fq::mul(sacc, sacc, y);
-    }
-    suf = shfl_fe_down(sacc, 1);
-    if (lane == 31) suf = one;
-    fe total = shfl_fe(pre, 31);
-    fe tinv = one;
-    if (lane == 0) ec::inv(tinv, total);
-    tinv = shfl_fe(tinv, 0);
-    fe before = shfl_fe_up(pre, 1);        // P_{l-1}
-    if (lane == 0) before = one;
-    // inverse of this thread's product: acc^-1 = total^-1 * P_{l-1} * S_l
-    fe inv;
-    fq::mul(inv, tinv, before);
-    fq::mul(inv, inv, suf);
-    // walk back through the chunk: inverse of den[j] = inv * (product of den[0..j-1])
-    fe prefix[kEdChunk];
-    fe run = one;
+    warp_batch_inverse(den, ok, m);
     for (int j = 0; j < m; ++j) {
-        prefix[j] = run;
-        if (ok[j]) fq::mul(run, run, den[j]);
-    }
-    for (int j = m - 1; j >= 0; --j) {
-        uint4* o = out + (size_t)ModelEdwards::kStored * (i0 + j);
-        if (!ok[j]) {
-            fe z, o1;
-            fq::set_zero(z);
-            fq::canon(o1, one);
-            store_fe(o, z);
-            store_fe(o + 3, o1);
-            store_fe(o + 6, z);
-            continue;
-        }
-        fe dinv, c, a, xe, ye, u;
-        fq::mul(dinv, inv, prefix[j]);
-        fq::mul(inv, inv, den[j]);
+        if (!ok[j]) continue;
+        fe c, a;
         fq::add(a, xs[j], one);
         fq::add(c, a, sp);                  // a + s
-        fq::mul(xe, a, c);
+        fq::mul(xe[j], a, c);
         ed::load_const(c, ed::kC1);
-        fq::mul(xe, xe, c);
-        fq::mul(xe, xe, dinv);              // c1 a (a + s) / D
+        fq::mul(xe[j], xe[j], c);
+        fq::mul(xe[j], xe[j], den[j]);      // c1 a (a + s) / D
         fq::sub(c, a, sp);                  // a - s
-        fq::mul(ye, c, ys[j]);
-        fq::mul(ye, ye, dinv);              // (a - s) y / D
-        ed::load_const(c, ed::kK);
-        fq::mul(u, xe, ye);
-        fq::mul(u, u, c);
-        fq::canon(xe, xe);
-        fq::canon(ye, ye);
-        fq::canon(u, u);
-        store_fe(o, xe);
-        store_fe(o + 3, ye);
-        store_fe(o + 6, u);
+        fq::mul(ye[j], c, ys[j]);
+        fq::mul(ye[j], ye[j], den[j]);      // (a - s) y / D
+    }
+}
+
+__device__ __forceinline__ void store_ed_stored(uint4* o, fe x, fe y) {
+    fe u, k;
+    ed::load_const(k, ed::kK);
+    fq::mul(u, x, y);
+    fq::mul(u, u, k);
+    fq::canon(x, x);
+    fq::canon(y, y);
+    fq::canon(u, u);
+    store_fe(o, x);
+    store_fe(o + 3, y);
+    store_fe(o + 6, u);
+}
+
+// One warp covers 32 * kEdChunk consecutive stored points; every lane of every
+// launched warp takes part in the shuffles (lanes past np carry the product 1).
+__global__ void __launch_bounds__(128) k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n,
+                                                    size_t np) {
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t i0 = t * kEdChunk;
+    const int m = i0 >= np ? 0 : (int)(np - i0 < (size_t)kEdChunk ? np - i0 : (size_t)kEdChunk);
+    fe xe[kEdChunk], ye[kEdChunk];
+    bool ok[kEdChunk];
+    ed_affine_chunk(in, n, np, i0, m, xe, ye, ok);
+    for (int j = 0; j < m; ++j) {
+        uint4* o = out + (size_t)ModelEdwards::kStored * (i0 + j);
+        if (ok[j])
+            store_ed_stored(o, xe[j], ye[j]);
+        else
+            store_ed_identity(o);
+    }
+}
+
+// Fixed-base precomputation for resident Edwards sets: row q Wd + j of out is the
+// stored form of 2^(c j) P'_q for j < Wd, P' the np stored points of the
+// standard-form input (point-major, so the rows of a contiguous range of points are
+// contiguous). Each lane maps its chunk to Edwards, then doubles it c times per
+// window and normalises it with one inversion per warp and window. With these,
+// every window of an MSM adds into the same buckets:
+// sum_j 2^(cj) sum_b b B_jb = sum_b b sum_j B'_jb with B' over the shifted points.
+__global__ void __launch_bounds__(128) k_precompute_ed(const uint4* __restrict__ in, uint4* __restrict__ out,
+                                                       size_t n, size_t np, int c, int Wd) {
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t i0 = t * kEdChunk;
+    const int m = i0 >= np ? 0 : (int)(np - i0 < (size_t)kEdChunk ? np - i0 : (size_t)kEdChunk);
+    fe den[kEdChunk];
+    bool ok[kEdChunk];
+    ed::ext P[kEdChunk];
+    {
+        fe xe[kEdChunk], ye[kEdChunk];
+        ed_affine_chunk(in, n, np, i0, m, xe, ye, ok);
+        for (int q = 0; q < m; ++q) {
+            uint4* o = out + (size_t)ModelEdwards::kStored * ((i0 + q) * (size_t)Wd);
+            if (ok[q]) {
+                ed::stored Q;
+                Q.x = xe[q];
+                Q.y = ye[q];
+                ed::from_stored(P[q], Q);   // u unused by from_stored
+                store_ed_stored(o, xe[q], ye[q]);
+            } else {
+                ed::set_inf(P[q]);          // the identity stays the identity
+                store_ed_identity(o);
+            }
+        }
+    }
+    for (int j = 1; j < Wd; ++j) {
+        for (int q = 0; q < m; ++q) {
+            for (int d = 0; d < c; ++d) ed::dbl(P[q]);
+            den[q] = P[q].Z;
+            ok[q] = !fq::is_zero(P[q].Z);
+        }
+        warp_batch_inverse(den, ok, m);
+        for (int q = 0; q < m; ++q) {
+            uint4* o = out + (size_t)ModelEdwards::kStored * ((i0 + q) * (size_t)Wd + j);
+            if (!ok[q]) {
+                store_ed_identity(o);
+                continue;
+            }
+            fe x, y;
+            fq::mul(x, P[q].X, den[q]);
+            fq::mul(y, P[q].Y, den[q]);
+            store_ed_stored(o, x, y);
+        }
     }
 }
 
 // ---------------------------------------------------------------- stage 2
 
 // Window digits of one scalar (8 words, little-endian) for point index `idx`:
-// key = |digit| (0 = no contribution), value = idx | sign << 31, window-major.
+// key = |digit| (0 = no contribution), value = point | sign << 31, window-major
+// ([W][np]). The point is idx, or with precomputed shifted points (`pre`) the
+// copy 2^(c j) P_idx at row idx W + j, so the W windows form one bucket problem.
 __device__ __forceinline__ void emit_digits(const uint32_t (&s)[8], int c, int W, int sgn, size_t idx,
-                                            size_t np, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                            size_t np, int pre, uint32_t* __restrict__ keys,
+                                            uint32_t* __restrict__ vals) {
     const uint32_t cmask = (1u << c) - 1u, half = 1u << (c - 1);
     uint32_t carry = 0;
     for (int j = 0; j < W; ++j) {
@@ -368,7 +456,7 @@ __device__ __forceinline__ void emit_digits(const uint32_t (&s)[8], int c, int W
             key = raw;
         }
         keys[(size_t)j * np + idx] = key;
-        vals[(size_t)j * np + idx] = (uint32_t)idx | (neg << 31);
+        vals[(size_t)j * np + idx] = (uint32_t)(pre ? idx * (size_t)W + j : idx) | (neg << 31);
     }
 }
 
@@ -476,7 +564,7 @@ __device__ __forceinline__ void glv_split(uint32_t (&k)[8], uint32_t (&k1)[8], u
 }
 
 __global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int W, int sgn,
-                         int bits, int glv, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                         int bits, int glv, int pre, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                          int* __restrict__ status) {
     size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -494,13 +582,13 @@ __global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int
         if (over) atomicExch(status, MSM377_ERANGE);
     }
     if (!glv) {
-        emit_digits(s, c, W, sgn, i, n, keys, vals);
+        emit_digits(s, c, W, sgn, i, n, pre, keys, vals);
         return;
     }
     uint32_t k1[8], k2[8];
     glv_split(s, k1, k2);
-    emit_digits(k1, c, W, sgn, 2 * i, 2 * n, keys, vals);      // P_i
-    emit_digits(k2, c, W, sgn, 2 * i + 1, 2 * n, keys, vals);  // phi(P_i)
+    emit_digits(k1, c, W, sgn, 2 * i, 2 * n, pre, keys, vals);      // P_i
+    emit_digits(k2, c, W, sgn, 2 * i + 1, 2 * n, pre, keys, vals);  // phi(P_i)
 }
 
 // ---------------------------------------------------------------- stage 3: radix sort
@@ -901,7 +989,8 @@ __global__ void k_chain(const uint4* __restrict__ S, int w_hi, int w_lo, int W, 
     else
         M::load(acc, accp);
     for (int w = w_hi - 1; w >= w_lo; --w) {
-        for (int k = 0; k < c; ++k) M::dbl(acc);
+        if (w < W - 1)  // the top window starts from the identity
+            for (int k = 0; k < c; ++k) M::dbl(acc);
         M::add_mem(acc, S + (size_t)w * kXyzzVec);
     }
     if (w_lo > 0) {
@@ -951,7 +1040,8 @@ __global__ void __launch_bounds__(32) k_chain4(const uint4* __restrict__ S, int 
     ed::ext acc;
     ed::set_inf(acc);
     for (int w = W - 1; w >= 0; --w) {
-        for (int k = 0; k < c; ++k) ed::dbl4(acc, sh[g], l, true);
+        if (w < W - 1)  // the top window starts from the identity
+            for (int k = 0; k < c; ++k) ed::dbl4(acc, sh[g], l, true);
         ed::add4(acc, MemQE{S + (size_t)w * kXyzzVec}, sh[g], l, true);
     }
     if (lane != 0) return;
@@ -971,6 +1061,9 @@ struct Plan {
     size_t n;        // scalars (and input points)
     size_t np;       // stored points = items per window: n, or 2n with GLV
     int edw, glv;    // curve model (0 XYZZ, 1 Edwards); GLV split
+    int pre;         // precomputed shifted points: the Wd digit windows share one bucket set
+    int Wd;          // digit windows per scalar (W = 1 when pre, else W = Wd)
+    size_t items;    // items per pipeline window: np, or Wd np when pre
     int stored_vec;  // uint4 per stored point
     int user_bits;   // scalar range checked against opts.scalar_bits
     int c, sgn, bits, W;
@@ -997,10 +1090,11 @@ int ilog2(uint64_t v) {
 // Tuned window widths for signed digits by floor(log2 n) (0 = not tuned), one
 // table per mode (Edwards, GLV), set by msm_g1_set_window_table from a measured
 // table.
-std::atomic<int> g_ctable[4][32];
+std::atomic<int> g_ctable[8][32];
 
 int table_mode(uint32_t flags) {
-    return ((flags & MSM377_EDWARDS) ? 1 : 0) | ((flags & MSM377_GLV) ? 2 : 0);
+    return ((flags & MSM377_EDWARDS) ? 1 : 0) | ((flags & MSM377_GLV) ? 2 : 0) |
+           ((flags & MSM377_PRECOMPUTED) ? 4 : 0);
 }
 
 int default_c(size_t n, int sgn, uint32_t flags) {
@@ -1010,6 +1104,7 @@ int default_c(size_t n, int sgn, uint32_t flags) {
         if (t > 0) return t;
     }
     if (flags & MSM377_GLV) ++lg;  // 2n points per window
+    if (flags & MSM377_PRECOMPUTED) lg += 2;  // one bucket set for all windows: wider windows pay
     int c = lg - 4;
     if (!sgn) c = lg - 3;
     if (c < 4) c = 4;
@@ -1022,6 +1117,9 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->n = n;
     p->edw = (o->flags & MSM377_EDWARDS) ? 1 : 0;
     p->glv = (o->flags & MSM377_GLV) ? 1 : 0;
+    p->pre = (o->flags & MSM377_PRECOMPUTED) ? 1 : 0;
+    // precomputed sets are Edwards stored points made for one explicit c
+    if (p->pre && (!p->edw || !(o->flags & MSM377_POINTS_PREPARED) || o->c == 0)) return false;
     p->stored_vec = p->edw ? ModelEdwards::kStored : ModelXyzz::kStored;
     p->sgn = o->signed_digits ? 1 : 0;
     p->user_bits = o->scalar_bits ? o->scalar_bits : 256;
@@ -1032,17 +1130,21 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     if (n >= (1ull << 30)) return false;
     const size_t np = p->glv ? 2 * n : n;
     p->np = np;
-    p->W = p->sgn ? (p->bits + 1 + p->c - 1) / p->c : (p->bits + p->c - 1) / p->c;
+    p->Wd = p->sgn ? (p->bits + 1 + p->c - 1) / p->c : (p->bits + p->c - 1) / p->c;
+    p->W = p->pre ? 1 : p->Wd;
+    p->items = p->pre ? (size_t)p->Wd * np : np;
+    if (p->items >= (1ull << 31)) return false;
+    const size_t items = p->items;
     p->B = p->sgn ? (1u << (p->c - 1)) : ((1u << p->c) - 1u);
     p->Bp = p->sgn ? p->B : (1u << p->c);
     p->passes = (p->c + 7) / 8;
-    p->tiles = (np + kSortTile - 1) / kSortTile;
+    p->tiles = (items + kSortTile - 1) / kSortTile;
     // about 150 resident threads x 512 per SM worth of chunks over all windows
-    size_t K = ((size_t)p->W * np) / (152 * 512);
+    size_t K = ((size_t)p->W * items) / (152 * 512);
     if (K < 2) K = 2;
     if (K > 64) K = 64;
     p->K = (int)K;
-    p->cpw = (uint32_t)((np + K - 1) / K);
+    p->cpw = (uint32_t)((items + K - 1) / K);
     if (p->cpw == 0) p->cpw = 1;
     p->gw = p->W;
     p->ngroups = 1;
@@ -1067,10 +1169,10 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     const size_t chunks = (size_t)p->W * p->cpw;
     p->off_status = take(256);
     p->off_points = take(o->flags & MSM377_POINTS_PREPARED ? 0 : np * 16 * (size_t)p->stored_vec);
-    p->off_keys0 = take((size_t)p->W * np * 4);
-    p->off_vals0 = take((size_t)p->W * np * 4);
-    p->off_keys1 = take((size_t)p->W * np * 4);
-    p->off_vals1 = take((size_t)p->W * np * 4);
+    p->off_keys0 = take((size_t)p->W * items * 4);
+    p->off_vals0 = take((size_t)p->W * items * 4);
+    p->off_keys1 = take((size_t)p->W * items * 4);
+    p->off_vals1 = take((size_t)p->W * items * 4);
     p->off_hist = take((size_t)p->W * kRadix * (p->tiles ? p->tiles : 1) * 4);
     p->off_dtot = take((size_t)p->W * kRadix * 4);
     p->off_buckets = take((size_t)p->W * p->Bp * XY);
@@ -1123,8 +1225,9 @@ extern "C" int msm_g1_default_c(size_t n, int signed_digits, uint32_t flags) {
 extern "C" int msm_g1_set_window_table(const int32_t* c_by_log2n, int len, uint32_t flags) {
     if (len < 0 || len > 32 || (len > 0 && !c_by_log2n))
         return set_error(MSM377_EINVAL, "msm_g1_set_window_table: bad table (len %d)", len);
-    if (flags & ~(MSM377_EDWARDS | MSM377_GLV))
-        return set_error(MSM377_EINVAL, "msm_g1_set_window_table: flags 0x%x (only EDWARDS and GLV select a table)",
+    if (flags & ~(MSM377_EDWARDS | MSM377_GLV | MSM377_PRECOMPUTED))
+        return set_error(MSM377_EINVAL,
+                         "msm_g1_set_window_table: flags 0x%x (only EDWARDS, GLV and PRECOMPUTED select a table)",
                          flags);
     for (int k = 0; k < len; ++k)
         if (c_by_log2n[k] != 0 && (c_by_log2n[k] < 2 || c_by_log2n[k] > 20))
@@ -1164,6 +1267,36 @@ extern "C" int msm_points_prepare(const uint32_t* points_std, size_t n, uint32_t
     return msm_points_prepare_ex(points_std, n, out, 0, stream);
 }
 
+extern "C" size_t msm_points_precomputed_bytes(size_t n, const msm_opts* opts) {
+    if (!opts || !(opts->flags & MSM377_PRECOMPUTED)) return 0;
+    msm_opts o = *opts;
+    o.flags |= MSM377_POINTS_PREPARED;
+    Plan p;
+    if (!make_plan(n, &o, &p)) return 0;
+    return p.items * 16 * (size_t)ModelEdwards::kStored;
+}
+
+extern "C" int msm_points_precompute(const uint32_t* points_std, size_t n, uint32_t* out, const msm_opts* opts) {
+    if (!opts) return set_error(MSM377_EINVAL, "msm_points_precompute: opts is NULL");
+    if (msm_points_precomputed_bytes(n > 0 ? n : 1, opts) == 0)  // options valid (n = 0 needs 0 bytes)
+        return set_error(MSM377_EINVAL,
+                         "msm_points_precompute: needs MSM377_EDWARDS | MSM377_PRECOMPUTED, an explicit c and "
+                         "valid options (c=%d scalar_bits=%d)", opts->c, opts->scalar_bits);
+    if (n == 0) return MSM377_OK;
+    if (!points_std || !out || !aligned(points_std, 16) || !aligned(out, 16))
+        return set_error(MSM377_EINVAL, "msm_points_precompute: null or non-16-byte-aligned pointer");
+    msm_opts o = *opts;
+    o.flags |= MSM377_POINTS_PREPARED;
+    Plan p;
+    make_plan(n, &o, &p);
+    cudaStream_t s = as_stream(opts->stream);
+    const size_t threads = (p.np + kEdChunk - 1) / kEdChunk;  // whole warps: grid_for rounds up to 128
+    k_precompute_ed<<<grid_for(threads, 128), 128, 0, s>>>(reinterpret_cast<const uint4*>(points_std),
+                                                           reinterpret_cast<uint4*>(out), n, p.np, p.c, p.Wd);
+    note_launches(1);
+    return check_launch("msm_points_precompute");
+}
+
 namespace {
 
 // Phase 1-3 of one MSM on stream s: status reset, preparation, digits, sort,
@@ -1179,11 +1312,11 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
         launch_prepare(pts, prep, n, opts->flags, s);
         pts = prep;
     }
-    const size_t np = p.np;
+    const size_t np = p.items;  // items per pipeline window
     uint32_t* keys[2] = {at<uint32_t>(workspace, p.off_keys0), at<uint32_t>(workspace, p.off_keys1)};
     uint32_t* vals[2] = {at<uint32_t>(workspace, p.off_vals0), at<uint32_t>(workspace, p.off_vals1)};
-    k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.W,
-                                              p.sgn, p.user_bits, p.glv, keys[0], vals[0], status);
+    k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.Wd,
+                                              p.sgn, p.user_bits, p.glv, p.pre, keys[0], vals[0], status);
     note_launches(1);
     uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
     uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);

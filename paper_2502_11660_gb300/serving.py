@@ -23,7 +23,8 @@ import time
 import numpy as np
 import torch
 
-from . import msm_g1, msm_g1_workspace, msm_points_prepare, g1_generator_mul, to_device, to_host
+from . import (msm_g1, msm_g1_workspace, msm_points_precompute, msm_points_prepare, g1_generator_mul,
+               to_device, to_host)
 
 
 @dataclasses.dataclass
@@ -57,26 +58,35 @@ class ResidentSets:
     """Resident point sets P_i = s_i G in prepared form on the device (XYZZ Montgomery
     affine, or the Edwards stored form; with GLV interleaved with phi(P_i))."""
 
-    def __init__(self, seeds: list[np.ndarray], device="cuda", edwards: bool = False, glv: bool = False):
-        self.edwards, self.glv = edwards, glv
+    def __init__(self, seeds: list[np.ndarray], device="cuda", edwards: bool = False, glv: bool = False,
+                 precompute_c: int = 0):
+        """precompute_c > 0: fixed-base sets (Edwards, 2^(c j) P_i for every window j) made for
+        that window width, which every request then uses."""
+        self.edwards, self.glv, self.c = edwards or precompute_c > 0, glv, precompute_c
         self.sets = []
         for s in seeds:
             pts = g1_generator_mul(to_device(s, device))
-            self.sets.append(msm_points_prepare(pts, edwards=edwards, glv=glv))
+            if precompute_c:
+                self.sets.append(msm_points_precompute(pts, c=precompute_c, scalar_bits=253, glv=glv))
+            else:
+                self.sets.append(msm_points_prepare(pts, edwards=edwards, glv=glv))
             del pts
         torch.cuda.synchronize(device)
+        n0 = seeds[0].shape[0] if seeds else 0
+        self.rows_per_point = (self.sets[0].shape[0] // n0) if (seeds and n0) else 1
 
     def slice(self, set_id: int, offset: int, n: int) -> torch.Tensor:
-        st = self.sets[set_id]
-        if not self.glv:
-            return st[offset:offset + n]
-        return st[2 * offset:2 * (offset + n)]   # rows P_i, phi(P_i) interleaved
+        # stored rows are point-major (GLV halves and precomputed windows of a point are adjacent)
+        r = self.rows_per_point
+        return self.sets[set_id][r * offset:r * (offset + n)]
 
 
 class MsmServer:
     def __init__(self, sets: ResidentSets, slots: int = 8, mem_budget: int | None = None, c: int = 0,
                  device="cuda"):
         self.sets = sets
+        if sets.c:
+            c = sets.c          # precomputed sets fix the window width
         self.device = torch.device(device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         if mem_budget is None:
@@ -88,20 +98,21 @@ class MsmServer:
     def footprint(self, n: int) -> int:
         from . import _opts, lib
         import ctypes
-        o = _opts(self.c, True, 253, True, edwards=self.sets.edwards, glv=self.sets.glv)
+        o = _opts(self.c, True, 253, True, edwards=self.sets.edwards, glv=self.sets.glv,
+                  precomputed=self.sets.c > 0)
         return int(lib().msm_g1_workspace_bytes(n, ctypes.byref(o))) + 32 * n + 96
 
     def _launch(self, req: Request, slot: int):
         st = self.streams[slot]
         with torch.cuda.stream(st):
             sc = device_scalars(req.n, req.seed, self.device)
-            ed, gl = self.sets.edwards, self.sets.glv
+            ed, gl, pre = self.sets.edwards, self.sets.glv, self.sets.c > 0
             ws = msm_g1_workspace(req.n, c=self.c, scalar_bits=253, prepared=True, device=self.device,
-                                  edwards=ed, glv=gl)
+                                  edwards=ed, glv=gl, precomputed=pre)
             out = torch.empty(24, dtype=torch.int32, device=self.device)
             pts = self.sets.slice(req.set_id, req.offset, req.n)
             msm_g1(pts, sc, out=out, workspace=ws, c=self.c, scalar_bits=253, prepared=True, stream=st,
-                   edwards=ed, glv=gl)
+                   edwards=ed, glv=gl, precomputed=pre)
             ev = torch.cuda.Event()
             ev.record(st)
         return {"req": req, "slot": slot, "event": ev, "out": out, "tensors": (sc, ws),

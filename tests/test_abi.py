@@ -164,3 +164,23 @@ def test_barrett_constant_matches_the_oracle():
     k, mu = barrett.barrett_params(fq.P)
     assert k == 377
     assert _const_limbs(src, "kMuB") == mu
+
+
+def test_precomputed_options():
+    import paper_2502_11660_gb300 as pkg
+    L = pkg.lib()
+    n = 1000
+    # explicit c and the Edwards model are required
+    assert L.msm_points_precomputed_bytes(n, ctypes.byref(pkg._opts(c=0, scalar_bits=253, edwards=True,
+                                                                      precomputed=True))) == 0
+    assert L.msm_points_precomputed_bytes(n, ctypes.byref(pkg._opts(c=16, scalar_bits=253, precomputed=True))) == 0
+    W = -(-(253 + 1) // 16)
+    assert pkg.msm_points_precomputed_bytes(n, 16, 253) == W * n * 144
+    assert pkg.msm_points_precomputed_bytes(n, 16, 253, glv=True) == -(-(127 + 1) // 16) * 2 * n * 144
+    # one window in the pipeline: the key buffers hold W n items, the buckets one window
+    o = pkg._opts(c=16, scalar_bits=253, prepared=True, edwards=True, precomputed=True)
+    assert L.msm_g1_workspace_bytes(n, ctypes.byref(o)) > 0
+    o2 = pkg._opts(c=16, scalar_bits=253, edwards=True, precomputed=True)   # not prepared: rejected
+    assert L.msm_g1_workspace_bytes(n, ctypes.byref(o2)) == 0
+    assert L.msm_points_precompute(None, n, None, ctypes.byref(pkg._opts(c=0, edwards=True,
+                                                                          precomputed=True))) == -1

@@ -181,3 +181,86 @@ def test_batched_and_graph(edw, split):
     torch.cuda.synchronize()
     for i, o in enumerate(outs):
         assert g1.from_limbs(pkg.to_host(o)) == closed_form_limbs(data[i][1], new[i]), f"job {i}"
+
+
+# ---------------------------------------------------------------- fixed-base precomputation
+
+@pytest.mark.parametrize("split", [False, True], ids=["plain", "glv"])
+@pytest.mark.parametrize("n", [1, 17, 1000, 2049])
+@pytest.mark.parametrize("c,signed", [(4, True), (8, True), (12, True), (7, False)])
+def test_precomputed_small_n(split, n, c, signed):
+    a, s, pts = msm_inputs(n, tag=100 + n)
+    want = closed_form_limbs(s, a)
+    pre = pkg.msm_points_precompute(pkg.to_device(pts), c=c, scalar_bits=253, signed=signed, glv=split)
+    out = pkg.msm_g1(pre, pkg.to_device(a), c=c, signed=signed, scalar_bits=253, edwards=True, glv=split,
+                     precomputed=True)
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == want
+
+
+def test_precomputed_rows_are_shifted_points():
+    """Row i W + j of the set is the stored form of 2^(c j) P_i (oracle's Edwards map)."""
+    n, c = 40, 9
+    _, s, pts = msm_inputs(n, tag=14)
+    pts = pts.copy()
+    pts[3] = 0
+    pre = pkg.to_host(pkg.msm_points_precompute(pkg.to_device(pts), c=c, scalar_bits=253)).reshape(-1, 36)
+    W = -(-(253 + 1) // c)
+    assert pre.shape[0] == W * n
+    for j in (0, 1, W - 1):
+        for i in (0, 3, n - 1):
+            P = None if i == 3 else g1.mul(1 << (c * j), g1.from_limbs(pts[i]))
+            want = list(edwards.stored_point(edwards.from_weierstrass(P)))
+            assert _mont_ints(pre[i * W + j].reshape(3, 12)) == want, (j, i)
+
+
+@pytest.mark.parametrize("split", [False, True], ids=["plain", "glv"])
+def test_precomputed_edges_and_full_width(split):
+    n = 700
+    a, s, pts = msm_inputs(n, tag=7)
+    a, s, pts = a.copy(), s.copy(), pts.copy()
+    a[0:10] = 0
+    a[10] = synth.int_to_limbs(fq.R - 1, 8)
+    a[11] = synth.int_to_limbs(2 ** 256 - 1, 8)
+    pts[40] = 0
+    s[40] = 0
+    want = closed_form_limbs(s, a)
+    for c in (5, 13):
+        pre = pkg.msm_points_precompute(pkg.to_device(pts), c=c, scalar_bits=256, glv=split)
+        out = pkg.msm_g1(pre, pkg.to_device(a), c=c, scalar_bits=256, edwards=True, glv=split, precomputed=True)
+        torch.cuda.synchronize()
+        assert g1.from_limbs(pkg.to_host(out)) == want
+
+
+def test_precomputed_heavy_bucket_and_batched():
+    n = 5000
+    a, s, pts = msm_inputs(n, tag=8)
+    a = np.tile(a[:1], (n, 1))
+    pre = pkg.msm_points_precompute(pkg.to_device(pts), c=16, scalar_bits=253)
+    out = pkg.msm_g1(pre, pkg.to_device(a), c=16, scalar_bits=253, edwards=True, precomputed=True)
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == closed_form_limbs(s, a)
+    sizes, cs = [1, 333, 2049, 0], [6, 11, 14, 9]
+    data = [msm_inputs(m, tag=78000 + i) for i, m in enumerate(sizes)]
+    pres = [pkg.msm_points_precompute(pkg.to_device(p), c=cc, scalar_bits=253)
+            for (_, _, p), cc in zip(data, cs)]
+    outs = pkg.msm_g1_batched(pres, [pkg.to_device(x) for x, _, _ in data], c_list=cs, scalar_bits=253,
+                              edwards=True, precomputed=True)
+    torch.cuda.synchronize()
+    for i, o in enumerate(outs):
+        assert g1.from_limbs(pkg.to_host(o)) == closed_form_limbs(data[i][1], data[i][0]), f"job {i}"
+
+
+@pytest.mark.parametrize("c", [16, 19])
+def test_precomputed_full_size_2e20(c):
+    n = 1 << 20
+    a, s, pts = msm_inputs(n, tag=2)
+    want = closed_form_limbs(s, a)
+    pre = pkg.msm_points_precompute(pkg.to_device(pts), c=c, scalar_bits=253)
+    da = pkg.to_device(a)
+    ws = pkg.msm_g1_workspace(n, c=c, scalar_bits=253, edwards=True, precomputed=True)
+    for _ in range(2):
+        out = pkg.msm_g1(pre, da, workspace=ws, c=c, scalar_bits=253, edwards=True, precomputed=True)
+        torch.cuda.synchronize()
+        assert g1.from_limbs(pkg.to_host(out)) == want
+    assert pkg.msm_g1_status(ws) == 0

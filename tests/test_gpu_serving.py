@@ -72,3 +72,14 @@ def test_edwards_glv_sets_serve_the_same_results(sets):
     b = serving.MsmServer(rs2, slots=4).run(reqs, realtime=False)
     for r in reqs:
         assert np.array_equal(a["results"][r.rid], b["results"][r.rid]), f"request {r.rid}"
+
+
+def test_precomputed_sets_serve_the_same_results(sets):
+    """Fixed-base resident sets (point-major rows): slices give the same exact results."""
+    seeds, rs = sets
+    rs3 = serving.ResidentSets(seeds, precompute_c=11, glv=True)
+    reqs = _requests(12, tag=74)
+    a = serving.MsmServer(rs, slots=4).run(reqs, realtime=False)
+    b = serving.MsmServer(rs3, slots=4).run(reqs, realtime=False)
+    for r in reqs:
+        assert np.array_equal(a["results"][r.rid], b["results"][r.rid]), f"request {r.rid}"
