@@ -83,20 +83,22 @@ __device__ __forceinline__ void from_stored(ext& P, const stored& Q) {
 // A = (Y1 - X1)(y2 - x2), B = (Y1 + X1)(y2 + x2), C = T1 u2, D = 2 Z1,
 // E = B - A, F = D - C, G = D + C, H = B + A,
 // X3 = E F, Y3 = G H, T3 = E H, Z3 = F G.
+// Values that only feed multiplications are left unfolded (fq::add_nr / sub_nr):
+// Y1 -+ X1, y2 -+ x2, E, H < 4p; D < 4p; F, G < 6p; every product below 36 p^2.
 __device__ __forceinline__ void madd(ext& P, const stored& Q) {
     fe A, B, t, u;
-    fq::sub(t, P.Y, P.X);
-    fq::sub(u, Q.y, Q.x);
+    fq::sub_nr<2>(t, P.Y, P.X);
+    fq::sub_nr<2>(u, Q.y, Q.x);
     fq::mul(A, t, u);
-    fq::add(t, P.Y, P.X);
-    fq::add(u, Q.y, Q.x);
+    fq::add_nr(t, P.Y, P.X);
+    fq::add_nr(u, Q.y, Q.x);
     fq::mul(B, t, u);
     fq::mul(t, P.T, Q.u);           // C
-    fq::dbl(u, P.Z);                // D
-    fq::sub(P.X, B, A);             // E
-    fq::add(P.Y, B, A);             // H
-    fq::sub(A, u, t);               // F
-    fq::add(B, u, t);               // G
+    fq::add_nr(u, P.Z, P.Z);        // D
+    fq::sub_nr<2>(P.X, B, A);       // E
+    fq::add_nr(P.Y, B, A);          // H
+    fq::sub_nr<2>(A, u, t);         // F = D - C + 2p
+    fq::add_nr(B, u, t);            // G
     fq::mul(P.T, P.X, P.Y);         // T3 = E H
     fq::mul(P.X, P.X, A);           // X3 = E F
     fq::mul(P.Y, B, P.Y);           // Y3 = G H
@@ -122,11 +124,11 @@ __device__ __forceinline__ void add_q(ext& P, const QL& q) {
     fe A, B, t, u;
     q.Y(u);
     q.X(t);
-    fq::sub(A, u, t);
-    fq::add(B, u, t);
-    fq::sub(t, P.Y, P.X);
+    fq::sub_nr<2>(A, u, t);
+    fq::add_nr(B, u, t);
+    fq::sub_nr<2>(t, P.Y, P.X);
     fq::mul(A, t, A);
-    fq::add(t, P.Y, P.X);
+    fq::add_nr(t, P.Y, P.X);
     fq::mul(B, t, B);
     q.T(t);
     load_const(u, kK);
@@ -134,11 +136,11 @@ __device__ __forceinline__ void add_q(ext& P, const QL& q) {
     fq::mul(t, P.T, t);             // C
     q.Z(u);
     fq::mul(u, P.Z, u);
-    fq::dbl(u, u);                  // D
-    fq::sub(P.X, B, A);             // E
-    fq::add(P.Y, B, A);             // H
-    fq::sub(A, u, t);               // F
-    fq::add(B, u, t);               // G
+    fq::add_nr(u, u, u);            // D
+    fq::sub_nr<2>(P.X, B, A);       // E
+    fq::add_nr(P.Y, B, A);          // H
+    fq::sub_nr<2>(A, u, t);         // F
+    fq::add_nr(B, u, t);            // G
     fq::mul(P.T, P.X, P.Y);
     fq::mul(P.X, P.X, A);
     fq::mul(P.Y, B, P.Y);
@@ -157,20 +159,23 @@ __device__ __forceinline__ void add(ext& P, const ext& Q) { add_q(P, RegQ{&Q}); 
 
 // P = 2P (a = -1): A = X^2, B = Y^2, C = 2 Z^2, D = -A, E = (X + Y)^2 - A - B,
 // G = D + B, F = G - C, H = D - B, X3 = E F, Y3 = G H, T3 = E H, Z3 = F G.
+// Unfolded: X + Y, 2 Z^2, G, H < 4p; E < 6p; F = G - 2 Z^2 + 4p < 8p; products below 48 p^2.
 __device__ __forceinline__ void dbl(ext& P) {
     fe A, B, C, t;
     fq::sqr(A, P.X);
     fq::sqr(B, P.Y);
     fq::sqr(C, P.Z);
-    fq::dbl(C, C);
-    fq::add(t, P.X, P.Y);
+    fq::add_nr(C, C, C);
+    fq::add_nr(t, P.X, P.Y);
     fq::sqr(t, t);
-    fq::sub(t, t, A);
-    fq::sub(t, t, B);               // E
-    fq::sub(P.Y, B, A);             // G = B - A
-    fq::neg(A, A);
-    fq::sub(A, A, B);               // H = -A - B
-    fq::sub(C, P.Y, C);             // F = G - C
+    fq::sub_nr<2>(t, t, A);
+    fq::sub_nr<2>(t, t, B);         // E
+    fq::sub_nr<2>(P.Y, B, A);       // G = B - A
+    fe z;
+    fq::set_zero(z);
+    fq::sub_nr<2>(A, z, A);
+    fq::sub_nr<2>(A, A, B);         // H = -A - B
+    fq::sub_nr<4>(C, P.Y, C);       // F = G - C
     fq::mul(P.T, t, A);             // E H
     fq::mul(P.X, t, C);             // E F
     fq::mul(P.Z, C, P.Y);           // F G
@@ -208,18 +213,19 @@ __device__ __forceinline__ fe pick4(int l, const fe& a, const fe& b, const fe& c
 // P = 2P: level 1 {X^2, Y^2, Z^2, (X + Y)^2}, level 2 {E F, G H, E H, F G}.
 __device__ __forceinline__ void dbl4(ext& P, fe* sh, int l, bool writer) {
     fe s, r, v[4];
-    fq::add(s, P.X, P.Y);
+    fq::add_nr(s, P.X, P.Y);
     const fe x = pick4(l, P.X, P.Y, P.Z, s);
     fq::sqr(r, x);
     xchg4(v, r, sh, l, writer);     // A, B, Z^2, (X + Y)^2
-    fe E, G, H, F;
-    fq::sub(E, v[3], v[0]);
-    fq::sub(E, E, v[1]);            // E = (X + Y)^2 - A - B
-    fq::sub(G, v[1], v[0]);         // G = B - A
-    fq::neg(H, v[0]);
-    fq::sub(H, H, v[1]);            // H = -A - B
-    fq::dbl(F, v[2]);
-    fq::sub(F, G, F);               // F = G - 2 Z^2
+    fe E, G, H, F, z;
+    fq::sub_nr<2>(E, v[3], v[0]);
+    fq::sub_nr<2>(E, E, v[1]);      // E = (X + Y)^2 - A - B
+    fq::sub_nr<2>(G, v[1], v[0]);   // G = B - A
+    fq::set_zero(z);
+    fq::sub_nr<2>(H, z, v[0]);
+    fq::sub_nr<2>(H, H, v[1]);      // H = -A - B
+    fq::add_nr(F, v[2], v[2]);
+    fq::sub_nr<4>(F, G, F);         // F = G - 2 Z^2 (ranges as in dbl)
     const fe a = pick4(l, E, G, E, F);
     const fe b = pick4(l, F, H, H, G);
     fq::mul(r, a, b);
@@ -240,10 +246,10 @@ __device__ __forceinline__ void add4(ext& P, const QL& q, fe* sh, int l, bool wr
     q.Z(Z2);
     q.T(T2);
     fe a0, b0, a1, b1;
-    fq::sub(a0, P.Y, P.X);
-    fq::sub(b0, Y2, X2);
-    fq::add(a1, P.Y, P.X);
-    fq::add(b1, Y2, X2);
+    fq::sub_nr<2>(a0, P.Y, P.X);
+    fq::sub_nr<2>(b0, Y2, X2);
+    fq::add_nr(a1, P.Y, P.X);
+    fq::add_nr(b1, Y2, X2);
     const fe x = pick4(l, a0, a1, P.T, P.Z);
     const fe y = pick4(l, b0, b1, T2, Z2);
     fq::mul(r, x, y);
@@ -251,11 +257,11 @@ __device__ __forceinline__ void add4(ext& P, const QL& q, fe* sh, int l, bool wr
     load_const(u, kK);
     fq::mul(w, v[2], u);            // C = k T1 T2 (every lane; one latency)
     fe E, F, G, H, D;
-    fq::dbl(D, v[3]);
-    fq::sub(E, v[1], v[0]);
-    fq::add(H, v[1], v[0]);
-    fq::sub(F, D, w);
-    fq::add(G, D, w);
+    fq::add_nr(D, v[3], v[3]);
+    fq::sub_nr<2>(E, v[1], v[0]);
+    fq::add_nr(H, v[1], v[0]);
+    fq::sub_nr<2>(F, D, w);
+    fq::add_nr(G, D, w);
     const fe a = pick4(l, E, G, E, F);
     const fe b = pick4(l, F, H, H, G);
     fq::mul(r, a, b);
@@ -270,20 +276,20 @@ __device__ __forceinline__ void add4(ext& P, const QL& q, fe* sh, int l, bool wr
 // {E F, G H, E H, F G}: two multiplication latencies per mixed addition.
 __device__ __forceinline__ void madd4(ext& P, const stored& Q, fe* sh, int l, bool writer) {
     fe a0, b0, a1, b1, r, v[4];
-    fq::sub(a0, P.Y, P.X);
-    fq::sub(b0, Q.y, Q.x);
-    fq::add(a1, P.Y, P.X);
-    fq::add(b1, Q.y, Q.x);
+    fq::sub_nr<2>(a0, P.Y, P.X);
+    fq::sub_nr<2>(b0, Q.y, Q.x);
+    fq::add_nr(a1, P.Y, P.X);
+    fq::add_nr(b1, Q.y, Q.x);
     const fe x = pick4(l, a0, a1, P.T, P.T);
     const fe y = pick4(l, b0, b1, Q.u, Q.u);
     fq::mul(r, x, y);
     xchg4(v, r, sh, l, writer);     // A, B, C, C
     fe E, F, G, H, D;
-    fq::dbl(D, P.Z);
-    fq::sub(E, v[1], v[0]);
-    fq::add(H, v[1], v[0]);
-    fq::sub(F, D, v[2]);
-    fq::add(G, D, v[2]);
+    fq::add_nr(D, P.Z, P.Z);
+    fq::sub_nr<2>(E, v[1], v[0]);
+    fq::add_nr(H, v[1], v[0]);
+    fq::sub_nr<2>(F, D, v[2]);
+    fq::add_nr(G, D, v[2]);
     const fe a = pick4(l, E, G, E, F);
     const fe b = pick4(l, F, H, H, G);
     fq::mul(r, a, b);

@@ -250,6 +250,93 @@ __device__ __forceinline__ void sub(fe& rr, const fe& a, const fe& bb) {
 
 __device__ __forceinline__ void dbl(fe& r, const fe& a) { add(r, a, a); }
 
+// Unfolded add / subtract for values that only feed multiplications. mul() stays
+// exact and lands in [0, 2p) for a b < p R (R / p > 152), so an operand may be a
+// few multiples of p: add_nr of two values below 2p is below 4p, sub_nr<K> of
+// a, b is a - b + K p (needs b <= a + K p), and the callers keep every product
+// below 152 p^2 (ed.cuh states the ranges per formula). One carry chain (add_nr)
+// or two (sub_nr) instead of the folded forms' chains, masks and selects.
+__device__ __forceinline__ void add_nr(fe& rr, const fe& a, const fe& bb) {
+    uint32_t r[N];
+    const uint32_t* b = bb.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r[k] = a.v[k];
+    asm(
+        "add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, %13;\n\t"
+        "addc.cc.u32 %2, %2, %14;\n\t"
+        "addc.cc.u32 %3, %3, %15;\n\t"
+        "addc.cc.u32 %4, %4, %16;\n\t"
+        "addc.cc.u32 %5, %5, %17;\n\t"
+        "addc.cc.u32 %6, %6, %18;\n\t"
+        "addc.cc.u32 %7, %7, %19;\n\t"
+        "addc.cc.u32 %8, %8, %20;\n\t"
+        "addc.cc.u32 %9, %9, %21;\n\t"
+        "addc.cc.u32 %10, %10, %22;\n\t"
+        "addc.u32 %11, %11, %23;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
+#pragma unroll
+    for (int k = 0; k < N; ++k) rr.v[k] = r[k];
+}
+
+template <int K>
+__device__ __forceinline__ void sub_nr(fe& rr, const fe& a, const fe& bb) {
+    static_assert(K == 2 || K == 4, "sub_nr adds 2p or 4p");
+    uint32_t r[N];
+    const uint32_t* b = bb.v;
+#pragma unroll
+    for (int k = 0; k < N; ++k) r[k] = a.v[k];
+    if constexpr (K == 2) {
+        asm(
+        "add.cc.u32 %0, %0, 0x00000002;\n\t"
+        "addc.cc.u32 %1, %1, 0x0a118000;\n\t"
+        "addc.cc.u32 %2, %2, 0x60000001;\n\t"
+        "addc.cc.u32 %3, %3, 0x2e16ba88;\n\t"
+        "addc.cc.u32 %4, %4, 0x74129000;\n\t"
+        "addc.cc.u32 %5, %5, 0x3de6c45f;\n\t"
+        "addc.cc.u32 %6, %6, 0x01ea271e;\n\t"
+        "addc.cc.u32 %7, %7, 0x3445b3e6;\n\t"
+        "addc.cc.u32 %8, %8, 0xd9429276;\n\t"
+        "addc.cc.u32 %9, %9, 0x8c760b80;\n\t"
+        "addc.cc.u32 %10, %10, 0x2f8a21d5;\n\t"
+        "addc.u32 %11, %11, 0x035c748c;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]));
+    } else {
+        asm(
+        "add.cc.u32 %0, %0, 0x00000004;\n\t"
+        "addc.cc.u32 %1, %1, 0x14230000;\n\t"
+        "addc.cc.u32 %2, %2, 0xc0000002;\n\t"
+        "addc.cc.u32 %3, %3, 0x5c2d7510;\n\t"
+        "addc.cc.u32 %4, %4, 0xe8252000;\n\t"
+        "addc.cc.u32 %5, %5, 0x7bcd88be;\n\t"
+        "addc.cc.u32 %6, %6, 0x03d44e3c;\n\t"
+        "addc.cc.u32 %7, %7, 0x688b67cc;\n\t"
+        "addc.cc.u32 %8, %8, 0xb28524ec;\n\t"
+        "addc.cc.u32 %9, %9, 0x18ec1701;\n\t"
+        "addc.cc.u32 %10, %10, 0x5f1443ab;\n\t"
+        "addc.u32 %11, %11, 0x06b8e918;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]));
+    }
+    asm(
+        "sub.cc.u32 %0, %0, %12;\n\t"
+        "subc.cc.u32 %1, %1, %13;\n\t"
+        "subc.cc.u32 %2, %2, %14;\n\t"
+        "subc.cc.u32 %3, %3, %15;\n\t"
+        "subc.cc.u32 %4, %4, %16;\n\t"
+        "subc.cc.u32 %5, %5, %17;\n\t"
+        "subc.cc.u32 %6, %6, %18;\n\t"
+        "subc.cc.u32 %7, %7, %19;\n\t"
+        "subc.cc.u32 %8, %8, %20;\n\t"
+        "subc.cc.u32 %9, %9, %21;\n\t"
+        "subc.cc.u32 %10, %10, %22;\n\t"
+        "subc.u32 %11, %11, %23;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
+#pragma unroll
+    for (int k = 0; k < N; ++k) rr.v[k] = r[k];
+}
+
 // [0, 2p) -> [0, p)
 __device__ __forceinline__ void canon(fe& rr, const fe& a) {
     uint32_t u[N], mask;
