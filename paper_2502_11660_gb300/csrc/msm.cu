@@ -831,36 +831,33 @@ __global__ void __launch_bounds__(128) k_accumulate_batched(const __grid_constan
 // Partial sums of runs that cross chunk edges are combined in log depth, so a
 // bucket holding a large share of the window (all-equal scalars, a nearly empty
 // top window) costs O(log) serial additions, not O(chunks):
-//  * k_merge_scan: start[u] = the last chunk t < u whose run leaves it (a tail),
-//    a prefix maximum per window (one block per window);
+//  * k_merge_start: for a chunk u whose first run continues an earlier chunk's
+//    run, start[u] = the chunk t0 where that run begins (its tail): the run's key
+//    first occurs at lower_bound(keys, key) in the sorted window, so t0 is that
+//    position / K (one binary search per chunk, no scan);
 //  * k_merge_round(d): for heads at offset j = u - start[u] - 1 with j % 2d == 0,
 //    head[u] += head[u + d] when u + d continues the same run; ceil(log2 cpw) rounds
 //    leave each run's sum of heads at its first head;
 //  * k_merge_final: bucket = tail[start] + that sum.
-constexpr int kScanThreads = 1024;
-
-__global__ void __launch_bounds__(kScanThreads) k_merge_scan(AccArgs a, int32_t* __restrict__ start) {
-    __shared__ int32_t part[kScanThreads];
-    const int w = a.w0 + blockIdx.x;
-    const size_t base = (size_t)w * a.cpw;
-    const uint32_t per = (a.cpw + kScanThreads - 1) / kScanThreads;
-    const uint32_t lo = threadIdx.x * per;
-    int32_t m = -1;
-    for (uint32_t u = lo; u < lo + per && u < a.cpw; ++u)
-        if (a.tailkey[base + u] != kNone) m = (int32_t)u;
-    part[threadIdx.x] = m;
-    __syncthreads();
-    for (int off = 1; off < kScanThreads; off <<= 1) {  // inclusive max-scan of the partials
-        int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : -1;
-        __syncthreads();
-        if (v > part[threadIdx.x]) part[threadIdx.x] = v;
-        __syncthreads();
+__global__ void k_merge_start(AccArgs a, int32_t* __restrict__ start) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)a.nwin * a.cpw) return;
+    const int w = a.w0 + (int)(id / a.cpw);
+    const uint32_t u = (uint32_t)(id % a.cpw);
+    const size_t ci = (size_t)w * a.cpw + u;
+    if (a.headflag[ci] == 0) {
+        start[ci] = -1;
+        return;
     }
-    int32_t run = threadIdx.x > 0 ? part[threadIdx.x - 1] : -1;  // exclusive prefix
-    for (uint32_t u = lo; u < lo + per && u < a.cpw; ++u) {
-        start[base + u] = run;   // last tail strictly before u
-        if (a.tailkey[base + u] != kNone) run = (int32_t)u;
+    const uint32_t* keys = a.keys + (size_t)w * a.n;
+    const size_t first = (size_t)u * a.K;   // u > 0 here: chunk 0 has no earlier run
+    const uint32_t key = keys[first];
+    size_t lo = 0, hi = first;              // first index in [0, first] with keys[i] >= key
+    while (lo < hi) {
+        const size_t mid = (lo + hi) >> 1;
+        if (keys[mid] < key) lo = mid + 1; else hi = mid;
     }
+    start[ci] = (int32_t)(lo / (size_t)a.K);
 }
 
 template <class M>
@@ -1139,8 +1136,14 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->Bp = p->sgn ? p->B : (1u << p->c);
     p->passes = (p->c + 7) / 8;
     p->tiles = (items + kSortTile - 1) / kSortTile;
-    // about 150 resident threads x 512 per SM worth of chunks over all windows
-    size_t K = ((size_t)p->W * items) / (152 * 512);
+    // Chunks of K <= 64 items, one per thread, sized so that the chunks over all
+    // windows fill whole waves of resident accumulation threads (152 SMs x 3 blocks
+    // of 128 on a GB300): m waves of K items rather than a last, partly idle wave.
+    constexpr size_t kWave = 152 * 384;
+    const size_t total = (size_t)p->W * items;
+    size_t waves = (total + 64 * kWave - 1) / (64 * kWave);
+    if (waves < 1) waves = 1;
+    size_t K = (total + waves * kWave - 1) / (waves * kWave);
     if (K < 2) K = 2;
     if (K > 64) K = 64;
     p->K = (int)K;
@@ -1365,7 +1368,7 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     const size_t nchunks = (size_t)p.W * p.cpw;
     // 5. merge partial sums of runs crossing chunk edges (log depth)
     int32_t* start = at<int32_t>(workspace, p.off_start);
-    k_merge_scan<<<p.W, kScanThreads, 0, s>>>(a, start);
+    k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start);
     note_launches(1);
     for (uint32_t d = 1; d < p.cpw; d <<= 1) {
         k_merge_round<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d);
