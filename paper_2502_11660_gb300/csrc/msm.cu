@@ -49,7 +49,6 @@ constexpr uint32_t kNone = 0xffffffffu;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
-constexpr int kRadix = 256;
 constexpr int kXyzzVec = 12;                // XYZZ in memory: 4 x 12 packed words = 12 uint4
 constexpr size_t kXyzzBytes = kXyzzVec * 16;
 
@@ -593,21 +592,24 @@ __global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int
 
 // ---------------------------------------------------------------- stage 3: radix sort
 
+// Digits of RB bits per pass, R = 2^RB bins (the library sorts 8 bits per pass).
+template <int RB>
 __global__ void k_sort_hist(const uint32_t* __restrict__ keys, size_t n, int shift, size_t tiles,
                             uint32_t* __restrict__ hist) {
-    __shared__ uint32_t cnt[kRadix];
+    constexpr int R = 1 << RB;
+    __shared__ uint32_t cnt[R];
     const size_t t = blockIdx.x, w = blockIdx.y;
-    cnt[threadIdx.x] = 0;
+    for (int d = threadIdx.x; d < R; d += kSortThreads) cnt[d] = 0;
     __syncthreads();
     const uint32_t* seg = keys + w * n;
     const size_t start = t * kSortTile;
 #pragma unroll
     for (int e = 0; e < kSortItems; ++e) {
         size_t idx = start + (size_t)e * kSortThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&cnt[(seg[idx] >> shift) & (kRadix - 1)], 1u);
+        if (idx < n) atomicAdd(&cnt[(seg[idx] >> shift) & (R - 1)], 1u);
     }
     __syncthreads();
-    hist[(w * kRadix + threadIdx.x) * tiles + t] = cnt[threadIdx.x];
+    for (int d = threadIdx.x; d < R; d += kSortThreads) hist[(w * R + d) * tiles + t] = cnt[d];
 }
 
 // Exclusive block-wide scan of one value per thread (256 threads).
@@ -639,9 +641,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
 }
 
 // For each (window, digit): exclusive scan over tiles in place; the digit total goes to dtot.
+template <int RB>
 __global__ void k_sort_scan_tiles(uint32_t* __restrict__ hist, size_t tiles, uint32_t* __restrict__ dtot) {
+    constexpr int R = 1 << RB;
     const size_t d = blockIdx.x, w = blockIdx.y;
-    uint32_t* row = hist + (w * kRadix + d) * tiles;
+    uint32_t* row = hist + (w * R + d) * tiles;
     const size_t per = (tiles + kSortThreads - 1) / kSortThreads;
     const size_t lo = threadIdx.x * per;
     uint32_t local = 0;
@@ -656,25 +660,39 @@ __global__ void k_sort_scan_tiles(uint32_t* __restrict__ hist, size_t tiles, uin
             run += c;
         }
     }
-    if (threadIdx.x == 0) dtot[w * kRadix + d] = total;
+    if (threadIdx.x == 0) dtot[w * R + d] = total;
 }
 
+// Exclusive scan of the R digit totals of a window (R / 256 consecutive digits per thread).
+template <int RB>
 __global__ void k_sort_scan_digits(uint32_t* __restrict__ dtot) {
-    uint32_t* row = dtot + blockIdx.x * kRadix;
-    uint32_t v = row[threadIdx.x];
-    uint32_t ex = block_exclusive_scan(v, nullptr);
-    row[threadIdx.x] = ex;
+    constexpr int R = 1 << RB, PER = R / kSortThreads;
+    uint32_t* row = dtot + blockIdx.x * R + threadIdx.x * PER;
+    uint32_t v[PER], local = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        v[k] = row[k];
+        local += v[k];
+    }
+    uint32_t run = block_exclusive_scan(local, nullptr);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        row[k] = run;
+        run += v[k];
+    }
 }
 
+template <int RB>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, size_t n, int shift, size_t tiles, const uint32_t* __restrict__ hist,
     const uint32_t* __restrict__ doff) {
-    __shared__ uint32_t wcnt[kSortThreads / 32][kRadix];
-    __shared__ uint32_t base[kRadix];
+    constexpr int R = 1 << RB;
+    __shared__ uint32_t wcnt[kSortThreads / 32][R];
+    __shared__ uint32_t base[R];
     const size_t t = blockIdx.x, w = blockIdx.y;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < (kSortThreads / 32) * kRadix; k += kSortThreads)
+    for (int k = threadIdx.x; k < (kSortThreads / 32) * R; k += kSortThreads)
         (&wcnt[0][0])[k] = 0;
     __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -688,7 +706,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
         key[r] = valid ? kin[seg + idx] : 0u;
         val[r] = valid ? vin[seg + idx] : 0u;
         // Items past the end sort last in the tile and are never written.
-        dig[r] = valid ? ((key[r] >> shift) & (kRadix - 1)) : (kRadix - 1);
+        dig[r] = valid ? ((key[r] >> shift) & (R - 1)) : (R - 1);
         uint32_t peers = __match_any_sync(0xffffffffu, dig[r]);
         uint32_t before = wcnt[wid][dig[r]];
         __syncwarp();
@@ -697,8 +715,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
         rank[r] = before + __popc(peers & lt_mask);
     }
     __syncthreads();
-    {
-        const int d = threadIdx.x;
+    for (int d = threadIdx.x; d < R; d += kSortThreads) {
         uint32_t run = 0;
 #pragma unroll
         for (int k = 0; k < kSortThreads / 32; ++k) {
@@ -706,7 +723,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
             wcnt[k][d] = run;
             run += c;
         }
-        base[d] = doff[w * kRadix + d] + hist[(w * kRadix + d) * tiles + t];
+        base[d] = doff[w * R + d] + hist[(w * R + d) * tiles + t];
     }
     __syncthreads();
 #pragma unroll
@@ -839,7 +856,7 @@ __global__ void __launch_bounds__(128) k_accumulate_batched(const __grid_constan
 //    head[u] += head[u + d] when u + d continues the same run; ceil(log2 cpw) rounds
 //    leave each run's sum of heads at its first head;
 //  * k_merge_final: bucket = tail[start] + that sum.
-__global__ void k_merge_start(AccArgs a, int32_t* __restrict__ start) {
+__global__ void k_merge_start(AccArgs a, int32_t* __restrict__ start, int* __restrict__ maxspan) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)a.nwin * a.cpw) return;
     const int w = a.w0 + (int)(id / a.cpw);
@@ -857,11 +874,15 @@ __global__ void k_merge_start(AccArgs a, int32_t* __restrict__ start) {
         const size_t mid = (lo + hi) >> 1;
         if (keys[mid] < key) lo = mid + 1; else hi = mid;
     }
-    start[ci] = (int32_t)(lo / (size_t)a.K);
+    const int32_t t0 = (int32_t)(lo / (size_t)a.K);
+    start[ci] = t0;
+    atomicMax(maxspan, (int)(u - (uint32_t)t0));  // heads of this run up to u
 }
 
 template <class M>
-__global__ void k_merge_round(AccArgs a, const int32_t* __restrict__ start, uint32_t d) {
+__global__ void k_merge_round(AccArgs a, const int32_t* __restrict__ start, uint32_t d,
+                              const int* __restrict__ maxspan) {
+    if (d >= (uint32_t)*maxspan) return;  // no run has heads this far apart: nothing to pair
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (uint32_t)a.nwin * a.cpw) return;
     const int w = a.w0 + (int)(id / a.cpw);
@@ -899,7 +920,7 @@ __global__ void k_merge_final(AccArgs a) {
 
 // Thread (wi, g): Y = sum_{i=1..L} B[gL+i], V = sum_{i=1..L} i * B[gL+i] (bucket b at index b-1).
 template <class M>
-__global__ void k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, int w0, int nwin,
+__global__ void __launch_bounds__(128, 4) k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, int w0, int nwin,
                                   uint32_t G, uint4* __restrict__ Y, uint4* __restrict__ V) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)nwin * G) return;
@@ -1065,7 +1086,7 @@ struct Plan {
     int user_bits;   // scalar range checked against opts.scalar_bits
     int c, sgn, bits, W;
     uint32_t B, Bp;
-    int passes;
+    int passes, rb;  // radix-sort passes of rb-bit digits
     size_t tiles;
     int K;
     uint32_t cpw;   // chunks per window
@@ -1134,7 +1155,11 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     const size_t items = p->items;
     p->B = p->sgn ? (1u << (p->c - 1)) : ((1u << p->c) - 1u);
     p->Bp = p->sgn ? p->B : (1u << p->c);
-    p->passes = (p->c + 7) / 8;
+    // keys are |digit| <= 2^(c-1) (signed) or < 2^c: c bits, sorted 8 bits per pass
+    // (10-bit digits would save a pass at c = 17..20 but measured slower on GB300:
+    // the 1024-bin scatter's shared-memory counters cost more than the pass)
+    p->rb = 8;
+    p->passes = (p->c + p->rb - 1) / p->rb;
     p->tiles = (items + kSortTile - 1) / kSortTile;
     // Chunks of K <= 64 items, one per thread, sized so that the chunks over all
     // windows fill whole waves of resident accumulation threads (152 SMs x 3 blocks
@@ -1176,8 +1201,8 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->off_vals0 = take((size_t)p->W * items * 4);
     p->off_keys1 = take((size_t)p->W * items * 4);
     p->off_vals1 = take((size_t)p->W * items * 4);
-    p->off_hist = take((size_t)p->W * kRadix * (p->tiles ? p->tiles : 1) * 4);
-    p->off_dtot = take((size_t)p->W * kRadix * 4);
+    p->off_hist = take((size_t)p->W * (1u << p->rb) * (p->tiles ? p->tiles : 1) * 4);
+    p->off_dtot = take((size_t)p->W * (1u << p->rb) * 4);
     p->off_buckets = take((size_t)p->W * p->Bp * XY);
     p->off_head = take(chunks * XY);
     p->off_tail = take(chunks * XY);
@@ -1308,7 +1333,7 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
                  const msm_opts* opts, cudaStream_t s, AccArgs* a_out) {
     const size_t n = p.n;
     int* status = at<int>(workspace, p.off_status);
-    MSM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+    MSM_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));  // status word, longest run of heads
     const uint4* pts = reinterpret_cast<const uint4*>(points);
     if (!(opts->flags & MSM377_POINTS_PREPARED)) {
         uint4* prep = at<uint4>(workspace, p.off_points);
@@ -1325,13 +1350,13 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
     int cur = 0;
     for (int pass = 0; pass < p.passes; ++pass) {
-        int shift = 8 * pass;
-        dim3 g((unsigned)p.tiles, (unsigned)p.W);
-        k_sort_hist<<<g, kSortThreads, 0, s>>>(keys[cur], np, shift, p.tiles, hist);
-        k_sort_scan_tiles<<<dim3(kRadix, p.W), kSortThreads, 0, s>>>(hist, p.tiles, dtot);
-        k_sort_scan_digits<<<p.W, kSortThreads, 0, s>>>(dtot);
-        k_sort_scatter<<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np,
-                                                  shift, p.tiles, hist, dtot);
+        const int shift = p.rb * pass;
+        const dim3 g((unsigned)p.tiles, (unsigned)p.W);
+        k_sort_hist<8><<<g, kSortThreads, 0, s>>>(keys[cur], np, shift, p.tiles, hist);
+        k_sort_scan_tiles<8><<<dim3(1u << 8, p.W), kSortThreads, 0, s>>>(hist, p.tiles, dtot);
+        k_sort_scan_digits<8><<<p.W, kSortThreads, 0, s>>>(dtot);
+        k_sort_scatter<8><<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np, shift,
+                                                     p.tiles, hist, dtot);
         note_launches(4);
         cur ^= 1;
     }
@@ -1368,10 +1393,11 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     const size_t nchunks = (size_t)p.W * p.cpw;
     // 5. merge partial sums of runs crossing chunk edges (log depth)
     int32_t* start = at<int32_t>(workspace, p.off_start);
-    k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start);
+    int* maxspan = at<int>(workspace, p.off_status) + 1;
+    k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, maxspan);
     note_launches(1);
     for (uint32_t d = 1; d < p.cpw; d <<= 1) {
-        k_merge_round<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d);
+        k_merge_round<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d, maxspan);
         note_launches(1);
     }
     k_merge_final<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a);
@@ -1386,7 +1412,7 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     uint4* zin = P0;
     uint4* zout = P1;
     while (m > 1) {
-        const uint32_t F = m >= 8 ? 8 : m;
+        const uint32_t F = 2;  // pairwise rounds: depth log2 Q additions
         k_sum_segments<M><<<grid_for(nseg * (m / F), 128), 128, 0, s>>>(zin, nseg, m, F, zout);
         note_launches(1);
         m /= F;
