@@ -7,8 +7,10 @@
 //                 random gather of one point reads three full 32 B sectors)
 //  2. digits      c-bit window digits per scalar (signed or unsigned);
 //                 key = |digit|, value = point index | sign << 31, window-major
-//  3. sort        stable LSD radix sort of (key, value) within each window,
-//                 8-bit digits per pass (histogram, scans, ranked scatter)
+//  3. sort        bucket order within each window: a counting sort over (window,
+//                 key) bins (count, scan, scatter with warp-aggregated atomics) for
+//                 few windows or wide keys, else a stable LSD radix sort with 8-bit
+//                 digits per pass (histogram, scans, ranked scatter)
 //  4. accumulate  per window, the sorted stream is cut into equal chunks of K
 //                 items, one per thread, so heavy buckets spread over threads;
 //                 runs inside a chunk are summed with mixed PADDs and written
@@ -739,6 +741,129 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     }
 }
 
+// ---------------------------------------------------------------- stage 3 (counting sort)
+//
+// Bucket order by counting: every (window, key) is a bin; one pass counts the
+// items of each bin with warp-aggregated atomics, a scan turns the counts into
+// bin offsets (window w's bins start at w np, since each window holds np items),
+// and one pass scatters every item to its bin's next free slot. The order inside
+// a bin is not kept -- it does not matter, since a bucket's sum is the same group
+// element in any order. Two passes over the (key, value) pairs instead of a
+// histogram and a scatter pass per 8 key bits.
+constexpr int kScanBlock = 1024, kScanPer = 4, kScanTile = kScanBlock * kScanPer;
+
+// Grid (items of a window / 256, windows): item i = w np + j of window w = blockIdx.y.
+__global__ void k_bin_count(const uint32_t* __restrict__ keys, size_t np, uint32_t nb,
+                            uint32_t* __restrict__ counts) {
+    const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const bool valid = j < np;
+    const uint32_t bin = valid ? blockIdx.y * nb + keys[(size_t)blockIdx.y * np + j] : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+    const int lane = threadIdx.x & 31;
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&counts[bin], (uint32_t)__popc(peers));
+}
+
+// In place exclusive scan of each tile of kScanTile counts; tile totals to bsum.
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(uint32_t* __restrict__ x, size_t m,
+                                                           uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t warp_tot[kScanBlock / 32];
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer], local = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < m ? x[base + k] : 0u;
+        local += v[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t run = inc - local + (wid ? warp_tot[wid - 1] : 0u);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < m) x[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = warp_tot[kScanBlock / 32 - 1];
+}
+
+// Exclusive scan of the tile totals in one block (any count: a serial run per thread).
+__global__ void __launch_bounds__(kScanBlock) k_scan_totals(uint32_t* __restrict__ bsum, size_t nb) {
+    __shared__ uint32_t warp_tot[kScanBlock / 32];
+    const size_t per = (nb + kScanBlock - 1) / kScanBlock;
+    const size_t lo = threadIdx.x * per;
+    uint32_t local = 0;
+    for (size_t k = lo; k < lo + per && k < nb; ++k) local += bsum[k];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    uint32_t run = inc - local + (wid ? warp_tot[wid - 1] : 0u);
+    for (size_t k = lo; k < lo + per && k < nb; ++k) {
+        const uint32_t c = bsum[k];
+        bsum[k] = run;
+        run += c;
+    }
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ x, size_t m, const uint32_t* __restrict__ bsum) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < m) x[i] += bsum[i / kScanTile];
+}
+
+// Each item to the next free slot of its bin (cursor = the bins' offsets, advanced
+// with one warp-aggregated atomic per bin and warp).
+__global__ void k_bin_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t total, size_t np,
+                              uint32_t nb, uint32_t* __restrict__ cursor) {
+    const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const bool valid = j < np;
+    const size_t i = (size_t)blockIdx.y * np + j;
+    const uint32_t bin = valid ? blockIdx.y * nb + kin[i] : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&cursor[bin], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (!valid) return;
+    const size_t pos = (size_t)base + __popc(peers & ((1u << lane) - 1u));
+    if (pos < total) {  // always true when the counts agree; keeps writes in bounds
+        kout[pos] = kin[i];
+        vout[pos] = vin[i];
+    }
+}
+
 // ---------------------------------------------------------------- stages 4-5
 
 struct AccArgs {
@@ -1095,6 +1220,8 @@ struct Plan {
     uint32_t L, G, Q;
     int logG, log2L;
     size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_hist, off_dtot;
+    int counting;                      // counting sort (else LSD radix sort)
+    size_t nbins, off_bins, off_bsum;  // counting sort: bins (window, key) and scan tile totals
     size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
     size_t off_S, off_acc, off_start, total;
 };
@@ -1160,6 +1287,10 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     // the 1024-bin scatter's shared-memory counters cost more than the pass)
     p->rb = 8;
     p->passes = (p->c + p->rb - 1) / p->rb;
+    // Measured on GB300: counting by (window, key) bins beats the radix passes when
+    // the radix sort needs three passes or there are few windows (large bins);
+    // with many small windows the two radix passes are as fast.
+    p->counting = (p->passes >= 3 || p->W <= 8) ? 1 : 0;
     p->tiles = (items + kSortTile - 1) / kSortTile;
     // Chunks of K <= 64 items, one per thread, sized so that the chunks over all
     // windows fill whole waves of resident accumulation threads (152 SMs x 3 blocks
@@ -1203,6 +1334,9 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->off_vals1 = take((size_t)p->W * items * 4);
     p->off_hist = take((size_t)p->W * (1u << p->rb) * (p->tiles ? p->tiles : 1) * 4);
     p->off_dtot = take((size_t)p->W * (1u << p->rb) * 4);
+    p->nbins = (size_t)p->W * (p->Bp + 1);  // keys 0 .. Bp of every window
+    p->off_bins = take(p->nbins * 4);
+    p->off_bsum = take(((p->nbins + kScanTile - 1) / kScanTile) * 4);
     p->off_buckets = take((size_t)p->W * p->Bp * XY);
     p->off_head = take(chunks * XY);
     p->off_tail = take(chunks * XY);
@@ -1346,19 +1480,37 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.Wd,
                                               p.sgn, p.user_bits, p.glv, p.pre, keys[0], vals[0], status);
     note_launches(1);
-    uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
-    uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
     int cur = 0;
-    for (int pass = 0; pass < p.passes; ++pass) {
-        const int shift = p.rb * pass;
-        const dim3 g((unsigned)p.tiles, (unsigned)p.W);
-        k_sort_hist<8><<<g, kSortThreads, 0, s>>>(keys[cur], np, shift, p.tiles, hist);
-        k_sort_scan_tiles<8><<<dim3(1u << 8, p.W), kSortThreads, 0, s>>>(hist, p.tiles, dtot);
-        k_sort_scan_digits<8><<<p.W, kSortThreads, 0, s>>>(dtot);
-        k_sort_scatter<8><<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np, shift,
-                                                     p.tiles, hist, dtot);
-        note_launches(4);
-        cur ^= 1;
+    if (p.counting) {
+        // counting sort: count, scan, scatter (window-major bins, window w at w np)
+        const size_t total = (size_t)p.W * np;
+        const uint32_t nb = p.Bp + 1;
+        uint32_t* bins = at<uint32_t>(workspace, p.off_bins);
+        uint32_t* bsum = at<uint32_t>(workspace, p.off_bsum);
+        const size_t ntiles = (p.nbins + kScanTile - 1) / kScanTile;
+        MSM_CUDA_TRY(cudaMemsetAsync(bins, 0, p.nbins * 4, s));
+        const dim3 gw(grid_for(np, 256), (unsigned)p.W);
+        k_bin_count<<<gw, 256, 0, s>>>(keys[0], np, nb, bins);
+        k_scan_tiles<<<(unsigned)ntiles, kScanBlock, 0, s>>>(bins, p.nbins, bsum);
+        k_scan_totals<<<1, kScanBlock, 0, s>>>(bsum, ntiles);
+        k_scan_add<<<grid_for(p.nbins, 256), 256, 0, s>>>(bins, p.nbins, bsum);
+        k_bin_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], keys[1], vals[1], total, np, nb, bins);
+        note_launches(5);
+        cur = 1;
+    } else {
+        uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
+        uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
+        for (int pass = 0; pass < p.passes; ++pass) {
+            const int shift = p.rb * pass;
+            const dim3 g((unsigned)p.tiles, (unsigned)p.W);
+            k_sort_hist<8><<<g, kSortThreads, 0, s>>>(keys[cur], np, shift, p.tiles, hist);
+            k_sort_scan_tiles<8><<<dim3(1u << 8, p.W), kSortThreads, 0, s>>>(hist, p.tiles, dtot);
+            k_sort_scan_digits<8><<<p.W, kSortThreads, 0, s>>>(dtot);
+            k_sort_scatter<8><<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np,
+                                                         shift, p.tiles, hist, dtot);
+            note_launches(4);
+            cur ^= 1;
+        }
     }
     uint4* buckets = at<uint4>(workspace, p.off_buckets);
     MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * kXyzzBytes, s));
