@@ -1226,6 +1226,8 @@ struct Plan {
     size_t off_S, off_acc, off_start, total;
 };
 
+constexpr uint64_t kReduceThreads = 32768;
+
 int ilog2(uint64_t v) {
     int r = 0;
     while ((1ull << (r + 1)) <= v) ++r;
@@ -1307,10 +1309,12 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     if (p->cpw == 0) p->cpw = 1;
     p->gw = p->W;
     p->ngroups = 1;
-    // bucket reduction geometry: enough level-1 threads over all windows
+    // bucket reduction geometry: segments of L buckets, the longest L that still
+    // leaves kReduceThreads level-1 threads over all windows (longer segments mean
+    // fewer segment sums for the bit-sum stage, but fewer threads for the running sums)
     uint64_t group_buckets = (uint64_t)p->W * p->Bp;
     uint32_t L = 2;
-    while (L < p->Bp && group_buckets / (2 * L) >= 65536) L <<= 1;
+    while (L < p->Bp && group_buckets / (2 * L) >= kReduceThreads) L <<= 1;
     if (L > p->Bp) L = p->Bp;
     p->L = L;
     p->G = p->Bp / L;
