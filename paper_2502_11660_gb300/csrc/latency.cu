@@ -28,6 +28,12 @@ __device__ __forceinline__ void load_fe16(fe& a, const uint4* p) {
     a.v[8] = u2.x; a.v[9] = u2.y; a.v[10] = u2.z; a.v[11] = u2.w;
 }
 
+__device__ __forceinline__ void load_stored(ed::stored& Q, const uint4* pts, size_t i) {
+    load_fe16(Q.x, pts + 9 * i);
+    load_fe16(Q.y, pts + 9 * i + 3);
+    load_fe16(Q.u, pts + 9 * i + 6);
+}
+
 __device__ __forceinline__ void store_affine_std(uint32_t* out, affine A) {
     if (!ec::is_inf(A)) {
         fq::from_mont(A.x, A.x);
@@ -43,10 +49,17 @@ __global__ void k_chain_xyzz1(const uint4* __restrict__ pts, size_t n, uint32_t*
     ec::xyzz acc;
     ec::set_inf(acc);
     bool inf = true;
+    affine next;
+    if (n) {
+        load_fe16(next.x, pts);
+        load_fe16(next.y, pts + 3);
+    }
     for (size_t i = 0; i < n; ++i) {
-        affine Q;
-        load_fe16(Q.x, pts + 6 * i);
-        load_fe16(Q.y, pts + 6 * i + 3);
+        const affine Q = next;          // the next point's loads overlap this addition
+        if (i + 1 < n) {
+            load_fe16(next.x, pts + 6 * (i + 1));
+            load_fe16(next.y, pts + 6 * (i + 1) + 3);
+        }
         ec::madd(acc, inf, Q);
     }
     affine A;
@@ -59,11 +72,11 @@ __global__ void k_chain_ed1(const uint4* __restrict__ pts, size_t n, uint32_t* _
     if (threadIdx.x != 0) return;
     ed::ext acc;
     ed::set_inf(acc);
+    ed::stored next;
+    if (n) load_stored(next, pts, 0);
     for (size_t i = 0; i < n; ++i) {
-        ed::stored Q;
-        load_fe16(Q.x, pts + 9 * i);
-        load_fe16(Q.y, pts + 9 * i + 3);
-        load_fe16(Q.u, pts + 9 * i + 6);
+        const ed::stored Q = next;      // the next point's loads overlap this addition
+        if (i + 1 < n) load_stored(next, pts, i + 1);
         ed::madd(acc, Q);
     }
     affine A;
@@ -78,11 +91,11 @@ __global__ void __launch_bounds__(32) k_chain_ed4(const uint4* __restrict__ pts,
     const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
     ed::ext acc;
     ed::set_inf(acc);
+    ed::stored next;
+    if (n) load_stored(next, pts, 0);
     for (size_t i = 0; i < n; ++i) {
-        ed::stored Q;
-        load_fe16(Q.x, pts + 9 * i);
-        load_fe16(Q.y, pts + 9 * i + 3);
-        load_fe16(Q.u, pts + 9 * i + 6);
+        const ed::stored Q = next;      // the next point's loads overlap this addition
+        if (i + 1 < n) load_stored(next, pts, i + 1);
         ed::madd4(acc, Q, sh[g], l, true);
     }
     if (lane != 0) return;
