@@ -253,9 +253,17 @@ int msm_g1_status(const void *workspace, const msm_opts *opts);
 
 /* End-to-end variant on host buffers (synchronous): copies points_host (24 u32
  * per point, standard form) and scalars_host (8 u32 per scalar) into the
- * workspace, runs msm_g1 and copies the 24-u32 result into out_host. Host
- * buffers may be pageable; pinned buffers copy faster. workspace must hold
- * msm_g1_host_workspace_bytes(n, opts) bytes. Returns the device status. */
+ * workspace, runs the MSM and copies the 24-u32 result into out_host. The points
+ * travel in 2 chunks on a library helper stream and each chunk is prepared (the
+ * options' curve model / GLV form) on a second helper stream as soon as it has
+ * arrived, while the scalars' copy, digits and bucket sort run on opts->stream;
+ * the accumulation starts when the last chunk is prepared. Host buffers may be
+ * pageable; pinned buffers copy faster and overlap. workspace (device, 256-byte
+ * aligned) must hold msm_g1_host_workspace_bytes(n, opts) bytes;
+ * MSM377_POINTS_PREPARED, MSM377_PRECOMPUTED and MSM377_PROFILE are not used here.
+ * The helper streams are shared per device: calls from several host threads on
+ * one device must not overlap (the same holds for msm_g1_batched).
+ * Returns the device status. */
 size_t msm_g1_host_workspace_bytes(size_t n, const msm_opts *opts);
 int msm_g1_host(const uint32_t *points_host, const uint32_t *scalars_host, size_t n,
                 uint32_t *out_host, void *workspace, size_t workspace_bytes,

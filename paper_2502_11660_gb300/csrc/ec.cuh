@@ -219,110 +219,192 @@ __device__ __forceinline__ void add_q(xyzz& P, const QL& q) {
 
 __device__ __forceinline__ void add(xyzz& P, const xyzz& Q) { add_q(P, RegQ{&Q}); }
 
-// Inverse by the binary extended Euclidean algorithm on exact 32-bit words
-// (variable time; MSM results are public). For u = aR it returns x with
-// x u = 1 mod p, i.e. a^-1 R^-1, and one Montgomery multiplication by R^3 mod p
-// turns that into a^-1 R. About 2 * 377 shift / subtract steps of 12-word
-// carry chains, an order of magnitude shorter than a^(p-2).
+// Inverse by the optimized binary GCD of T. Pornin ("Optimized Binary GCD for
+// Modular Inversion", 2020): the binary extended GCD on (a, b) = (y, p), but 31
+// steps at a time on 64-bit approximations of a and b (their top 33 and low 31
+// bits), which fix an update matrix (f0 g0; f1 g1) with entries of at most 2^31
+// in magnitude; the matrix is then applied once to the full a, b and to the
+// Bezout coefficients u, v (a = u y, b = v y mod p), dividing by 2^31 (exact for
+// a, b; mod p for u, v, where x / 2^31 = (x + m p) / 2^31 with m = -x mod 2^31
+// because p = 1 mod 2^31). ceil((2 * 377 - 1) / 31) = 25 rounds bring a to 0 and
+// b to 1 = gcd, and then v = y^-1. For u = aR (Montgomery form) that is
+// a^-1 R^-1, and one Montgomery multiplication by R^3 mod p turns it into a^-1 R.
+// Variable time (MSM results are public); every loop has a fixed trip count.
 namespace detail {
 constexpr int W = 12;
-__device__ __forceinline__ bool w_is_one(const uint32_t (&a)[W]) {
-    uint32_t o = a[0] ^ 1u;
-#pragma unroll
-    for (int k = 1; k < W; ++k) o |= a[k];
-    return o == 0;
-}
-__device__ __forceinline__ bool w_geq(const uint32_t (&a)[W], const uint32_t (&b)[W]) {
-#pragma unroll
-    for (int k = W - 1; k >= 0; --k)
-        if (a[k] != b[k]) return a[k] > b[k];
-    return true;
-}
-__device__ __forceinline__ void w_sub(uint32_t (&a)[W], const uint32_t (&b)[W]) {
-    uint64_t borrow = 0;
+
+// r (13 words, two's complement) = f x + g y for |f|, |g| <= 2^31 and x, y < 2^384.
+__device__ __forceinline__ void lin_comb(uint32_t (&r)[W + 1], const uint32_t (&x)[W], const uint32_t (&y)[W],
+                                         int64_t f, int64_t g) {
+    const uint32_t fa = (uint32_t)(f < 0 ? -f : f), ga = (uint32_t)(g < 0 ? -g : g);
+    uint32_t px[W + 1], py[W + 1];
+    uint64_t cx = 0, cy = 0;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        uint64_t t = (uint64_t)a[k] - b[k] - borrow;
-        a[k] = (uint32_t)t;
-        borrow = (t >> 63) & 1u;
+        uint64_t t = (uint64_t)fa * x[k] + cx;
+        px[k] = (uint32_t)t;
+        cx = t >> 32;
+        uint64_t u = (uint64_t)ga * y[k] + cy;
+        py[k] = (uint32_t)u;
+        cy = u >> 32;
     }
-}
-__device__ __forceinline__ uint32_t w_add(uint32_t (&a)[W], const uint32_t (&b)[W]) {
-    uint64_t carry = 0;
+    px[W] = (uint32_t)cx;
+    py[W] = (uint32_t)cy;
+    // r = (+-px) + (+-py) in 13-word two's complement (|r| < 2^416 fits)
+    const uint32_t nx = f < 0 ? 0xffffffffu : 0u, ny = g < 0 ? 0xffffffffu : 0u;
+    uint64_t carry = (nx ? 1u : 0u) + (ny ? 1u : 0u);  // two's complement: ~v + 1
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        uint64_t t = (uint64_t)a[k] + b[k] + carry;
-        a[k] = (uint32_t)t;
+    for (int k = 0; k <= W; ++k) {
+        uint64_t t = (uint64_t)(px[k] ^ nx) + (py[k] ^ ny) + carry;
+        r[k] = (uint32_t)t;
         carry = t >> 32;
     }
-    return (uint32_t)carry;
 }
-__device__ __forceinline__ void w_shr1(uint32_t (&a)[W], uint32_t top) {
+
+// x = r >> 31 (r's low 31 bits are zero), made non-negative; returns true if r < 0.
+__device__ __forceinline__ bool shift31_abs(uint32_t (&x)[W], uint32_t (&r)[W + 1]) {
+    const bool neg = (r[W] >> 31) != 0;
+    if (neg) {
+        uint64_t carry = 1;
 #pragma unroll
-    for (int k = 0; k < W - 1; ++k) a[k] = (a[k] >> 1) | (a[k + 1] << 31);
-    a[W - 1] = (a[W - 1] >> 1) | (top << 31);
+        for (int k = 0; k <= W; ++k) {
+            uint64_t t = (uint64_t)(~r[k]) + carry;
+            r[k] = (uint32_t)t;
+            carry = t >> 32;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) x[k] = (r[k] >> 31) | (r[k + 1] << 1);
+    return neg;
 }
-// x / 2 mod p for x in [0, p)
-__device__ __forceinline__ void w_half(uint32_t (&x)[W], const uint32_t (&p)[W]) {
-    uint32_t top = 0;
-    if (x[0] & 1u) top = w_add(x, p);
-    w_shr1(x, top);
-}
-// x = x - y mod p for x, y in [0, p)
-__device__ __forceinline__ void w_submod(uint32_t (&x)[W], const uint32_t (&y)[W], const uint32_t (&p)[W]) {
-    if (w_geq(x, y)) {
-        w_sub(x, y);
-    } else {
-        w_add(x, p);
-        w_sub(x, y);
+
+// u = (f u0 + g v0) / 2^31 mod p in [0, p), for u0, v0 in [0, p) and |f|, |g| <= 2^31.
+__device__ __forceinline__ void lin_comb_mod(uint32_t (&u)[W], const uint32_t (&u0)[W], const uint32_t (&v0)[W],
+                                             int64_t f, int64_t g) {
+    uint32_t r[W + 1];
+    lin_comb(r, u0, v0, f, g);          // |r| < 2^32 p
+    // + 2^32 p: r > 0, below 2^33 p < 2^411 (words 1..12 of 2^32 p are p's words)
+    uint64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k <= W; ++k) {
+        uint64_t t = (uint64_t)r[k] + (k >= 1 ? fq::kP[k - 1] : 0u) + carry;
+        r[k] = (uint32_t)t;
+        carry = t >> 32;
+    }
+    // + m p with m = -r mod 2^31 makes the low 31 bits zero (p = 1 mod 2^31)
+    const uint32_t m = (0u - r[0]) & 0x7fffffffu;
+    uint32_t s[W + 2];
+    carry = 0;
+#pragma unroll
+    for (int k = 0; k <= W; ++k) {
+        uint64_t t = (uint64_t)r[k] + (k < W ? (uint64_t)m * fq::kP[k] : 0u) + carry;
+        s[k] = (uint32_t)t;
+        carry = t >> 32;
+    }
+    s[W + 1] = (uint32_t)carry;
+    // / 2^31: below (2^33 p + 2^31 p) / 2^31 = 5 p
+#pragma unroll
+    for (int k = 0; k < W; ++k) u[k] = (s[k] >> 31) | (s[k + 1] << 1);
+    // subtract 4p, 2p, p where possible
+#pragma unroll
+    for (int mult = 4; mult >= 1; mult >>= 1) {
+        uint32_t d[W];
+        uint64_t borrow = 0, cm = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            uint64_t pk = (uint64_t)fq::kP[k] * mult + cm;
+            cm = pk >> 32;
+            uint64_t t = (uint64_t)u[k] - (uint32_t)pk - borrow;
+            d[k] = (uint32_t)t;
+            borrow = (t >> 63) & 1u;
+        }
+        if (!borrow && cm == 0) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) u[k] = d[k];
+        }
     }
 }
 }  // namespace detail
 
 __device__ __noinline__ static void inv(fe& r, const fe& a_in) {
     using namespace detail;
-    const uint32_t p[W] = {0x00000001u, 0x8508c000u, 0x30000000u, 0x170b5d44u, 0xba094800u, 0x1ef3622fu,
-                           0x00f5138fu, 0x1a22d9f3u, 0x6ca1493bu, 0xc63b05c0u, 0x17c510eau, 0x01ae3a46u};
     fe a;
     fq::canon(a, a_in);
-    uint32_t u[W], v[W], x1[W], x2[W];
+    uint32_t A[W], B[W], U[W], V[W];
     uint32_t z = 0;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        u[k] = a.v[k];
-        v[k] = p[k];
-        x1[k] = 0;
-        x2[k] = 0;
+        A[k] = a.v[k];
+        B[k] = fq::kP[k];
+        U[k] = 0;
+        V[k] = 0;
         z |= a.v[k];
     }
-    x1[0] = 1;
+    U[0] = 1;
     if (z == 0) {
         fq::set_zero(r);
         return;
     }
-    // each pass removes at least one bit from u or v; the bounds only guard the loops
-    for (int guard = 0; guard < 2 * 384 + 8 && !w_is_one(u) && !w_is_one(v); ++guard) {
-        for (int s = 0; s < 384 && !(u[0] & 1u); ++s) {
-            w_shr1(u, 0);
-            w_half(x1, p);
-        }
-        for (int s = 0; s < 384 && !(v[0] & 1u); ++s) {
-            w_shr1(v, 0);
-            w_half(x2, p);
-        }
-        if (w_geq(u, v)) {
-            w_sub(u, v);
-            w_submod(x1, x2, p);
+    for (int round = 0; round < 25; ++round) {
+        // bit length n = max(len A, len B, 64) and the 64-bit approximations
+        int top = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            if (A[k] | B[k]) top = k;
+        const uint32_t hiw = A[top] | B[top];
+        const int n = 32 * top + (32 - __clz(hiw));
+        uint64_t ah, bh;
+        if (n <= 64) {
+            ah = ((uint64_t)A[1] << 32) | A[0];
+            bh = ((uint64_t)B[1] << 32) | B[0];
         } else {
-            w_sub(v, u);
-            w_submod(x2, x1, p);
+            const int sbit = n - 33, idx = sbit >> 5, sh = sbit & 31;
+            uint32_t alo = 0, ahi = 0, blo = 0, bhi = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (k == idx) { alo = A[k]; blo = B[k]; }
+                if (k == idx + 1) { ahi = A[k]; bhi = B[k]; }
+            }
+            const uint64_t at = ((((uint64_t)ahi << 32) | alo) >> sh) & 0x1ffffffffull;
+            const uint64_t bt = ((((uint64_t)bhi << 32) | blo) >> sh) & 0x1ffffffffull;
+            ah = (at << 31) | (A[0] & 0x7fffffffu);
+            bh = (bt << 31) | (B[0] & 0x7fffffffu);
+        }
+        int64_t f0 = 1, g0 = 0, f1 = 0, g1 = 1;
+#pragma unroll 1
+        for (int i = 0; i < 31; ++i) {
+            if (ah & 1) {
+                if (ah < bh) {
+                    uint64_t t = ah; ah = bh; bh = t;
+                    int64_t tf = f0; f0 = f1; f1 = tf;
+                    int64_t tg = g0; g0 = g1; g1 = tg;
+                }
+                ah -= bh;
+                f0 -= f1;
+                g0 -= g1;
+            }
+            ah >>= 1;
+            f1 <<= 1;
+            g1 <<= 1;
+        }
+        uint32_t ra[W + 1], rb[W + 1];
+        lin_comb(ra, A, B, f0, g0);
+        lin_comb(rb, A, B, f1, g1);
+        if (shift31_abs(A, ra)) { f0 = -f0; g0 = -g0; }
+        if (shift31_abs(B, rb)) { f1 = -f1; g1 = -g1; }
+        uint32_t U2[W], V2[W];
+        lin_comb_mod(U2, U, V, f0, g0);
+        lin_comb_mod(V2, U, V, f1, g1);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            U[k] = U2[k];
+            V[k] = V2[k];
         }
     }
     fe x, r3;
-    const bool one_u = w_is_one(u);
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        x.v[k] = one_u ? x1[k] : x2[k];
+        x.v[k] = V[k];
         r3.v[k] = fq::kR3[k];
     }
     fq::mul(r, x, r3);  // a^-1 R^-1 * R^3 * R^-1 = a^-1 R

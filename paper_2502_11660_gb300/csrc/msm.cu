@@ -206,9 +206,11 @@ __device__ __forceinline__ void glv_source(fe& x, fe& y, const uint4* __restrict
     }
 }
 
-__global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n, size_t np) {
-    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (i >= np) return;
+// Stored rows [lo, hi) of np (the whole set: lo = 0, hi = np).
+__global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n, size_t np, size_t lo,
+                          size_t hi) {
+    size_t i = lo + blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= hi) return;
     fe x, y;
     glv_source(x, y, in, i, n, np);
     store_fe(out + 6 * i, x);
@@ -351,13 +353,14 @@ __device__ __forceinline__ void store_ed_stored(uint4* o, fe x, fe y) {
     store_fe(o + 6, u);
 }
 
-// One warp covers 32 * kEdChunk consecutive stored points; every lane of every
-// launched warp takes part in the shuffles (lanes past np carry the product 1).
+// One warp covers 32 * kEdChunk consecutive stored points of rows [lo, hi); every
+// lane of every launched warp takes part in the shuffles (lanes past hi carry the
+// product 1).
 __global__ void __launch_bounds__(128) k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n,
-                                                    size_t np) {
+                                                    size_t np, size_t lo, size_t hi) {
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const size_t i0 = t * kEdChunk;
-    const int m = i0 >= np ? 0 : (int)(np - i0 < (size_t)kEdChunk ? np - i0 : (size_t)kEdChunk);
+    const size_t i0 = lo + t * kEdChunk;
+    const int m = i0 >= hi ? 0 : (int)(hi - i0 < (size_t)kEdChunk ? hi - i0 : (size_t)kEdChunk);
     fe xe[kEdChunk], ye[kEdChunk];
     bool ok[kEdChunk];
     ed_affine_chunk(in, n, np, i0, m, xe, ye, ok);
@@ -1086,18 +1089,40 @@ __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__
     M::store(P + id * kXyzzVec, acc);
 }
 
-// out[s][i] = sum_{e < F} in[s][i F + e], segments of m points.
+// Block (s, b) sums in[s][256 b .. 256 b + 255] (within the segment's m points) into
+// out[s][b]: one addition per thread, then a tree over the block in shared memory
+// (depth 8 additions per launch; a segment of m points needs log256 m launches).
+constexpr int kTreeThreads = 128;
+
 template <class M>
-__global__ void k_sum_segments(const uint4* __restrict__ in, size_t nseg, uint32_t m, uint32_t F,
-                               uint4* __restrict__ out) {
-    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const uint32_t mo = m / F;
-    if (id >= nseg * mo) return;
-    const size_t s = id / mo, i = id % mo;
+__global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restrict__ in, size_t nseg, uint32_t m,
+                                                          uint4* __restrict__ out) {
+    __shared__ uint4 sh[kTreeThreads * kXyzzVec];
+    const uint32_t nb = (m + 2 * kTreeThreads - 1) / (2 * kTreeThreads);
+    const size_t seg = blockIdx.x / nb;
+    const uint32_t b = blockIdx.x % nb;
+    if (seg >= nseg) return;
+    const int t = threadIdx.x;
+    const uint32_t i0 = b * 2 * kTreeThreads + t, i1 = i0 + kTreeThreads;
     typename M::acc acc;
-    M::set_inf(acc);
-    for (uint32_t e = 0; e < F; ++e) M::add_mem(acc, in + (s * m + i * F + e) * kXyzzVec);
-    M::store(out + id * kXyzzVec, acc);
+    if (i0 < m)
+        M::load(acc, in + (seg * m + i0) * kXyzzVec);
+    else
+        M::set_inf(acc);
+    if (i1 < m) M::add_mem(acc, in + (seg * m + i1) * kXyzzVec);
+    M::store(sh + t * kXyzzVec, acc);
+    for (int h = kTreeThreads / 2; h >= 1; h >>= 1) {
+        __syncthreads();
+        if (t < h) {
+            M::load(acc, sh + t * kXyzzVec);
+            M::add_mem(acc, sh + (t + h) * kXyzzVec);
+            M::store(sh + t * kXyzzVec, acc);
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int v = 0; v < kXyzzVec; ++v) out[(seg * nb + b) * kXyzzVec + v] = sh[v];
+    }
 }
 
 // Thread wi: S_w = Z_V + L * sum_k 2^k Z_k (Horner over k), Z laid out [nwin][logG + 1].
@@ -1364,15 +1389,23 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
 size_t stored_count(size_t n, uint32_t flags) { return (flags & MSM377_GLV) ? 2 * n : n; }
 int stored_vec(uint32_t flags) { return (flags & MSM377_EDWARDS) ? ModelEdwards::kStored : ModelXyzz::kStored; }
 
-void launch_prepare(const uint4* in, uint4* out, size_t n, uint32_t flags, cudaStream_t s) {
+// Stored rows of input points [a, b) (rows [a, b), or [2a, 2b) with GLV).
+void launch_prepare_range(const uint4* in, uint4* out, size_t n, size_t a, size_t b, uint32_t flags,
+                          cudaStream_t s) {
     const size_t np = stored_count(n, flags);
+    const size_t lo = stored_count(a, flags), hi = stored_count(b, flags);
+    if (hi <= lo) return;
     if (flags & MSM377_EDWARDS) {
-        const size_t threads = (np + kEdChunk - 1) / kEdChunk;  // whole warps: grid_for rounds up to 128
-        k_prepare_ed<<<msm377::grid_for(threads, 128), 128, 0, s>>>(in, out, n, np);
+        const size_t threads = (hi - lo + kEdChunk - 1) / kEdChunk;  // whole warps: grid_for rounds up to 128
+        k_prepare_ed<<<msm377::grid_for(threads, 128), 128, 0, s>>>(in, out, n, np, lo, hi);
     } else {
-        k_prepare<<<msm377::grid_for(np, 256), 256, 0, s>>>(in, out, n, np);
+        k_prepare<<<msm377::grid_for(hi - lo, 256), 256, 0, s>>>(in, out, n, np, lo, hi);
     }
     msm377::note_launches(1);
+}
+
+void launch_prepare(const uint4* in, uint4* out, size_t n, uint32_t flags, cudaStream_t s) {
+    launch_prepare_range(in, out, n, 0, n, flags, s);
 }
 
 template <typename T>
@@ -1568,10 +1601,10 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     uint4* zin = P0;
     uint4* zout = P1;
     while (m > 1) {
-        const uint32_t F = 2;  // pairwise rounds: depth log2 Q additions
-        k_sum_segments<M><<<grid_for(nseg * (m / F), 128), 128, 0, s>>>(zin, nseg, m, F, zout);
+        const uint32_t nb = (m + 2 * kTreeThreads - 1) / (2 * kTreeThreads);
+        k_sum_tree<M><<<(unsigned)(nseg * nb), kTreeThreads, 0, s>>>(zin, nseg, m, zout);
         note_launches(1);
-        m /= F;
+        m = nb;
         uint4* tmp = zin;
         zin = zout;
         zout = tmp;
@@ -1606,11 +1639,13 @@ int enqueue_accumulate(const Plan& p, const AccArgs& a, cudaStream_t s) {
 // Library-owned helper streams for batched calls, per device, created once.
 constexpr int kMaxDevices = 64;
 constexpr int kAuxStreams = 16;
+constexpr int kHostChunks = 2;  // the copy is short (about 200 GB/s); fewer, full-size preparation launches
 struct DeviceAux {
     bool ready = false;
     int sms = 0, acc_blocks_per_sm[2] = {0, 0};  // k_accumulate_batched per model
     cudaStream_t st[kAuxStreams];
     cudaEvent_t fork, done[kAuxStreams];
+    cudaEvent_t chunk[kHostChunks];  // msm_g1_host: point chunk k has arrived
 };
 DeviceAux g_aux[kMaxDevices];
 std::mutex g_aux_mu;
@@ -1634,6 +1669,7 @@ int device_aux(DeviceAux** out) {
             MSM_CUDA_TRY(cudaEventCreateWithFlags(&a.done[i], cudaEventDisableTiming));
         }
         MSM_CUDA_TRY(cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming));
+        for (int k = 0; k < kHostChunks; ++k) MSM_CUDA_TRY(cudaEventCreateWithFlags(&a.chunk[k], cudaEventDisableTiming));
         a.ready = true;
     }
     *out = &a;
@@ -1827,19 +1863,53 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
     if (!need) return set_error(MSM377_EINVAL, "msm_g1_host: bad options");
     if (workspace_bytes < need)
         return set_error(MSM377_ENOMEM, "msm_g1_host: workspace %zu bytes, need %zu", workspace_bytes, need);
+    if (!aligned(workspace, 256)) return set_error(MSM377_EINVAL, "msm_g1_host: workspace not 256-byte aligned");
     msm_opts o = *opts;
-    o.flags &= ~MSM377_POINTS_PREPARED;
-    size_t core = msm_g1_workspace_bytes(n, &o);
+    o.flags &= ~(MSM377_POINTS_PREPARED | MSM377_PROFILE);
+    Plan p;
+    if (!make_plan(n, &o, &p)) return set_error(MSM377_EINVAL, "msm_g1_host: bad options");
+    const size_t core = p.total;
     char* base = static_cast<char*>(workspace);
     uint32_t* d_pts = reinterpret_cast<uint32_t*>(base + core);
     uint32_t* d_sc = reinterpret_cast<uint32_t*>(base + core + align_up(n * 96, 256));
     uint32_t* d_out = reinterpret_cast<uint32_t*>(base + core + align_up(n * 96, 256) + align_up(n * 32, 256));
     cudaStream_t s = as_stream(o.stream);
-    if (n) {
-        MSM_CUDA_TRY(cudaMemcpyAsync(d_pts, points_host, n * 96, cudaMemcpyHostToDevice, s));
-        MSM_CUDA_TRY(cudaMemcpyAsync(d_sc, scalars_host, n * 32, cudaMemcpyHostToDevice, s));
+    if (n == 0) {
+        int r = msm_g1(d_pts, d_sc, 0, d_out, workspace, core, &o);
+        if (r) return r;
+        MSM_CUDA_TRY(cudaMemcpyAsync(out_host, d_out, 24 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        return msm_g1_status(workspace, &o);
     }
-    int r = msm_g1(d_pts, d_sc, n, d_out, workspace, core, &o);
+    // The points travel in chunks on one helper stream and are prepared chunk by
+    // chunk on another, while the scalars' copy, digits and bucket sort run on the
+    // caller's stream; the accumulation waits for the last prepared chunk.
+    DeviceAux* aux = nullptr;
+    int r = device_aux(&aux);
+    if (r) return r;
+    cudaStream_t sc = aux->st[0], sp = aux->st[1];
+    r = fork_from(aux, s, 2);
+    if (r) return r;
+    uint4* prep = at<uint4>(workspace, p.off_points);
+    const size_t per = (n + kHostChunks - 1) / kHostChunks;
+    for (int k = 0; k < kHostChunks; ++k) {
+        const size_t a = (size_t)k * per, b = a + per < n ? a + per : n;
+        if (a >= b) break;
+        MSM_CUDA_TRY(cudaMemcpyAsync(d_pts + 24 * a, points_host + 24 * a, (b - a) * 96, cudaMemcpyHostToDevice, sc));
+        MSM_CUDA_TRY(cudaEventRecord(aux->chunk[k], sc));
+        MSM_CUDA_TRY(cudaStreamWaitEvent(sp, aux->chunk[k], 0));
+        launch_prepare_range(reinterpret_cast<const uint4*>(d_pts), prep, n, a, b, o.flags, sp);
+    }
+    MSM_CUDA_TRY(cudaMemcpyAsync(d_sc, scalars_host, n * 32, cudaMemcpyHostToDevice, s));
+    msm_opts op = o;
+    op.flags |= MSM377_POINTS_PREPARED;  // the plan above keeps the prepared region in the workspace
+    AccArgs acc;
+    r = enqueue_head(p, reinterpret_cast<const uint32_t*>(prep), d_sc, workspace, &op, s, &acc);
+    if (r) return r;
+    r = join_into(aux, s, 2);
+    if (r) return r;
+    r = enqueue_accumulate(p, acc, s);
+    if (r) return r;
+    r = enqueue_tail(p, acc, workspace, d_out, s);
     if (r) return r;
     MSM_CUDA_TRY(cudaMemcpyAsync(out_host, d_out, 24 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     return msm_g1_status(workspace, &o);
