@@ -219,6 +219,117 @@ __device__ __forceinline__ void add_q(xyzz& P, const QL& q) {
 
 __device__ __forceinline__ void add(xyzz& P, const xyzz& Q) { add_q(P, RegQ{&Q}); }
 
+// ---- four lanes per point operation (latency-bound chains)
+//
+// A dependent chain of point operations (the window combination, the per-window
+// Horner sums) runs at the latency of one thread's multiplications. The
+// multiplications inside one formula fall into a few levels of independent
+// products, so four lanes of a warp that hold the same point each compute one
+// product of a level and exchange the results through shared memory. Every lane
+// of the warp calls these functions (lanes of the same group of four hold the same
+// values, so every branch is uniform within a group); `sh` is the group's
+// four-element shared slot and `l` = lane % 4.
+
+__device__ __forceinline__ void xchg4(fe (&v)[4], const fe& mine, fe* sh, int l, bool writer) {
+    if (writer) sh[l] = mine;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = sh[k];
+    __syncwarp();
+}
+
+// Word-wise select by lane role (no addresses taken, so everything stays in registers).
+__device__ __forceinline__ fe pick4(int l, const fe& a, const fe& b, const fe& c, const fe& d) {
+    fe r;
+#pragma unroll
+    for (int k = 0; k < fq::N; ++k)
+        r.v[k] = l == 0 ? a.v[k] : (l == 1 ? b.v[k] : (l == 2 ? c.v[k] : d.v[k]));
+    return r;
+}
+
+// P = 2P in three levels: {U^2 (U = 2Y), X^2}, {U V, X V, ZZ V, M^2 (M = 3X^2)},
+// {ZZZ W, W Y, M (S - X3)}: three multiplication latencies instead of nine. The
+// identity (ZZ = 0) and Y = 0 give ZZ3 = ZZ V = 0 without a branch.
+__device__ __forceinline__ void dbl4(xyzz& P, fe* sh, int l, bool writer) {
+    fe U, r, v[4];
+    fq::dbl(U, P.Y);
+    fe x = pick4(l, U, P.X, U, P.X);
+    fq::sqr(r, x);
+    xchg4(v, r, sh, l, writer);     // V, X^2
+    fe V = v[0], M, t;
+    fq::dbl(M, v[1]);
+    fq::add(M, M, v[1]);            // M = 3 X^2
+    x = pick4(l, U, P.X, P.ZZ, M);
+    fe y = pick4(l, V, V, V, M);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // W, S, ZZ3, M^2
+    fe W = v[0], S = v[1];
+    P.ZZ = v[2];
+    fq::dbl(t, S);
+    fq::sub(P.X, v[3], t);          // X3 = M^2 - 2S
+    fq::sub(t, S, P.X);             // S - X3
+    x = pick4(l, P.ZZZ, W, M, M);
+    y = pick4(l, W, P.Y, t, t);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // ZZZ3, W Y, M (S - X3)
+    P.ZZZ = v[0];
+    fq::sub(P.Y, v[2], v[1]);       // Y3
+}
+
+// P += Q (both XYZZ, Q through a loader) in four levels: {U1, U2, S1, S2},
+// {PP = Pd^2, R^2, ZZ1 ZZ2, ZZZ1 ZZZ2}, {PPP, Q1 = U1 PP, ZZ3}, {ZZZ3, S1 PPP,
+// R (Q1 - X3)}. The special cases branch as in add_q (uniform within a group).
+template <class QL>
+__device__ __forceinline__ void add4(xyzz& P, const QL& q, fe* sh, int l, bool writer) {
+    xyzz Q;
+    q.all(Q);
+    if (fq::is_zero(Q.ZZ)) return;  // Q = O
+    if (is_inf(P)) {
+        P = Q;
+        return;
+    }
+    fe r, v[4];
+    fe x = pick4(l, P.X, Q.X, P.Y, Q.Y);
+    fe y = pick4(l, Q.ZZ, P.ZZ, Q.ZZZ, P.ZZZ);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // U1, U2, S1, S2
+    const fe U1 = v[0], S1 = v[2];
+    fe Pd, R;
+    fq::sub(Pd, v[1], U1);
+    fq::sub(R, v[3], S1);
+    if (fq::is_zero(Pd)) {
+        if (fq::is_zero(R)) {
+            P = Q;                  // P = Q: the sum is 2Q
+            dbl4(P, sh, l, writer);
+        } else {
+            set_inf(P);
+        }
+        return;
+    }
+    x = pick4(l, Pd, R, P.ZZ, P.ZZZ);
+    y = pick4(l, Pd, R, Q.ZZ, Q.ZZZ);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // PP, R^2, ZZ1 ZZ2, ZZZ1 ZZZ2
+    const fe PP = v[0], RR = v[1], Z12 = v[2], ZZZ12 = v[3];
+    x = pick4(l, Pd, U1, Z12, Z12);
+    y = pick4(l, PP, PP, PP, PP);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // PPP, Q1, ZZ3
+    const fe PPP = v[0], Q1 = v[1];
+    P.ZZ = v[2];
+    fe t;
+    fq::sub(P.X, RR, PPP);
+    fq::dbl(t, Q1);
+    fq::sub(P.X, P.X, t);           // X3 = R^2 - PPP - 2 Q1
+    fq::sub(t, Q1, P.X);            // Q1 - X3
+    x = pick4(l, ZZZ12, S1, R, R);
+    y = pick4(l, PPP, PPP, t, t);
+    fq::mul(r, x, y);
+    xchg4(v, r, sh, l, writer);     // ZZZ3, S1 PPP, R (Q1 - X3)
+    P.ZZZ = v[0];
+    fq::sub(P.Y, v[2], v[1]);       // Y3
+}
+
 // Inverse by the optimized binary GCD of T. Pornin ("Optimized Binary GCD for
 // Modular Inversion", 2020): the binary extended GCD on (a, b) = (y, p), but 31
 // steps at a time on 64-bit approximations of a and b (their top 33 and low 31

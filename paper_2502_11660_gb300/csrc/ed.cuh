@@ -182,33 +182,12 @@ __device__ __forceinline__ void dbl(ext& P) {
     fq::mul(P.Y, P.Y, A);           // G H
 }
 
-// ---- four lanes per point operation (latency-bound chains)
-//
-// A dependent chain of point operations (the window combination, the per-window
-// Horner sums) runs at the latency of one thread's multiplications. The
-// multiplications inside one Edwards formula fall into two or three levels of
-// independent products, so four lanes of a warp that hold the same point each
-// compute one product of a level and exchange the results through shared memory:
-// a doubling costs two multiplication latencies instead of eight. Every lane of
-// the warp calls these functions (lanes of the same group of four hold the same
-// values); `sh` is the group's four-element shared slot and `l` = lane % 4.
-
-__device__ __forceinline__ void xchg4(fe (&v)[4], const fe& mine, fe* sh, int l, bool writer) {
-    if (writer) sh[l] = mine;
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = sh[k];
-    __syncwarp();
-}
-
-// Word-wise select by lane role (no addresses taken, so everything stays in registers).
-__device__ __forceinline__ fe pick4(int l, const fe& a, const fe& b, const fe& c, const fe& d) {
-    fe r;
-#pragma unroll
-    for (int k = 0; k < fq::N; ++k)
-        r.v[k] = l == 0 ? a.v[k] : (l == 1 ? b.v[k] : (l == 2 ? c.v[k] : d.v[k]));
-    return r;
-}
+// ---- four lanes per point operation (latency-bound chains; see ec::xchg4):
+// the multiplications of one Edwards formula fall into two or three levels of
+// independent products, so a doubling costs two multiplication latencies instead
+// of eight.
+using ec::pick4;
+using ec::xchg4;
 
 // P = 2P: level 1 {X^2, Y^2, Z^2, (X + Y)^2}, level 2 {E F, G H, E H, F G}.
 __device__ __forceinline__ void dbl4(ext& P, fe* sh, int l, bool writer) {

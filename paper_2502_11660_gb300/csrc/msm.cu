@@ -140,6 +140,10 @@ struct ModelXyzz {
     static __device__ __forceinline__ void add(acc& P, const acc& Q) { ec::add(P, Q); }
     static __device__ __forceinline__ void dbl(acc& P) { ec::dbl(P); }
     static __device__ __forceinline__ void to_affine(affine& A, const acc& P) { ec::to_affine(A, P); }
+    static __device__ __forceinline__ void dbl4(acc& P, fe* sh, int l) { ec::dbl4(P, sh, l, true); }
+    static __device__ __forceinline__ void add4_mem(acc& P, const uint4* q, fe* sh, int l) {
+        ec::add4(P, MemQ{q}, sh, l, true);
+    }
 };
 
 struct ModelEdwards {
@@ -176,6 +180,10 @@ struct ModelEdwards {
     static __device__ __forceinline__ void add(acc& P, const acc& Q) { ed::add(P, Q); }
     static __device__ __forceinline__ void dbl(acc& P) { ed::dbl(P); }
     static __device__ __forceinline__ void to_affine(affine& A, const acc& P) { ed::to_weierstrass(A, P); }
+    static __device__ __forceinline__ void dbl4(acc& P, fe* sh, int l) { ed::dbl4(P, sh, l, true); }
+    static __device__ __forceinline__ void add4_mem(acc& P, const uint4* q, fe* sh, int l) {
+        ed::add4(P, MemQE{q}, sh, l, true);
+    }
 };
 
 // ---------------------------------------------------------------- stage 1
@@ -1125,63 +1133,16 @@ __global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restri
     }
 }
 
-// Thread wi: S_w = Z_V + L * sum_k 2^k Z_k (Horner over k), Z laid out [nwin][logG + 1].
-template <class M>
-__global__ void k_window_horner(const uint4* __restrict__ Z, int nwin, int logG, int log2L, uint4* __restrict__ S) {
-    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (wi >= nwin) return;
-    const uint4* z = Z + (size_t)wi * (logG + 1) * kXyzzVec;
-    typename M::acc acc;
-    M::set_inf(acc);
-    for (int k = logG - 1; k >= 0; --k) {
-        M::dbl(acc);
-        M::add_mem(acc, z + (size_t)k * kXyzzVec);
-    }
-    for (int l = 0; l < log2L; ++l) M::dbl(acc);
-    M::add_mem(acc, z + (size_t)logG * kXyzzVec);
-    M::store(S + (size_t)wi * kXyzzVec, acc);
-}
-
 // ---------------------------------------------------------------- stage 7
 
-// One thread: acc = 2^(c) acc + S_w for w = w_hi - 1 down to w_lo (acc starts at
-// O for the top window of the MSM); when w_lo = 0 it normalises acc and writes
-// the affine result in standard form.
-template <class M>
-__global__ void k_chain(const uint4* __restrict__ S, int w_hi, int w_lo, int W, int c, uint4* __restrict__ accp,
-                        uint32_t* __restrict__ out) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    typename M::acc acc;
-    if (w_hi == W)
-        M::set_inf(acc);
-    else
-        M::load(acc, accp);
-    for (int w = w_hi - 1; w >= w_lo; --w) {
-        if (w < W - 1)  // the top window starts from the identity
-            for (int k = 0; k < c; ++k) M::dbl(acc);
-        M::add_mem(acc, S + (size_t)w * kXyzzVec);
-    }
-    if (w_lo > 0) {
-        M::store(accp, acc);
-        return;
-    }
-    affine A;
-    M::to_affine(A, acc);
-    if (!ec::is_inf(A)) {
-        fq::from_mont(A.x, A.x);
-        fq::from_mont(A.y, A.y);
-    }
-    fq::store(out, A.x);
-    fq::store(out + 12, A.y);
-}
-
-// Edwards versions of the two latency-bound chains with four lanes per point
-// operation (ed::dbl4 / ed::add4): each group of four lanes of a warp holds one
-// accumulator; all 32 lanes take part (every __syncwarp is warp-wide).
+// The two latency-bound chains with four lanes per point operation (dbl4 / add4 of
+// the model): each group of four lanes of a warp holds one accumulator; all 32
+// lanes take part (every __syncwarp is warp-wide).
 constexpr int kGroups = 8;  // groups of four lanes per warp
 
 // Group g of warp b: S_w for window w = 8 b + g (windows past nwin recompute the
 // last window and store nothing).
+template <class M>
 __global__ void __launch_bounds__(32) k_window_horner4(const uint4* __restrict__ Z, int nwin, int logG, int log2L,
                                                        uint4* __restrict__ S) {
     __shared__ fe sh[kGroups][4];
@@ -1189,32 +1150,33 @@ __global__ void __launch_bounds__(32) k_window_horner4(const uint4* __restrict__
     const int w = blockIdx.x * kGroups + g;
     const int wi = w < nwin ? w : nwin - 1;
     const uint4* z = Z + (size_t)wi * (logG + 1) * kXyzzVec;
-    ed::ext acc;
-    ed::set_inf(acc);
+    typename M::acc acc;
+    M::set_inf(acc);
     for (int k = logG - 1; k >= 0; --k) {
-        ed::dbl4(acc, sh[g], l, true);
-        ed::add4(acc, MemQE{z + (size_t)k * kXyzzVec}, sh[g], l, true);
+        M::dbl4(acc, sh[g], l);
+        M::add4_mem(acc, z + (size_t)k * kXyzzVec, sh[g], l);
     }
-    for (int t = 0; t < log2L; ++t) ed::dbl4(acc, sh[g], l, true);
-    ed::add4(acc, MemQE{z + (size_t)logG * kXyzzVec}, sh[g], l, true);
-    if (w < nwin && l == 0) ModelEdwards::store(S + (size_t)w * kXyzzVec, acc);
+    for (int t = 0; t < log2L; ++t) M::dbl4(acc, sh[g], l);
+    M::add4_mem(acc, z + (size_t)logG * kXyzzVec, sh[g], l);
+    if (w < nwin && l == 0) M::store(S + (size_t)w * kXyzzVec, acc);
 }
 
 // sum_w 2^(c w) S_w from the top window, then the affine result in standard form.
 // Every group computes the same chain; lane 0 writes the result.
+template <class M>
 __global__ void __launch_bounds__(32) k_chain4(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
     __shared__ fe sh[kGroups][4];
     const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
-    ed::ext acc;
-    ed::set_inf(acc);
+    typename M::acc acc;
+    M::set_inf(acc);
     for (int w = W - 1; w >= 0; --w) {
         if (w < W - 1)  // the top window starts from the identity
-            for (int k = 0; k < c; ++k) ed::dbl4(acc, sh[g], l, true);
-        ed::add4(acc, MemQE{S + (size_t)w * kXyzzVec}, sh[g], l, true);
+            for (int k = 0; k < c; ++k) M::dbl4(acc, sh[g], l);
+        M::add4_mem(acc, S + (size_t)w * kXyzzVec, sh[g], l);
     }
     if (lane != 0) return;
     affine A;
-    ModelEdwards::to_affine(A, acc);
+    M::to_affine(A, acc);
     if (!ec::is_inf(A)) {
         fq::from_mont(A.x, A.x);
         fq::from_mont(A.y, A.y);
@@ -1248,7 +1210,7 @@ struct Plan {
     int counting;                      // counting sort (else LSD radix sort)
     size_t nbins, off_bins, off_bsum;  // counting sort: bins (window, key) and scan tile totals
     size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
-    size_t off_S, off_acc, off_start, total;
+    size_t off_S, off_start, total;
 };
 
 constexpr uint64_t kReduceThreads = 32768;
@@ -1378,7 +1340,6 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->off_P0 = take(zs * XY);
     p->off_P1 = take(zs * XY);
     p->off_S = take((size_t)p->W * XY);
-    p->off_acc = take(XY);
     p->total = off;
     return true;
 }
@@ -1578,7 +1539,6 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     uint4* P0 = at<uint4>(workspace, p.off_P0);
     uint4* P1 = at<uint4>(workspace, p.off_P1);
     uint4* S = at<uint4>(workspace, p.off_S);
-    uint4* accp = at<uint4>(workspace, p.off_acc);
     const size_t nchunks = (size_t)p.W * p.cpw;
     // 5. merge partial sums of runs crossing chunk edges (log depth)
     int32_t* start = at<int32_t>(workspace, p.off_start);
@@ -1610,13 +1570,8 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
         zout = tmp;
     }
     // 7. window combination and normalisation
-    if (p.edw) {
-        k_window_horner4<<<grid_for(p.W, kGroups), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
-        k_chain4<<<1, 32, 0, s>>>(S, p.W, p.c, out);
-    } else {
-        k_window_horner<M><<<grid_for(p.W, 32), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
-        k_chain<M><<<1, 32, 0, s>>>(S, p.W, 0, p.W, p.c, accp, out);
-    }
+    k_window_horner4<M><<<grid_for(p.W, kGroups), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+    k_chain4<M><<<1, 32, 0, s>>>(S, p.W, p.c, out);
     note_launches(2);
     return check_launch("msm tail");
 }
