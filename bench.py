@@ -215,10 +215,12 @@ ACC_SECTIONS = (("// -----------------------------------------------------------
                  "// Batched MSMs:"))
 
 
-def kernel_hash() -> str:
+def kernel_hash(edwards: bool = True) -> str:
+    """Source hash of the accumulation kernel of one curve model: the field header,
+    that model's header and the msm.cu sections the kernel is compiled from."""
     csrc = os.path.join(ROOT, "paper_2502_11660_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("fq.cuh", "ec.cuh", "ed.cuh"):
+    for f in ("fq.cuh", "ed.cuh" if edwards else "ec.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     src = open(os.path.join(csrc, "msm.cu")).read()
     for start, end in ACC_SECTIONS:
@@ -235,7 +237,7 @@ def recorded_traffic(mode: str):
         return None, None
     recs = json.load(open(path))
     rec = recs.get(mode) if isinstance(recs, dict) and "kernel_hash" not in recs else None
-    if rec is None or rec.get("kernel_hash") != kernel_hash():
+    if rec is None or rec.get("kernel_hash") != kernel_hash(MODES[mode][0] or MODES[mode][2]):
         return None, rec
     return rec, rec
 
