@@ -278,16 +278,25 @@ __device__ __forceinline__ void dbl4(xyzz& P, fe* sh, int l, bool writer) {
 
 // P += Q (both XYZZ, Q through a loader) in four levels: {U1, U2, S1, S2},
 // {PP = Pd^2, R^2, ZZ1 ZZ2, ZZZ1 ZZZ2}, {PPP, Q1 = U1 PP, ZZ3}, {ZZZ3, S1 PPP,
-// R (Q1 - X3)}. The special cases branch as in add_q (uniform within a group).
+// R (Q1 - X3)}. Groups of one warp may hold different points, so every group runs
+// the same exchanges (a __syncwarp is warp-wide): the special cases (Q = O, P = O,
+// P = -Q, P = Q) are computed alongside and chosen by selects, and the doubling
+// that P = Q needs runs, for every group, only when some group of the warp needs it.
+__device__ __forceinline__ void select(xyzz& P, bool take, const xyzz& Q) {
+#pragma unroll
+    for (int k = 0; k < fq::N; ++k) {
+        P.X.v[k] = take ? Q.X.v[k] : P.X.v[k];
+        P.Y.v[k] = take ? Q.Y.v[k] : P.Y.v[k];
+        P.ZZ.v[k] = take ? Q.ZZ.v[k] : P.ZZ.v[k];
+        P.ZZZ.v[k] = take ? Q.ZZZ.v[k] : P.ZZZ.v[k];
+    }
+}
+
 template <class QL>
 __device__ __forceinline__ void add4(xyzz& P, const QL& q, fe* sh, int l, bool writer) {
     xyzz Q;
     q.all(Q);
-    if (fq::is_zero(Q.ZZ)) return;  // Q = O
-    if (is_inf(P)) {
-        P = Q;
-        return;
-    }
+    const bool q_inf = fq::is_zero(Q.ZZ), p_inf = is_inf(P);
     fe r, v[4];
     fe x = pick4(l, P.X, Q.X, P.Y, Q.Y);
     fe y = pick4(l, Q.ZZ, P.ZZ, Q.ZZZ, P.ZZZ);
@@ -297,15 +306,12 @@ __device__ __forceinline__ void add4(xyzz& P, const QL& q, fe* sh, int l, bool w
     fe Pd, R;
     fq::sub(Pd, v[1], U1);
     fq::sub(R, v[3], S1);
-    if (fq::is_zero(Pd)) {
-        if (fq::is_zero(R)) {
-            P = Q;                  // P = Q: the sum is 2Q
-            dbl4(P, sh, l, writer);
-        } else {
-            set_inf(P);
-        }
-        return;
-    }
+    const bool same_x = !q_inf && !p_inf && fq::is_zero(Pd);
+    const bool doubling = same_x && fq::is_zero(R);     // P = Q
+    const bool cancel = same_x && !doubling;            // P = -Q
+    xyzz D = Q;
+    if (__any_sync(0xffffffffu, doubling)) dbl4(D, sh, l, writer);  // warp-uniform branch
+    xyzz S = P;
     x = pick4(l, Pd, R, P.ZZ, P.ZZZ);
     y = pick4(l, Pd, R, Q.ZZ, Q.ZZZ);
     fq::mul(r, x, y);
@@ -316,18 +322,25 @@ __device__ __forceinline__ void add4(xyzz& P, const QL& q, fe* sh, int l, bool w
     fq::mul(r, x, y);
     xchg4(v, r, sh, l, writer);     // PPP, Q1, ZZ3
     const fe PPP = v[0], Q1 = v[1];
-    P.ZZ = v[2];
+    S.ZZ = v[2];
     fe t;
-    fq::sub(P.X, RR, PPP);
+    fq::sub(S.X, RR, PPP);
     fq::dbl(t, Q1);
-    fq::sub(P.X, P.X, t);           // X3 = R^2 - PPP - 2 Q1
-    fq::sub(t, Q1, P.X);            // Q1 - X3
+    fq::sub(S.X, S.X, t);           // X3 = R^2 - PPP - 2 Q1
+    fq::sub(t, Q1, S.X);            // Q1 - X3
     x = pick4(l, ZZZ12, S1, R, R);
     y = pick4(l, PPP, PPP, t, t);
     fq::mul(r, x, y);
     xchg4(v, r, sh, l, writer);     // ZZZ3, S1 PPP, R (Q1 - X3)
-    P.ZZZ = v[0];
-    fq::sub(P.Y, v[2], v[1]);       // Y3
+    S.ZZZ = v[0];
+    fq::sub(S.Y, v[2], v[1]);       // Y3
+    xyzz O;
+    set_inf(O);
+    select(S, doubling, D);
+    select(S, cancel, O);
+    select(S, p_inf, Q);
+    select(S, q_inf, P);
+    P = S;
 }
 
 // Inverse by the optimized binary GCD of T. Pornin ("Optimized Binary GCD for
