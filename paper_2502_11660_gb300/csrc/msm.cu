@@ -126,6 +126,7 @@ struct MemQE {
 
 struct ModelXyzz {
     using acc = xyzz;
+    static constexpr int kDblDepth = 3, kAddDepth = 4;  // multiplication levels of dbl4 / add4
     static constexpr int kStored = 6;  // affine (x, y)
     static __device__ __forceinline__ void set_inf(acc& P) { ec::set_inf(P); }
     static __device__ __forceinline__ void load(acc& P, const uint4* p) { load_xyzz(P, p); }
@@ -148,6 +149,7 @@ struct ModelXyzz {
 
 struct ModelEdwards {
     using acc = ed::ext;
+    static constexpr int kDblDepth = 2, kAddDepth = 3;  // multiplication levels of dbl4 / add4
     static constexpr int kStored = 9;  // (x, y, u = k x y), the paper's (X, Y, U) with Z = 1
     static __device__ __forceinline__ void set_inf(acc& P) { ed::set_inf(P); }
     static __device__ __forceinline__ void load(acc& P, const uint4* p) {
@@ -1073,8 +1075,10 @@ __global__ void __launch_bounds__(128, 4) k_reduce_segments(const uint4* __restr
     M::store(V + id * kXyzzVec, S);
 }
 
-// Thread (wi, k, q): partial of Z_k = sum_{g in chunk q, bit k of g set} Y_g, or for
-// k == logG the partial of sum_{g in chunk q} V_g.
+// Thread (wi, k, q): partial of Z_k = sum_{g: bit k of g set} Y_g over the q-th of Q
+// equal slices of those G/2 indices, or for k == logG the partial of sum_g V_g over
+// the q-th slice of all G indices. The j-th index with bit k set is j with a one
+// inserted at bit k, so the threads of a warp (same k) run the same additions.
 template <class M>
 __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__ V, int nwin, uint32_t G,
                           int logG, uint32_t Q, uint4* __restrict__ P) {
@@ -1084,53 +1088,69 @@ __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__
     const size_t wi = id / per_w;
     const int k = (int)((id % per_w) / Q);
     const uint32_t q = (uint32_t)(id % Q);
-    const uint32_t span = G / Q, g0 = q * span;
     typename M::acc acc;
     M::set_inf(acc);
-    for (uint32_t g = g0; g < g0 + span; ++g) {
-        if (k == logG) {
-            M::add_mem(acc, V + (wi * G + g) * kXyzzVec);
-        } else if ((g >> k) & 1u) {
+    if (k == logG) {
+        const uint32_t span = G / Q, g0 = q * span;
+        for (uint32_t g = g0; g < g0 + span; ++g) M::add_mem(acc, V + (wi * G + g) * kXyzzVec);
+    } else {
+        const uint32_t span = (G / 2) / Q, j0 = q * span, low = (1u << k) - 1u;
+        for (uint32_t j = j0; j < j0 + span; ++j) {
+            const uint32_t g = ((j & ~low) << 1) | (1u << k) | (j & low);
             M::add_mem(acc, Y + (wi * G + g) * kXyzzVec);
         }
     }
     M::store(P + id * kXyzzVec, acc);
 }
 
-// Block (s, b) sums in[s][256 b .. 256 b + 255] (within the segment's m points) into
-// out[s][b]: one addition per thread, then a tree over the block in shared memory
-// (depth 8 additions per launch; a segment of m points needs log256 m launches).
+// Block (s, b) sums in[s][64 b .. 64 b + 63] (within the segment's m points) into
+// out[s][b] with four lanes per addition: group j of the block's 32 groups adds
+// in[64 b + j] and in[64 b + 32 + j], then a tree over the groups in shared memory
+// (depth 6 four-lane additions per launch; a segment of m points needs log64 m
+// launches). Every group of a warp runs the same additions (a missing operand is
+// the identity; idle groups of warp 0 add and discard), so each __syncwarp inside
+// them is warp-wide; a warp with no active group skips a level as a whole.
 constexpr int kTreeThreads = 128;
+constexpr int kTreeGroups = kTreeThreads / 4;
+constexpr uint32_t kTreeFanIn = 2 * kTreeGroups;
 
 template <class M>
 __global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restrict__ in, size_t nseg, uint32_t m,
                                                           uint4* __restrict__ out) {
-    __shared__ uint4 sh[kTreeThreads * kXyzzVec];
-    const uint32_t nb = (m + 2 * kTreeThreads - 1) / (2 * kTreeThreads);
+    __shared__ uint4 pub[kTreeGroups * kXyzzVec];
+    __shared__ uint4 idn[kXyzzVec];
+    __shared__ fe sh[kTreeGroups][4];
+    const uint32_t nb = (m + kTreeFanIn - 1) / kTreeFanIn;
     const size_t seg = blockIdx.x / nb;
     const uint32_t b = blockIdx.x % nb;
-    if (seg >= nseg) return;
-    const int t = threadIdx.x;
-    const uint32_t i0 = b * 2 * kTreeThreads + t, i1 = i0 + kTreeThreads;
+    if (seg >= nseg) return;  // whole block
+    const int t = threadIdx.x, g = t >> 2, l = t & 3, warp = t >> 5;
+    if (t == 0) {
+        typename M::acc e;
+        M::set_inf(e);
+        M::store(idn, e);
+    }
+    __syncthreads();
+    const uint32_t i0 = b * kTreeFanIn + g, i1 = i0 + kTreeGroups;
     typename M::acc acc;
     if (i0 < m)
         M::load(acc, in + (seg * m + i0) * kXyzzVec);
     else
         M::set_inf(acc);
-    if (i1 < m) M::add_mem(acc, in + (seg * m + i1) * kXyzzVec);
-    M::store(sh + t * kXyzzVec, acc);
-    for (int h = kTreeThreads / 2; h >= 1; h >>= 1) {
+    M::add4_mem(acc, i1 < m ? in + (seg * m + i1) * kXyzzVec : idn, sh[g], l);
+    // level h: groups [h, 2h) publish, groups [0, h) add them. The slots read at
+    // level h, [h, 2h), are never written at a later level (those write [h', 2h')
+    // with 2h' <= h), so one barrier per level orders every access.
+    for (int h = kTreeGroups / 2; h >= 1; h >>= 1) {
+        if (g >= h && g < 2 * h && l == 0) M::store(pub + g * kXyzzVec, acc);
         __syncthreads();
-        if (t < h) {
-            M::load(acc, sh + t * kXyzzVec);
-            M::add_mem(acc, sh + (t + h) * kXyzzVec);
-            M::store(sh + t * kXyzzVec, acc);
+        if (warp * 8 < h) {
+            typename M::acc r = acc;
+            M::add4_mem(r, pub + (g + h) * kXyzzVec, sh[g], l);  // g + h < 32: g < h for h >= 8, g <= 7 below
+            if (g < h) acc = r;
         }
     }
-    __syncthreads();
-    if (t == 0) {
-        for (int v = 0; v < kXyzzVec; ++v) out[(seg * nb + b) * kXyzzVec + v] = sh[v];
-    }
+    if (t == 0) M::store(out + (seg * nb + b) * kXyzzVec, acc);
 }
 
 // ---------------------------------------------------------------- stage 7
@@ -1140,40 +1160,77 @@ __global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restri
 // lanes take part (every __syncwarp is warp-wide).
 constexpr int kGroups = 8;  // groups of four lanes per warp
 
-// Group g of warp b: S_w for window w = 8 b + g (windows past nwin recompute the
-// last window and store nothing).
+// Every group of the warp ends with acc = sum_{j < cnt} 2^(e j) X_j (X_j at
+// x + j * kXyzzVec). With 2^q groups of four lanes and r = ceil(cnt / 2^q) terms
+// each, group i forms T_i = sum_{j < r} 2^(e j) X_{ir+j} by Horner (e (r - 1)
+// doublings, r additions); then q rounds of a tree give sum_i 2^(e r i) T_i: in the
+// round of stride s group i + s doubles a copy of its partial e r s times and group
+// i (a multiple of 2s) adds it. The critical path is e (r 2^q - 1) doublings and
+// r + q additions (Horner alone: e (cnt - 1) and cnt); q is chosen to minimise its
+// multiplication depth. Every group runs the same operations (groups past 2^q work
+// on the identity and on copies), so every __syncwarp is warp-wide; group 0 holds
+// the result (the other groups' acc is not meaningful).
+template <class M>
+__device__ __forceinline__ void weighted_sum4(typename M::acc& acc, const uint4* __restrict__ x, int cnt, int e,
+                                              fe (*sh)[4], uint4* pub, uint4* idn, int g, int l) {
+    if ((threadIdx.x & 31) == 0) {
+        typename M::acc id;
+        M::set_inf(id);
+        M::store(idn, id);
+    }
+    int q = 0, r = cnt, best = e * (cnt - 1) * M::kDblDepth + cnt * M::kAddDepth;
+    for (int qq = 1; (1 << qq) <= kGroups; ++qq) {
+        const int rr = (cnt + (1 << qq) - 1) >> qq;
+        const int cost = e * (rr * (1 << qq) - 1) * M::kDblDepth + (rr + qq) * M::kAddDepth;
+        if (cost < best) best = cost, q = qq, r = rr;
+    }
+    __syncwarp();
+    M::set_inf(acc);
+    for (int j = r - 1; j >= 0; --j) {
+        if (j < r - 1)
+            for (int t = 0; t < e; ++t) M::dbl4(acc, sh[g], l);
+        const int k = g * r + j;
+        M::add4_mem(acc, k < cnt ? x + (size_t)k * kXyzzVec : idn, sh[g], l);
+    }
+    for (int st = 1; st < (1 << q); st <<= 1) {
+        typename M::acc D = acc;
+        for (int t = 0; t < e * r * st; ++t) M::dbl4(D, sh[g], l);
+        if (l == 0) M::store(pub + g * kXyzzVec, D);
+        __syncwarp();
+        typename M::acc R = acc;
+        M::add4_mem(R, pub + ((g + st) & (kGroups - 1)) * kXyzzVec, sh[g], l);
+        if ((g & (2 * st - 1)) == 0) acc = R;
+        __syncwarp();  // every lane has read pub before the next round writes it
+    }
+}
+
+// Warp w: S_w = L sum_{k < logG} 2^k Z_k + Z_logG for window w.
 template <class M>
 __global__ void __launch_bounds__(32) k_window_horner4(const uint4* __restrict__ Z, int nwin, int logG, int log2L,
                                                        uint4* __restrict__ S) {
     __shared__ fe sh[kGroups][4];
+    __shared__ uint4 pub[kGroups * kXyzzVec];
+    __shared__ uint4 idn[kXyzzVec];
     const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
-    const int w = blockIdx.x * kGroups + g;
-    const int wi = w < nwin ? w : nwin - 1;
-    const uint4* z = Z + (size_t)wi * (logG + 1) * kXyzzVec;
+    const int w = blockIdx.x;
+    if (w >= nwin) return;  // whole warp
+    const uint4* z = Z + (size_t)w * (logG + 1) * kXyzzVec;
     typename M::acc acc;
-    M::set_inf(acc);
-    for (int k = logG - 1; k >= 0; --k) {
-        M::dbl4(acc, sh[g], l);
-        M::add4_mem(acc, z + (size_t)k * kXyzzVec, sh[g], l);
-    }
+    weighted_sum4<M>(acc, z, logG, 1, sh, pub, idn, g, l);
     for (int t = 0; t < log2L; ++t) M::dbl4(acc, sh[g], l);
     M::add4_mem(acc, z + (size_t)logG * kXyzzVec, sh[g], l);
-    if (w < nwin && l == 0) M::store(S + (size_t)w * kXyzzVec, acc);
+    if (lane == 0) M::store(S + (size_t)w * kXyzzVec, acc);
 }
 
-// sum_w 2^(c w) S_w from the top window, then the affine result in standard form.
-// Every group computes the same chain; lane 0 writes the result.
+// sum_w 2^(c w) S_w, then the affine result in standard form (lane 0 writes it).
 template <class M>
 __global__ void __launch_bounds__(32) k_chain4(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
     __shared__ fe sh[kGroups][4];
+    __shared__ uint4 pub[kGroups * kXyzzVec];
+    __shared__ uint4 idn[kXyzzVec];
     const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
     typename M::acc acc;
-    M::set_inf(acc);
-    for (int w = W - 1; w >= 0; --w) {
-        if (w < W - 1)  // the top window starts from the identity
-            for (int k = 0; k < c; ++k) M::dbl4(acc, sh[g], l);
-        M::add4_mem(acc, S + (size_t)w * kXyzzVec, sh[g], l);
-    }
+    weighted_sum4<M>(acc, S, W, c, sh, pub, idn, g, l);
     if (lane != 0) return;
     affine A;
     M::to_affine(A, acc);
@@ -1561,7 +1618,7 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     uint4* zin = P0;
     uint4* zout = P1;
     while (m > 1) {
-        const uint32_t nb = (m + 2 * kTreeThreads - 1) / (2 * kTreeThreads);
+        const uint32_t nb = (m + kTreeFanIn - 1) / kTreeFanIn;
         k_sum_tree<M><<<(unsigned)(nseg * nb), kTreeThreads, 0, s>>>(zin, nseg, m, zout);
         note_launches(1);
         m = nb;
@@ -1570,7 +1627,7 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
         zout = tmp;
     }
     // 7. window combination and normalisation
-    k_window_horner4<M><<<grid_for(p.W, kGroups), 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+    k_window_horner4<M><<<(unsigned)p.W, 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
     k_chain4<M><<<1, 32, 0, s>>>(S, p.W, p.c, out);
     note_launches(2);
     return check_launch("msm tail");
