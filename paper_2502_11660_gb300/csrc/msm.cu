@@ -1086,7 +1086,8 @@ __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__
     const size_t per_w = (size_t)(logG + 1) * Q;
     if (id >= (size_t)nwin * per_w) return;
     const size_t wi = id / per_w;
-    const int k = (int)((id % per_w) / Q);
+    const int kk = (int)((id % per_w) / Q);
+    const int k = kk == 0 ? logG : kk - 1;  // the V slices (twice as long) are scheduled first
     const uint32_t q = (uint32_t)(id % Q);
     typename M::acc acc;
     M::set_inf(acc);
@@ -1100,27 +1101,29 @@ __global__ void k_bitsums(const uint4* __restrict__ Y, const uint4* __restrict__
             M::add_mem(acc, Y + (wi * G + g) * kXyzzVec);
         }
     }
-    M::store(P + id * kXyzzVec, acc);
+    M::store(P + (wi * per_w + (size_t)k * Q + q) * kXyzzVec, acc);
 }
 
-// Block (s, b) sums in[s][64 b .. 64 b + 63] (within the segment's m points) into
-// out[s][b] with four lanes per addition: group j of the block's 32 groups adds
-// in[64 b + j] and in[64 b + 32 + j], then a tree over the groups in shared memory
-// (depth 6 four-lane additions per launch; a segment of m points needs log64 m
-// launches). Every group of a warp runs the same additions (a missing operand is
-// the identity; idle groups of warp 0 add and discard), so each __syncwarp inside
-// them is warp-wide; a warp with no active group skips a level as a whole.
+// Block (s, b) sums in[s][F 32 b .. F 32 (b + 1) - 1] (within the segment's m points)
+// into out[s][b] with four lanes per addition: group j of the block's 32 groups sums
+// in[F 32 b + j + 32 f] for f < F in sequence, then a tree over the groups in shared
+// memory (depth F - 1 + 5 four-lane additions; a segment of m points needs
+// log_(32 F) m launches; F is chosen so that a launch fills about one wave of
+// blocks). Every group of a warp runs the same additions (a missing operand is the
+// identity; idle groups of warp 0 add and discard), so each __syncwarp inside them
+// is warp-wide; a warp with no active group skips a level as a whole.
 constexpr int kTreeThreads = 128;
 constexpr int kTreeGroups = kTreeThreads / 4;
-constexpr uint32_t kTreeFanIn = 2 * kTreeGroups;
+constexpr size_t kTreeWave = 152 * 3;  // blocks resident at once (3 per SM)
 
 template <class M>
 __global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restrict__ in, size_t nseg, uint32_t m,
-                                                          uint4* __restrict__ out) {
+                                                          uint32_t F, uint4* __restrict__ out) {
     __shared__ uint4 pub[kTreeGroups * kXyzzVec];
     __shared__ uint4 idn[kXyzzVec];
     __shared__ fe sh[kTreeGroups][4];
-    const uint32_t nb = (m + kTreeFanIn - 1) / kTreeFanIn;
+    const uint32_t per = kTreeGroups * F;
+    const uint32_t nb = (m + per - 1) / per;
     const size_t seg = blockIdx.x / nb;
     const uint32_t b = blockIdx.x % nb;
     if (seg >= nseg) return;  // whole block
@@ -1131,13 +1134,16 @@ __global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restri
         M::store(idn, e);
     }
     __syncthreads();
-    const uint32_t i0 = b * kTreeFanIn + g, i1 = i0 + kTreeGroups;
+    const uint32_t i0 = b * per + g;
     typename M::acc acc;
     if (i0 < m)
         M::load(acc, in + (seg * m + i0) * kXyzzVec);
     else
         M::set_inf(acc);
-    M::add4_mem(acc, i1 < m ? in + (seg * m + i1) * kXyzzVec : idn, sh[g], l);
+    for (uint32_t f = 1; f < F; ++f) {
+        const uint32_t i = i0 + f * kTreeGroups;
+        M::add4_mem(acc, i < m ? in + (seg * m + i) * kXyzzVec : idn, sh[g], l);
+    }
     // level h: groups [h, 2h) publish, groups [0, h) add them. The slots read at
     // level h, [h, 2h), are never written at a later level (those write [h', 2h')
     // with 2h' <= h), so one barrier per level orders every access.
@@ -1618,8 +1624,10 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     uint4* zin = P0;
     uint4* zout = P1;
     while (m > 1) {
-        const uint32_t nb = (m + kTreeFanIn - 1) / kTreeFanIn;
-        k_sum_tree<M><<<(unsigned)(nseg * nb), kTreeThreads, 0, s>>>(zin, nseg, m, zout);
+        uint32_t F = 2;  // per-group fan-in: about one wave of blocks, at most 8 sequential additions
+        while (F < 8 && nseg * ((m + kTreeGroups * F - 1) / (kTreeGroups * F)) > kTreeWave) F <<= 1;
+        const uint32_t nb = (m + kTreeGroups * F - 1) / (kTreeGroups * F);
+        k_sum_tree<M><<<(unsigned)(nseg * nb), kTreeThreads, 0, s>>>(zin, nseg, m, F, zout);
         note_launches(1);
         m = nb;
         uint4* tmp = zin;
