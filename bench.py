@@ -414,7 +414,7 @@ def run_ours(args):
     kname = "k_accumulate<%s>" % ("ModelEdwards" if edw else "ModelXyzz")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak / 1e12,
                 "unit": "Tprod/s", "frac": achieved / peak,
-                "peak_source": "of measured: msm377_imad_probe (mad.lo.cc/madc.hi.cc rows, all SMs)",
+                "peak_source": "of measured: msm377_imad_probe (even/odd mad.lo.cc/madc.hi.cc chains, all SMs)",
                 "algorithmic_products_per_launch": ops["accumulate_products"],
                 "traffic": (rec["bytes_per_launch_full"] if rec else None)}
     padds = ops["madd"] + ops["bucket_running_sum_adds"] + ops["window_dbls"]
@@ -611,10 +611,11 @@ def batch_ops(pkg, torch, dev, stream):
 
     ms_mul = timed(lambda: pkg.fq_mul_batch(mA, mB, out=out, form=pkg.FORM_MONTGOMERY))
     # the alternative multiplications on the same operands (variants: Sec. III-C Barrett,
-    # Karatsuba top level, radix-2^24 carry-save), one kernel each
+    # Karatsuba top level, radix-2^24 carry-save, two-pass CIOS rows), one kernel each
     variants = {}
     for name, v in (("cios", pkg.FQMUL_CIOS), ("barrett", pkg.FQMUL_BARRETT),
-                    ("karatsuba", pkg.FQMUL_KARATSUBA), ("carrysave", pkg.FQMUL_CARRYSAVE)):
+                    ("karatsuba", pkg.FQMUL_KARATSUBA), ("carrysave", pkg.FQMUL_CARRYSAVE),
+                    ("cios_twopass", pkg.FQMUL_CIOS_TWOPASS)):
         ms_v = timed(lambda v=v: pkg.fq_mul_batch_variant(mA, mB, v, out=out))
         variants[name] = {"ms_2^24": ms_v, "mul_per_s": n / (ms_v / 1e3)}
     del mA, mB, out

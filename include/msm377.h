@@ -79,11 +79,17 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
  *                          word-by-word Montgomery reduction
  *   MSM377_FQMUL_CARRYSAVE a b 2^-384 mod p on 16 digits of 24 bits with 64-bit
  *                          column sums and deferred carries (Sec. III-B, III-D)
+ *   MSM377_FQMUL_CIOS_TWOPASS a b 2^-384 mod p, the same CIOS product with each
+ *                          row as a chain of low halves followed by a chain of
+ *                          high halves (the library's multiplication runs each
+ *                          row as two independent chains of adjacent low/high
+ *                          halves of the even- and odd-indexed limbs' products)
  * MSM377_EINVAL for another variant. */
 #define MSM377_FQMUL_CIOS 0
 #define MSM377_FQMUL_BARRETT 1
 #define MSM377_FQMUL_KARATSUBA 2
 #define MSM377_FQMUL_CARRYSAVE 3
+#define MSM377_FQMUL_CIOS_TWOPASS 4
 int fq_mul_batch_variant(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, int variant,
                          void *stream);
 
@@ -324,8 +330,10 @@ uint64_t msm377_launch_count(void);
 
 /* ------------------------------------------------------------------------
  * Micro-benchmark for the roofline denominator: runs `iters` rounds of
- * independent mad.lo.cc / madc.hi.cc pairs on every SM and writes the measured
- * count of 32x32->64 limb products per second into *products_per_s. Synchronous.
+ * Montgomery-row-shaped carry chains (mad.lo.cc / madc.hi.cc of one product
+ * adjacent, even- and odd-indexed limbs in two chains, two independent rows) on
+ * every SM and writes the measured count of 32x32->64 limb products per second
+ * into *products_per_s. Synchronous.
  */
 int msm377_imad_probe(int iters, double *products_per_s, void *stream);
 

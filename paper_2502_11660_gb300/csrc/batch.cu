@@ -162,58 +162,53 @@ __global__ void k_gen_mul(const uint32_t* __restrict__ seeds, size_t n, uint32_t
     }
 }
 
-// Roofline probe: two independent 12-product rows per iteration, the same
-// mad.lo.cc / madc.hi.cc chain shape as a Montgomery multiplication row.
+// Roofline probe: two independent 12-product rows per iteration, each in the shape
+// of a Montgomery multiplication row: two carry chains (the products with the
+// even- and the odd-indexed limbs), the low and high halves of one product
+// adjacent in a chain. (The same products as one low-half chain followed by one
+// high-half chain run at two thirds of this rate on GB300, so the denominator is
+// the faster shape.)
 __global__ void k_imad_probe(int iters, uint32_t seed, uint32_t* sink) {
-    uint32_t t[13], u[13], b[12];
+    uint32_t t[13], u[13], v[13], w[13], b[12];
 #pragma unroll
     for (int k = 0; k < 13; ++k) {
         t[k] = seed + k + threadIdx.x;
         u[k] = seed * 3 + k;
+        v[k] = seed * 5 + k;
+        w[k] = seed * 7 + k + blockIdx.x;
     }
 #pragma unroll
     for (int k = 0; k < 12; ++k) b[k] = seed ^ (0x9e3779b9u * (k + 1));
     uint32_t x = threadIdx.x | 1u, y = blockIdx.x | 3u;
     for (int it = 0; it < iters; ++it) {
-#define PROBE_ROW(T, A)                                                                           \
+#define PROBE_CHAIN(T, A, B0, B1, B2, B3, B4, B5)                                                  \
     asm("mad.lo.cc.u32 %0, %13, %14, %0;\n\t"                                                     \
-        "madc.lo.cc.u32 %1, %13, %15, %1;\n\t"                                                    \
-        "madc.lo.cc.u32 %2, %13, %16, %2;\n\t"                                                    \
-        "madc.lo.cc.u32 %3, %13, %17, %3;\n\t"                                                    \
-        "madc.lo.cc.u32 %4, %13, %18, %4;\n\t"                                                    \
-        "madc.lo.cc.u32 %5, %13, %19, %5;\n\t"                                                    \
-        "madc.lo.cc.u32 %6, %13, %20, %6;\n\t"                                                    \
-        "madc.lo.cc.u32 %7, %13, %21, %7;\n\t"                                                    \
-        "madc.lo.cc.u32 %8, %13, %22, %8;\n\t"                                                    \
-        "madc.lo.cc.u32 %9, %13, %23, %9;\n\t"                                                    \
-        "madc.lo.cc.u32 %10, %13, %24, %10;\n\t"                                                  \
-        "madc.lo.cc.u32 %11, %13, %25, %11;\n\t"                                                  \
-        "addc.u32 %12, %12, 0;\n\t"                                                               \
-        "mad.hi.cc.u32 %1, %13, %14, %1;\n\t"                                                     \
-        "madc.hi.cc.u32 %2, %13, %15, %2;\n\t"                                                    \
-        "madc.hi.cc.u32 %3, %13, %16, %3;\n\t"                                                    \
-        "madc.hi.cc.u32 %4, %13, %17, %4;\n\t"                                                    \
-        "madc.hi.cc.u32 %5, %13, %18, %5;\n\t"                                                    \
-        "madc.hi.cc.u32 %6, %13, %19, %6;\n\t"                                                    \
-        "madc.hi.cc.u32 %7, %13, %20, %7;\n\t"                                                    \
-        "madc.hi.cc.u32 %8, %13, %21, %8;\n\t"                                                    \
-        "madc.hi.cc.u32 %9, %13, %22, %9;\n\t"                                                    \
-        "madc.hi.cc.u32 %10, %13, %23, %10;\n\t"                                                  \
-        "madc.hi.cc.u32 %11, %13, %24, %11;\n\t"                                                  \
-        "madc.hi.u32 %12, %13, %25, %12;"                                                         \
+        "madc.hi.cc.u32 %1, %13, %14, %1;\n\t"                                                    \
+        "madc.lo.cc.u32 %2, %13, %15, %2;\n\t"                                                    \
+        "madc.hi.cc.u32 %3, %13, %15, %3;\n\t"                                                    \
+        "madc.lo.cc.u32 %4, %13, %16, %4;\n\t"                                                    \
+        "madc.hi.cc.u32 %5, %13, %16, %5;\n\t"                                                    \
+        "madc.lo.cc.u32 %6, %13, %17, %6;\n\t"                                                    \
+        "madc.hi.cc.u32 %7, %13, %17, %7;\n\t"                                                    \
+        "madc.lo.cc.u32 %8, %13, %18, %8;\n\t"                                                    \
+        "madc.hi.cc.u32 %9, %13, %18, %9;\n\t"                                                    \
+        "madc.lo.cc.u32 %10, %13, %19, %10;\n\t"                                                  \
+        "madc.hi.cc.u32 %11, %13, %19, %11;\n\t"                                                  \
+        "addc.u32 %12, %12, 0;"                                                                   \
         : "+r"(T[0]), "+r"(T[1]), "+r"(T[2]), "+r"(T[3]), "+r"(T[4]), "+r"(T[5]), "+r"(T[6]),     \
           "+r"(T[7]), "+r"(T[8]), "+r"(T[9]), "+r"(T[10]), "+r"(T[11]), "+r"(T[12])               \
-        : "r"(A), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]),    \
-          "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]))
-        PROBE_ROW(t, x);
-        PROBE_ROW(u, y);
-#undef PROBE_ROW
+        : "r"(A), "r"(B0), "r"(B1), "r"(B2), "r"(B3), "r"(B4), "r"(B5))
+        PROBE_CHAIN(t, x, b[0], b[2], b[4], b[6], b[8], b[10]);
+        PROBE_CHAIN(u, x, b[1], b[3], b[5], b[7], b[9], b[11]);
+        PROBE_CHAIN(v, y, b[0], b[2], b[4], b[6], b[8], b[10]);
+        PROBE_CHAIN(w, y, b[1], b[3], b[5], b[7], b[9], b[11]);
+#undef PROBE_CHAIN
         x = t[0] | 1u;
-        y = u[1] | 1u;
+        y = v[1] | 1u;
     }
     uint32_t acc = 0;
 #pragma unroll
-    for (int k = 0; k < 13; ++k) acc ^= t[k] ^ u[k];
+    for (int k = 0; k < 13; ++k) acc ^= t[k] ^ u[k] ^ v[k] ^ w[k];
     if (acc == 0x12345678u) sink[0] = acc;  // keeps the work observable
 }
 

@@ -85,24 +85,22 @@ __device__ __forceinline__ void from_stored(ext& P, const stored& Q) {
 // X3 = E F, Y3 = G H, T3 = E H, Z3 = F G.
 // Values that only feed multiplications are left unfolded (fq::add_nr / sub_nr):
 // Y1 -+ X1, y2 -+ x2, E, H < 4p; D < 4p; F, G < 6p; every product below 36 p^2.
+// Independent products go in pairs through fq::mul2 (four carry chains in flight).
 __device__ __forceinline__ void madd(ext& P, const stored& Q) {
-    fe A, B, t, u;
+    fe A, B, t, u, v, w;
     fq::sub_nr<2>(t, P.Y, P.X);
     fq::sub_nr<2>(u, Q.y, Q.x);
-    fq::mul(A, t, u);
-    fq::add_nr(t, P.Y, P.X);
-    fq::add_nr(u, Q.y, Q.x);
-    fq::mul(B, t, u);
+    fq::add_nr(v, P.Y, P.X);
+    fq::add_nr(w, Q.y, Q.x);
+    fq::mul2(A, t, u, B, v, w);
     fq::mul(t, P.T, Q.u);           // C
     fq::add_nr(u, P.Z, P.Z);        // D
     fq::sub_nr<2>(P.X, B, A);       // E
     fq::add_nr(P.Y, B, A);          // H
     fq::sub_nr<2>(A, u, t);         // F = D - C + 2p
     fq::add_nr(B, u, t);            // G
-    fq::mul(P.T, P.X, P.Y);         // T3 = E H
-    fq::mul(P.X, P.X, A);           // X3 = E F
-    fq::mul(P.Y, B, P.Y);           // Y3 = G H
-    fq::mul(P.Z, A, B);             // Z3 = F G
+    fq::mul2(P.T, P.X, P.Y, P.Z, A, B);  // T3 = E H, Z3 = F G
+    fq::mul2(P.X, P.X, A, P.Y, B, P.Y);  // X3 = E F, Y3 = G H
 }
 
 // P += Q with an identity flag kept by the caller (the first point of a run is
@@ -121,30 +119,26 @@ __device__ __forceinline__ void madd(ext& P, bool& p_inf, const stored& Q) {
 // A = (Y1 - X1)(Y2 - X2), B = (Y1 + X1)(Y2 + X2), C = T1 k T2, D = 2 Z1 Z2, then as madd.
 template <class QL>
 __device__ __forceinline__ void add_q(ext& P, const QL& q) {
-    fe A, B, t, u;
+    fe A, B, t, u, v;
     q.Y(u);
     q.X(t);
     fq::sub_nr<2>(A, u, t);
     fq::add_nr(B, u, t);
     fq::sub_nr<2>(t, P.Y, P.X);
-    fq::mul(A, t, A);
-    fq::add_nr(t, P.Y, P.X);
-    fq::mul(B, t, B);
+    fq::add_nr(v, P.Y, P.X);
+    fq::mul2(A, t, A, B, v, B);
     q.T(t);
     load_const(u, kK);
-    fq::mul(t, t, u);               // k T2
+    q.Z(v);
+    fq::mul2(t, t, u, u, P.Z, v);   // k T2, Z1 Z2
     fq::mul(t, P.T, t);             // C
-    q.Z(u);
-    fq::mul(u, P.Z, u);
     fq::add_nr(u, u, u);            // D
     fq::sub_nr<2>(P.X, B, A);       // E
     fq::add_nr(P.Y, B, A);          // H
     fq::sub_nr<2>(A, u, t);         // F
     fq::add_nr(B, u, t);            // G
-    fq::mul(P.T, P.X, P.Y);
-    fq::mul(P.X, P.X, A);
-    fq::mul(P.Y, B, P.Y);
-    fq::mul(P.Z, A, B);
+    fq::mul2(P.T, P.X, P.Y, P.Z, A, B);
+    fq::mul2(P.X, P.X, A, P.Y, B, P.Y);
 }
 
 struct RegQ {
@@ -162,12 +156,10 @@ __device__ __forceinline__ void add(ext& P, const ext& Q) { add_q(P, RegQ{&Q}); 
 // Unfolded: X + Y, 2 Z^2, G, H < 4p; E < 6p; F = G - 2 Z^2 + 4p < 8p; products below 48 p^2.
 __device__ __forceinline__ void dbl(ext& P) {
     fe A, B, C, t;
-    fq::sqr(A, P.X);
-    fq::sqr(B, P.Y);
-    fq::sqr(C, P.Z);
-    fq::add_nr(C, C, C);
     fq::add_nr(t, P.X, P.Y);
-    fq::sqr(t, t);
+    fq::mul2(A, P.X, P.X, B, P.Y, P.Y);
+    fq::mul2(C, P.Z, P.Z, t, t, t);
+    fq::add_nr(C, C, C);
     fq::sub_nr<2>(t, t, A);
     fq::sub_nr<2>(t, t, B);         // E
     fq::sub_nr<2>(P.Y, B, A);       // G = B - A
@@ -176,10 +168,8 @@ __device__ __forceinline__ void dbl(ext& P) {
     fq::sub_nr<2>(A, z, A);
     fq::sub_nr<2>(A, A, B);         // H = -A - B
     fq::sub_nr<4>(C, P.Y, C);       // F = G - C
-    fq::mul(P.T, t, A);             // E H
-    fq::mul(P.X, t, C);             // E F
-    fq::mul(P.Z, C, P.Y);           // F G
-    fq::mul(P.Y, P.Y, A);           // G H
+    fq::mul2(P.T, t, A, P.X, t, C);      // E H, E F
+    fq::mul2(P.Z, C, P.Y, P.Y, P.Y, A);  // F G, G H
 }
 
 // ---- four lanes per point operation (latency-bound chains; see ec::xchg4):

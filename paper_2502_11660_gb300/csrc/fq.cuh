@@ -2,10 +2,11 @@
 //
 // Elements are 12 little-endian 32-bit limbs in Montgomery form x*R mod p with
 // R = 2^384. Multiplication is word-serial Montgomery (CIOS): for each limb a_i
-// the row a_i*b is added with a mad.lo.cc / madc.hi.cc carry chain, then
-// m = -t_0 (because -p^-1 = 0xffffffff mod 2^32, p = 1 mod 2^46) and the row
-// m*p is added the same way, and the accumulator drops one word. Every chain of
-// one row sits in one asm statement so the carry flag never crosses statements.
+// the row a_i*b is added, then m = -t_0 (because -p^-1 = 0xffffffff mod 2^32,
+// p = 1 mod 2^46) and the row m*p is added, and the accumulator drops one word.
+// Each row runs as two independent mad.lo.cc / madc.hi.cc carry chains (the
+// products with the even- and with the odd-indexed limbs; see mul_inl). Every
+// chain sits in one asm statement so the carry flag never crosses statements.
 //
 // mul() is one out-of-line function. A point operation makes 10-14 calls; with
 // the body inlined at every call site the code of one point addition is about
@@ -20,8 +21,10 @@
 // All values kept in registers or memory by the curve code live in [0, 2p);
 // add/sub fold back into [0, 2p) with one masked correction of 2p, so every
 // product satisfies a*b < 4p^2 < p*R (R/p > 152). canon() maps [0, 2p) to [0, p).
-// Accumulator bound: with b < 2^383 the running value before each shift stays
-// below 2^416, so 13 words hold it and the final hi-chain carries are zero.
+// Accumulator bound: with a, b < 2p < 2^378 a row adds less than 2^411 to each
+// of the two chains, whose values stay below 2^380 after each shift and below
+// 2^412 before it, so 13 words hold them; the result, below 2p, fits the 12
+// words of e + 2^32 o.
 //
 // (A carry-save variant in the style of the paper's Sec. III-D -- 16 digits of
 // 24 bits, 64-bit mad.wide column sums, two coarse carry rounds -- was built and
@@ -76,73 +79,142 @@ __device__ __forceinline__ void set_one(fe& r) {
 }
 
 // r = a*b*R^-1 mod p, result in [0, 2p) when a*b < p*R. Inlined body.
-__device__ __forceinline__ void mul_inl(fe& r, const fe& a, const fe& bb) {
-    const uint32_t* b = bb.v;
-    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0, t9 = 0,
-             t10 = 0, t11 = 0, t12 = 0;
+// Word-serial Montgomery (one row per limb a_i: t += a_i b, m = -t_0, t += m p,
+// t >>= 32) with each row's partial products split into two independent carry
+// chains: the even-indexed limbs of the multiplicand accumulate in e (low half of
+// a_i b_j at e[j], high half at e[j + 1]) and the odd-indexed ones in o, held one
+// limb up (a_i b_j for odd j at o[j - 1], o[j]); so each chain is one run of
+// lo/hi multiply-adds of the same product, with no second pass for the high
+// halves (on GB300 this shape runs 1.4x faster than a low-half chain followed by
+// a high-half chain, in throughput and in latency). The running value is
+// e + 2^32 o, so the quotient digit is m = -e[0] (-p^-1 = -1 mod 2^32). m p is
+// split the same way; since p_0 = 1, the high half of m p_0 is zero, and that
+// slot of the even chain adds o[0] instead, after which both chains shift down
+// one limb and e + 2^32 o again has o one limb above e. After the 12 rows the
+// result is e + 2^32 o (one carry chain).
+struct MontAcc {
+    uint32_t e[13], o[13];
+};
+
+// One row: t += x b, m = -e[0], t += m p, shift (see mul_inl).
+__device__ __forceinline__ void mont_row(MontAcc& t, uint32_t x, const uint32_t* b) {
+    uint32_t* e = t.e;
+    uint32_t* o = t.o;
+    asm("mad.lo.cc.u32 %0, %13, %14, %0;\n\t"
+        "madc.hi.cc.u32 %1, %13, %14, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, %15, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, %15, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, %16, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, %16, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, %17, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, %17, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, %18, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, %18, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, %19, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, %19, %11;\n\t"
+        "addc.u32 %12, %12, 0;"
+        : "+r"(e[0]), "+r"(e[1]), "+r"(e[2]), "+r"(e[3]), "+r"(e[4]), "+r"(e[5]), "+r"(e[6]), "+r"(e[7]),
+          "+r"(e[8]), "+r"(e[9]), "+r"(e[10]), "+r"(e[11]), "+r"(e[12])
+        : "r"(x), "r"(b[0]), "r"(b[2]), "r"(b[4]), "r"(b[6]), "r"(b[8]), "r"(b[10]));
+    asm("mad.lo.cc.u32 %0, %13, %14, %0;\n\t"
+        "madc.hi.cc.u32 %1, %13, %14, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, %15, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, %15, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, %16, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, %16, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, %17, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, %17, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, %18, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, %18, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, %19, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, %19, %11;\n\t"
+        "addc.u32 %12, %12, 0;"
+        : "+r"(o[0]), "+r"(o[1]), "+r"(o[2]), "+r"(o[3]), "+r"(o[4]), "+r"(o[5]), "+r"(o[6]), "+r"(o[7]),
+          "+r"(o[8]), "+r"(o[9]), "+r"(o[10]), "+r"(o[11]), "+r"(o[12])
+        : "r"(x), "r"(b[1]), "r"(b[3]), "r"(b[5]), "r"(b[7]), "r"(b[9]), "r"(b[11]));
+    const uint32_t m = 0u - e[0];
+    asm("mad.lo.cc.u32 %0, %13, 0x8508c000, %0;\n\t"
+        "madc.hi.cc.u32 %1, %13, 0x8508c000, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, 0x170b5d44, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, 0x170b5d44, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, 0x1ef3622f, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, 0x1ef3622f, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, 0x1a22d9f3, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, 0x1a22d9f3, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, 0xc63b05c0, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, 0xc63b05c0, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, 0x01ae3a46, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, 0x01ae3a46, %11;\n\t"
+        "addc.u32 %12, %12, 0;"
+        : "+r"(o[0]), "+r"(o[1]), "+r"(o[2]), "+r"(o[3]), "+r"(o[4]), "+r"(o[5]), "+r"(o[6]), "+r"(o[7]),
+          "+r"(o[8]), "+r"(o[9]), "+r"(o[10]), "+r"(o[11]), "+r"(o[12])
+        : "r"(m));
+    asm("add.cc.u32 %0, %0, %14;\n\t"
+        "addc.cc.u32 %1, %1, %13;\n\t"
+        "madc.lo.cc.u32 %2, %14, 0x30000000, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, 0x30000000, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, 0xba094800, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, 0xba094800, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, 0x00f5138f, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, 0x00f5138f, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, 0x6ca1493b, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, 0x6ca1493b, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, 0x17c510ea, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, 0x17c510ea, %11;\n\t"
+        "addc.u32 %12, %12, 0;"
+        : "+r"(e[0]), "+r"(e[1]), "+r"(e[2]), "+r"(e[3]), "+r"(e[4]), "+r"(e[5]), "+r"(e[6]), "+r"(e[7]),
+          "+r"(e[8]), "+r"(e[9]), "+r"(e[10]), "+r"(e[11]), "+r"(e[12])
+        : "r"(o[0]), "r"(m));
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        e[k] = e[k + 1];
+        o[k] = o[k + 1];
+    }
+    e[12] = 0;
+    o[12] = 0;
+}
+
+// r = e + 2^32 o after the last row (the words from 12 up cancel).
+__device__ __forceinline__ void mont_final(fe& r, const MontAcc& t) {
+    const uint32_t* e = t.e;
+    const uint32_t* o = t.o;
+    r.v[0] = e[0];
+    asm("add.cc.u32 %0, %11, %22;\n\t"
+        "addc.cc.u32 %1, %12, %23;\n\t"
+        "addc.cc.u32 %2, %13, %24;\n\t"
+        "addc.cc.u32 %3, %14, %25;\n\t"
+        "addc.cc.u32 %4, %15, %26;\n\t"
+        "addc.cc.u32 %5, %16, %27;\n\t"
+        "addc.cc.u32 %6, %17, %28;\n\t"
+        "addc.cc.u32 %7, %18, %29;\n\t"
+        "addc.cc.u32 %8, %19, %30;\n\t"
+        "addc.cc.u32 %9, %20, %31;\n\t"
+        "addc.u32 %10, %21, %32;"
+        : "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]), "=r"(r.v[6]), "=r"(r.v[7]),
+          "=r"(r.v[8]), "=r"(r.v[9]), "=r"(r.v[10]), "=r"(r.v[11])
+        : "r"(e[1]), "r"(e[2]), "r"(e[3]), "r"(e[4]), "r"(e[5]), "r"(e[6]), "r"(e[7]), "r"(e[8]), "r"(e[9]),
+          "r"(e[10]), "r"(e[11]), "r"(o[0]), "r"(o[1]), "r"(o[2]), "r"(o[3]), "r"(o[4]), "r"(o[5]), "r"(o[6]),
+          "r"(o[7]), "r"(o[8]), "r"(o[9]), "r"(o[10]));
+}
+
+__device__ __forceinline__ void mul_inl(fe& r, const fe& a, const fe& b) {
+    MontAcc t = {};
+#pragma unroll
+    for (int i = 0; i < N; ++i) mont_row(t, a.v[i], b.v);
+    mont_final(r, t);
+}
+
+// Two independent products with their rows interleaved: four independent carry
+// chains in flight instead of two.
+__device__ __forceinline__ void mul2_inl(fe& r1, const fe& a1, const fe& b1, fe& r2, const fe& a2, const fe& b2) {
+    MontAcc t1 = {}, t2 = {};
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        asm(
-        "mad.lo.cc.u32 %0, %13, %14, %0;\n\t"
-        "madc.lo.cc.u32 %1, %13, %15, %1;\n\t"
-        "madc.lo.cc.u32 %2, %13, %16, %2;\n\t"
-        "madc.lo.cc.u32 %3, %13, %17, %3;\n\t"
-        "madc.lo.cc.u32 %4, %13, %18, %4;\n\t"
-        "madc.lo.cc.u32 %5, %13, %19, %5;\n\t"
-        "madc.lo.cc.u32 %6, %13, %20, %6;\n\t"
-        "madc.lo.cc.u32 %7, %13, %21, %7;\n\t"
-        "madc.lo.cc.u32 %8, %13, %22, %8;\n\t"
-        "madc.lo.cc.u32 %9, %13, %23, %9;\n\t"
-        "madc.lo.cc.u32 %10, %13, %24, %10;\n\t"
-        "madc.lo.cc.u32 %11, %13, %25, %11;\n\t"
-        "addc.u32 %12, %12, 0;\n\t"
-        "mad.hi.cc.u32 %1, %13, %14, %1;\n\t"
-        "madc.hi.cc.u32 %2, %13, %15, %2;\n\t"
-        "madc.hi.cc.u32 %3, %13, %16, %3;\n\t"
-        "madc.hi.cc.u32 %4, %13, %17, %4;\n\t"
-        "madc.hi.cc.u32 %5, %13, %18, %5;\n\t"
-        "madc.hi.cc.u32 %6, %13, %19, %6;\n\t"
-        "madc.hi.cc.u32 %7, %13, %20, %7;\n\t"
-        "madc.hi.cc.u32 %8, %13, %21, %8;\n\t"
-        "madc.hi.cc.u32 %9, %13, %22, %9;\n\t"
-        "madc.hi.cc.u32 %10, %13, %23, %10;\n\t"
-        "madc.hi.cc.u32 %11, %13, %24, %11;\n\t"
-        "madc.hi.u32 %12, %13, %25, %12;"
-            : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9), "+r"(t10), "+r"(t11), "+r"(t12)
-            : "r"(a.v[i]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
-        uint32_t m = 0u - t0;
-        asm(
-        "add.cc.u32 %0, %0, %13;\n\t"
-        "madc.lo.cc.u32 %1, %13, 0x8508c000, %1;\n\t"
-        "madc.lo.cc.u32 %2, %13, 0x30000000, %2;\n\t"
-        "madc.lo.cc.u32 %3, %13, 0x170b5d44, %3;\n\t"
-        "madc.lo.cc.u32 %4, %13, 0xba094800, %4;\n\t"
-        "madc.lo.cc.u32 %5, %13, 0x1ef3622f, %5;\n\t"
-        "madc.lo.cc.u32 %6, %13, 0x00f5138f, %6;\n\t"
-        "madc.lo.cc.u32 %7, %13, 0x1a22d9f3, %7;\n\t"
-        "madc.lo.cc.u32 %8, %13, 0x6ca1493b, %8;\n\t"
-        "madc.lo.cc.u32 %9, %13, 0xc63b05c0, %9;\n\t"
-        "madc.lo.cc.u32 %10, %13, 0x17c510ea, %10;\n\t"
-        "madc.lo.cc.u32 %11, %13, 0x01ae3a46, %11;\n\t"
-        "addc.u32 %12, %12, 0;\n\t"
-        "mad.hi.cc.u32 %2, %13, 0x8508c000, %2;\n\t"
-        "madc.hi.cc.u32 %3, %13, 0x30000000, %3;\n\t"
-        "madc.hi.cc.u32 %4, %13, 0x170b5d44, %4;\n\t"
-        "madc.hi.cc.u32 %5, %13, 0xba094800, %5;\n\t"
-        "madc.hi.cc.u32 %6, %13, 0x1ef3622f, %6;\n\t"
-        "madc.hi.cc.u32 %7, %13, 0x00f5138f, %7;\n\t"
-        "madc.hi.cc.u32 %8, %13, 0x1a22d9f3, %8;\n\t"
-        "madc.hi.cc.u32 %9, %13, 0x6ca1493b, %9;\n\t"
-        "madc.hi.cc.u32 %10, %13, 0xc63b05c0, %10;\n\t"
-        "madc.hi.cc.u32 %11, %13, 0x17c510ea, %11;\n\t"
-        "madc.hi.u32 %12, %13, 0x01ae3a46, %12;"
-            : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9), "+r"(t10), "+r"(t11), "+r"(t12)
-            : "r"(m));
-        t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8; t8 = t9;
-        t9 = t10; t10 = t11; t11 = t12; t12 = 0;
+        mont_row(t1, a1.v[i], b1.v);
+        mont_row(t2, a2.v[i], b2.v);
     }
-    r.v[0] = t0; r.v[1] = t1; r.v[2] = t2; r.v[3] = t3; r.v[4] = t4; r.v[5] = t5;
-    r.v[6] = t6; r.v[7] = t7; r.v[8] = t8; r.v[9] = t9; r.v[10] = t10; r.v[11] = t11;
+    mont_final(r1, t1);
+    mont_final(r2, t2);
 }
 
 // Out-of-line multiplication used by the point arithmetic (one copy of the code).
@@ -154,6 +226,21 @@ static __device__ __noinline__ fe mul_v(fe a, fe b) {
     return r;
 }
 __device__ __forceinline__ void mul(fe& r, const fe& a, const fe& b) { r = mul_v(a, b); }
+
+struct fe2 {
+    fe a, b;
+};
+static __device__ __noinline__ fe2 mul2_v(fe a1, fe b1, fe a2, fe b2) {
+    fe2 r;
+    mul2_inl(r.a, a1, b1, r.b, a2, b2);
+    return r;
+}
+// r1 = a1 b1, r2 = a2 b2 (R^-1 mod p each) in one call.
+__device__ __forceinline__ void mul2(fe& r1, const fe& a1, const fe& b1, fe& r2, const fe& a2, const fe& b2) {
+    const fe2 r = mul2_v(a1, b1, a2, b2);
+    r1 = r.a;
+    r2 = r.b;
+}
 
 __device__ __forceinline__ void sqr(fe& r, const fe& a) { mul(r, a, a); }
 

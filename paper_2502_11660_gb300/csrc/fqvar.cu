@@ -13,9 +13,13 @@
 //  * CARRYSAVE -- Montgomery on 16 digits of 24 bits in 32-bit registers, 64-bit
 //                 column sums and two rounds of coarse carry propagation (the
 //                 element format of Sec. III-B / III-D carried to the GPU).
+//  * CIOS_TWOPASS -- the library's word-serial Montgomery product with each row
+//                 as one chain of low halves followed by one chain of high halves
+//                 (the library's multiplication runs each row as two independent
+//                 chains of adjacent low/high halves instead).
 //
 // Every variant reads 12 x 32-bit limbs in structure-of-arrays layout and writes the
-// canonical result in [0, p), so all four are bit-comparable.
+// canonical result in [0, p), so all five are bit-comparable.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -312,6 +316,78 @@ __device__ __forceinline__ void mul_carrysave(uint32_t* r, const uint32_t* aw, c
     for (int k = 0; k < N; ++k) r[k] = w[k];
 }
 
+// CIOS with one low-half chain and one high-half chain per row (the form the
+// library used before its even/odd chains): same quotient digits, same lazy result
+// in [0, 2p).
+__device__ __forceinline__ void mul_cios_twopass(fe& r, const fe& a, const fe& bb) {
+    const uint32_t* b = bb.v;
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0, t4 = 0, t5 = 0, t6 = 0, t7 = 0, t8 = 0, t9 = 0,
+             t10 = 0, t11 = 0, t12 = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        asm(
+        "mad.lo.cc.u32 %0, %13, %14, %0;\n\t"
+        "madc.lo.cc.u32 %1, %13, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, %16, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, %17, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, %18, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, %19, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, %20, %6;\n\t"
+        "madc.lo.cc.u32 %7, %13, %21, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, %22, %8;\n\t"
+        "madc.lo.cc.u32 %9, %13, %23, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, %24, %10;\n\t"
+        "madc.lo.cc.u32 %11, %13, %25, %11;\n\t"
+        "addc.u32 %12, %12, 0;\n\t"
+        "mad.hi.cc.u32 %1, %13, %14, %1;\n\t"
+        "madc.hi.cc.u32 %2, %13, %15, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, %16, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, %18, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, %19, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, %20, %7;\n\t"
+        "madc.hi.cc.u32 %8, %13, %21, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, %22, %9;\n\t"
+        "madc.hi.cc.u32 %10, %13, %23, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, %24, %11;\n\t"
+        "madc.hi.u32 %12, %13, %25, %12;"
+            : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9), "+r"(t10), "+r"(t11), "+r"(t12)
+            : "r"(a.v[i]), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]), "r"(b[9]), "r"(b[10]), "r"(b[11]));
+        uint32_t m = 0u - t0;
+        asm(
+        "add.cc.u32 %0, %0, %13;\n\t"
+        "madc.lo.cc.u32 %1, %13, 0x8508c000, %1;\n\t"
+        "madc.lo.cc.u32 %2, %13, 0x30000000, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, 0x170b5d44, %3;\n\t"
+        "madc.lo.cc.u32 %4, %13, 0xba094800, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, 0x1ef3622f, %5;\n\t"
+        "madc.lo.cc.u32 %6, %13, 0x00f5138f, %6;\n\t"
+        "madc.lo.cc.u32 %7, %13, 0x1a22d9f3, %7;\n\t"
+        "madc.lo.cc.u32 %8, %13, 0x6ca1493b, %8;\n\t"
+        "madc.lo.cc.u32 %9, %13, 0xc63b05c0, %9;\n\t"
+        "madc.lo.cc.u32 %10, %13, 0x17c510ea, %10;\n\t"
+        "madc.lo.cc.u32 %11, %13, 0x01ae3a46, %11;\n\t"
+        "addc.u32 %12, %12, 0;\n\t"
+        "mad.hi.cc.u32 %2, %13, 0x8508c000, %2;\n\t"
+        "madc.hi.cc.u32 %3, %13, 0x30000000, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, 0x170b5d44, %4;\n\t"
+        "madc.hi.cc.u32 %5, %13, 0xba094800, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, 0x1ef3622f, %6;\n\t"
+        "madc.hi.cc.u32 %7, %13, 0x00f5138f, %7;\n\t"
+        "madc.hi.cc.u32 %8, %13, 0x1a22d9f3, %8;\n\t"
+        "madc.hi.cc.u32 %9, %13, 0x6ca1493b, %9;\n\t"
+        "madc.hi.cc.u32 %10, %13, 0xc63b05c0, %10;\n\t"
+        "madc.hi.cc.u32 %11, %13, 0x17c510ea, %11;\n\t"
+        "madc.hi.u32 %12, %13, 0x01ae3a46, %12;"
+            : "+r"(t0), "+r"(t1), "+r"(t2), "+r"(t3), "+r"(t4), "+r"(t5), "+r"(t6), "+r"(t7), "+r"(t8), "+r"(t9), "+r"(t10), "+r"(t11), "+r"(t12)
+            : "r"(m));
+        t0 = t1; t1 = t2; t2 = t3; t3 = t4; t4 = t5; t5 = t6; t6 = t7; t7 = t8; t8 = t9;
+        t9 = t10; t10 = t11; t11 = t12; t12 = 0;
+    }
+    r.v[0] = t0; r.v[1] = t1; r.v[2] = t2; r.v[3] = t3; r.v[4] = t4; r.v[5] = t5;
+    r.v[6] = t6; r.v[7] = t7; r.v[8] = t8; r.v[9] = t9; r.v[10] = t10; r.v[11] = t11;
+}
+
 // ---------------------------------------------------------------- kernel
 
 template <int V>
@@ -335,6 +411,17 @@ __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t*
             fq::canon(fr, fr);
 #pragma unroll
             for (int k = 0; k < N; ++k) r[k] = fr.v[k];
+        } else if (V == MSM377_FQMUL_CIOS_TWOPASS) {
+            fe fa, fb, fr;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                fa.v[k] = x[k];
+                fb.v[k] = y[k];
+            }
+            mul_cios_twopass(fr, fa, fb);
+            fq::canon(fr, fr);
+#pragma unroll
+            for (int k = 0; k < N; ++k) r[k] = fr.v[k];
         } else if (V == MSM377_FQMUL_BARRETT) {
             mul_barrett(r, x, y);
         } else if (V == MSM377_FQMUL_KARATSUBA) {
@@ -353,7 +440,7 @@ using namespace msm377;
 
 extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n, int variant,
                                     void* stream) {
-    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_CARRYSAVE)
+    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_CIOS_TWOPASS)
         return set_error(MSM377_EINVAL, "fq_mul_batch_variant: unknown variant %d", variant);
     if (n == 0) return MSM377_OK;
     if (!a || !b || !out) return set_error(MSM377_EINVAL, "fq_mul_batch_variant: NULL pointer");
@@ -374,8 +461,11 @@ extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32
         case MSM377_FQMUL_KARATSUBA:
             k_fq_mul_variant<MSM377_FQMUL_KARATSUBA><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
             break;
-        default:
+        case MSM377_FQMUL_CARRYSAVE:
             k_fq_mul_variant<MSM377_FQMUL_CARRYSAVE><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        default:
+            k_fq_mul_variant<MSM377_FQMUL_CIOS_TWOPASS><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
     }
     note_launches(1);
     return check_launch("fq_mul_batch_variant");

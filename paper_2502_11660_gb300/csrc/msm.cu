@@ -1058,7 +1058,7 @@ __global__ void k_merge_final(AccArgs a) {
 
 // Thread (wi, g): Y = sum_{i=1..L} B[gL+i], V = sum_{i=1..L} i * B[gL+i] (bucket b at index b-1).
 template <class M>
-__global__ void __launch_bounds__(128, 4) k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, int w0, int nwin,
+__global__ void __launch_bounds__(128) k_reduce_segments(const uint4* __restrict__ buckets, uint32_t Bp, uint32_t L, int w0, int nwin,
                                   uint32_t G, uint4* __restrict__ Y, uint4* __restrict__ V) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)nwin * G) return;

@@ -1,7 +1,8 @@
 """GPU parity of the alternative multiplications (fq_mul_batch_variant) vs Python
 integers: the paper's Barrett reduction (Sec. III-C; also checked against the
 oracle's own Barrett), the Karatsuba-top Montgomery product and the carry-save
-radix-2^24 Montgomery product, all bit-exact and canonical."""
+radix-2^24 Montgomery product and the two-pass-row CIOS product, all
+bit-exact and canonical."""
 import random
 
 import pytest
@@ -21,6 +22,7 @@ VARIANTS = {
     "barrett": (1, lambda x, y: x * y % fq.P),
     "karatsuba": (2, lambda x, y: x * y * RINV % fq.P),
     "carrysave": (3, lambda x, y: x * y * RINV % fq.P),
+    "cios_twopass": (4, lambda x, y: x * y * RINV % fq.P),
 }
 
 
