@@ -86,26 +86,22 @@ __device__ __forceinline__ void mdbl(xyzz& R, const affine& Q) {
 // P = 2 P: U = 2Y, V = U^2, W = U V, S = X V, M = 3X^2,
 // X3 = M^2 - 2S, Y3 = M (S - X3) - W Y, ZZ3 = V ZZ, ZZZ3 = W ZZZ.
 // Y = 0 gives V = 0 and so ZZ3 = 0 (the identity) without a branch.
-// Temporaries die as early as possible (register pressure).
+// Independent products go in pairs through fq::mul2 (four carry chains in flight).
 __device__ __forceinline__ void dbl(xyzz& P) {
     if (is_inf(P)) return;
-    fe V, W, t;
-    fq::dbl(t, P.Y);                // U
-    fq::sqr(V, t);
-    fq::mul(W, t, V);               // U dead
-    fq::mul(P.ZZ, P.ZZ, V);         // ZZ3
-    fq::mul(P.ZZZ, P.ZZZ, W);       // ZZZ3
-    fq::mul(P.Y, W, P.Y);           // W Y; W dead
-    fq::mul(V, P.X, V);             // S in V's slot
-    fq::sqr(t, P.X);
-    fq::dbl(W, t);
-    fq::add(W, W, t);               // M in W's slot
-    fq::dbl(t, V);                  // 2S
-    fq::sqr(P.X, W);
-    fq::sub(P.X, P.X, t);           // X3
-    fq::sub(t, V, P.X);             // S - X3
-    fq::mul(t, W, t);
-    fq::sub(P.Y, t, P.Y);           // Y3
+    fe U, V, W, M, t;
+    fq::dbl(U, P.Y);
+    fq::mul2(V, U, U, t, P.X, P.X);          // V = U^2, X^2
+    fq::dbl(M, t);
+    fq::add(M, M, t);                        // M = 3 X^2
+    fq::mul2(W, U, V, U, P.X, V);            // W = U V, S = X V (in U's slot)
+    fq::mul2(P.ZZ, P.ZZ, V, t, M, M);        // ZZ3 = ZZ V, M^2
+    fq::mul2(P.ZZZ, P.ZZZ, W, P.Y, W, P.Y);  // ZZZ3 = ZZZ W, W Y
+    fq::dbl(V, U);                           // 2S
+    fq::sub(P.X, t, V);                      // X3
+    fq::sub(t, U, P.X);                      // S - X3
+    fq::mul(t, M, t);
+    fq::sub(P.Y, t, P.Y);                    // Y3
 }
 
 // P += Q (Q affine). `p_inf` says P is the identity (kept by the caller).
@@ -120,8 +116,7 @@ __device__ __forceinline__ void madd(xyzz& P, bool& p_inf, const affine& Q) {
         return;
     }
     fe U2, S2, Pd, R;
-    fq::mul(U2, Q.x, P.ZZ);
-    fq::mul(S2, Q.y, P.ZZZ);
+    fq::mul2(U2, Q.x, P.ZZ, S2, Q.y, P.ZZZ);
     fq::sub(Pd, U2, P.X);
     fq::sub(R, S2, P.Y);
     if (fq::is_zero(Pd)) {
@@ -135,18 +130,14 @@ __device__ __forceinline__ void madd(xyzz& P, bool& p_inf, const affine& Q) {
         return;
     }
     fe PP, PPP, Q1, t;
-    fq::sqr(PP, Pd);
-    fq::mul(PPP, Pd, PP);
-    fq::mul(Q1, P.X, PP);
-    fq::mul(P.ZZ, P.ZZ, PP);
-    fq::mul(P.ZZZ, P.ZZZ, PPP);
-    fq::sqr(P.X, R);
-    fq::sub(P.X, P.X, PPP);
+    fq::mul2(PP, Pd, Pd, t, R, R);              // PP, R^2
+    fq::mul2(PPP, Pd, PP, Q1, P.X, PP);
+    fq::mul2(P.ZZ, P.ZZ, PP, P.ZZZ, P.ZZZ, PPP);
+    fq::sub(P.X, t, PPP);
     fq::dbl(t, Q1);
     fq::sub(P.X, P.X, t);       // X3
-    fq::mul(PPP, P.Y, PPP);     // Y1 PPP
     fq::sub(t, Q1, P.X);
-    fq::mul(t, R, t);
+    fq::mul2(PPP, P.Y, PPP, t, R, t);           // Y1 PPP, R (Q1 - X3)
     fq::sub(P.Y, t, PPP);
 }
 
