@@ -615,7 +615,7 @@ def batch_ops(pkg, torch, dev, stream):
     variants = {}
     for name, v in (("cios", pkg.FQMUL_CIOS), ("barrett", pkg.FQMUL_BARRETT),
                     ("karatsuba", pkg.FQMUL_KARATSUBA), ("carrysave", pkg.FQMUL_CARRYSAVE),
-                    ("cios_twopass", pkg.FQMUL_CIOS_TWOPASS)):
+                    ("cios_twopass", pkg.FQMUL_CIOS_TWOPASS), ("cios_doublerow", pkg.FQMUL_CIOS_DOUBLEROW)):
         ms_v = timed(lambda v=v: pkg.fq_mul_batch_variant(mA, mB, v, out=out))
         variants[name] = {"ms_2^24": ms_v, "mul_per_s": n / (ms_v / 1e3)}
     del mA, mB, out

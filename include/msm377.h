@@ -84,12 +84,15 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
  *                          high halves (the library's multiplication runs each
  *                          row as two independent chains of adjacent low/high
  *                          halves of the even- and odd-indexed limbs' products)
+ *   MSM377_FQMUL_CIOS_DOUBLEROW a b 2^-384 mod p, the same product two rows and two
+ *                          quotient digits per step (accumulators shift two limbs)
  * MSM377_EINVAL for another variant. */
 #define MSM377_FQMUL_CIOS 0
 #define MSM377_FQMUL_BARRETT 1
 #define MSM377_FQMUL_KARATSUBA 2
 #define MSM377_FQMUL_CARRYSAVE 3
 #define MSM377_FQMUL_CIOS_TWOPASS 4
+#define MSM377_FQMUL_CIOS_DOUBLEROW 5
 int fq_mul_batch_variant(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, int variant,
                          void *stream);
 

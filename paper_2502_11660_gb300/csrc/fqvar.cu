@@ -13,6 +13,8 @@
 //  * CARRYSAVE -- Montgomery on 16 digits of 24 bits in 32-bit registers, 64-bit
 //                 column sums and two rounds of coarse carry propagation (the
 //                 element format of Sec. III-B / III-D carried to the GPU).
+//  * CIOS_DOUBLEROW -- the same product two rows and two quotient digits per step,
+//                 accumulators shifted by two limbs (mul_doublerow).
 //  * CIOS_TWOPASS -- the library's word-serial Montgomery product with each row
 //                 as one chain of low halves followed by one chain of high halves
 //                 (the library's multiplication runs each row as two independent
@@ -388,6 +390,226 @@ __device__ __forceinline__ void mul_cios_twopass(fe& r, const fe& a, const fe& b
     r.v[6] = t6; r.v[7] = t7; r.v[8] = t8; r.v[9] = t9; r.v[10] = t10; r.v[11] = t11;
 }
 
+// ---- CIOS_DOUBLEROW: two rows and two quotient digits per step, accumulators
+// shifted by two limbs, so the register pair holding the low and high half of one
+// partial product keeps its alignment from step to step (bare product chains that
+// shift two limbs per row run 1.3x faster than chains that shift one; the whole
+// multiplication, with its extra carry words and the merge chain below, does not).
+//
+// The running value is E + 2^32 O: E[k] at limb k holds the partial products that
+// start at an even limb (a low half at 2j, its high half at 2j + 1), O[k] at limb
+// k + 1 those that start at an odd limb. One step, for x0 = a_2s, x1 = a_2s+1:
+//   E += x0 b_even,  O += x0 b_odd,  O += x1 b_even,  E += 2^64 x1 b_odd (E[2..]),
+//   m0 = -E[0];  O += m0 p_odd;  E += m0 p_even, where p_0 = 1 leaves the high
+//   half of m0 p_0 zero and that slot adds O[0] (so limb 1 is held by E alone);
+//   m1 = -E[1];  E += 2^32 m1 (at limb 1) + 2^64 m1 p_odd (E[2..]);
+//   O += m1 p_even without its p_0 term (O[2..], limbs 3 up);
+//   then O[1] (limb 2) and the carry of limb 1 move into E, E[0] = E[1] = 0, and
+//   both accumulators drop two limbs.
+// The quotient digits are those of the word-serial form (the pair (m0, m1) is the
+// two-limb digit -t p^-1 mod 2^64), so the lazy result in [0, 2p) is the same.
+// Bounds: E stays below 2^444 and O below 2^413 within a step, so E[0..13] and
+// O[0..13] hold them and the top carries are zero.
+struct MontAcc2 {
+    uint32_t e[14], o[14];
+};
+
+__device__ __forceinline__ void mont_step2(MontAcc2& t, uint32_t x0, uint32_t x1, const uint32_t* b) {
+    uint32_t* E = t.e;
+    uint32_t* O = t.o;
+    // E[0..11] += x0 b_even, carry into E[12..13]
+    asm("mad.lo.cc.u32 %0, %14, %15, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, %16, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, %16, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, %18, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, %18, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, %19, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, %19, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, %20, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, %20, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(E[0]), "+r"(E[1]), "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]),
+          "+r"(E[8]), "+r"(E[9]), "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(x0), "r"(b[0]), "r"(b[2]), "r"(b[4]), "r"(b[6]), "r"(b[8]), "r"(b[10]));
+    // O[0..11] += x0 b_odd, carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %14, %15, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, %16, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, %16, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, %18, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, %18, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, %19, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, %19, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, %20, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, %20, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(O[0]), "+r"(O[1]), "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]),
+          "+r"(O[8]), "+r"(O[9]), "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(x0), "r"(b[1]), "r"(b[3]), "r"(b[5]), "r"(b[7]), "r"(b[9]), "r"(b[11]));
+    // O[0..11] += x1 b_even (limbs 1..12), carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %14, %15, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, %16, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, %16, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, %18, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, %18, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, %19, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, %19, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, %20, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, %20, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(O[0]), "+r"(O[1]), "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]),
+          "+r"(O[8]), "+r"(O[9]), "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(x1), "r"(b[0]), "r"(b[2]), "r"(b[4]), "r"(b[6]), "r"(b[8]), "r"(b[10]));
+    // E[2..13] += x1 b_odd (limbs 2..13); no carry leaves E[13]
+    asm("mad.lo.cc.u32 %0, %12, %13, %0;\n\t"
+        "madc.hi.cc.u32 %1, %12, %13, %1;\n\t"
+        "madc.lo.cc.u32 %2, %12, %14, %2;\n\t"
+        "madc.hi.cc.u32 %3, %12, %14, %3;\n\t"
+        "madc.lo.cc.u32 %4, %12, %15, %4;\n\t"
+        "madc.hi.cc.u32 %5, %12, %15, %5;\n\t"
+        "madc.lo.cc.u32 %6, %12, %16, %6;\n\t"
+        "madc.hi.cc.u32 %7, %12, %16, %7;\n\t"
+        "madc.lo.cc.u32 %8, %12, %17, %8;\n\t"
+        "madc.hi.cc.u32 %9, %12, %17, %9;\n\t"
+        "madc.lo.cc.u32 %10, %12, %18, %10;\n\t"
+        "madc.hi.u32 %11, %12, %18, %11;"
+        : "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]), "+r"(E[8]), "+r"(E[9]),
+          "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(x1), "r"(b[1]), "r"(b[3]), "r"(b[5]), "r"(b[7]), "r"(b[9]), "r"(b[11]));
+    const uint32_t m0 = 0u - E[0];
+    // O[0..11] += m0 p_odd (limbs 1..12), carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %14, 0x8508c000, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, 0x8508c000, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, 0x170b5d44, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, 0x170b5d44, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, 0x1ef3622f, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, 0x1ef3622f, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, 0x1a22d9f3, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, 0x1a22d9f3, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, 0xc63b05c0, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, 0xc63b05c0, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, 0x01ae3a46, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, 0x01ae3a46, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(O[0]), "+r"(O[1]), "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]),
+          "+r"(O[8]), "+r"(O[9]), "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(m0));
+    // E[0..11] += m0 p_even: limb 0 takes m0 (p_0 = 1), limb 1 takes O[0] in the
+    // zero high half of m0 p_0; carry into E[12..13]
+    asm("add.cc.u32 %0, %0, %15;\n\t"
+        "addc.cc.u32 %1, %1, %14;\n\t"
+        "madc.lo.cc.u32 %2, %15, 0x30000000, %2;\n\t"
+        "madc.hi.cc.u32 %3, %15, 0x30000000, %3;\n\t"
+        "madc.lo.cc.u32 %4, %15, 0xba094800, %4;\n\t"
+        "madc.hi.cc.u32 %5, %15, 0xba094800, %5;\n\t"
+        "madc.lo.cc.u32 %6, %15, 0x00f5138f, %6;\n\t"
+        "madc.hi.cc.u32 %7, %15, 0x00f5138f, %7;\n\t"
+        "madc.lo.cc.u32 %8, %15, 0x6ca1493b, %8;\n\t"
+        "madc.hi.cc.u32 %9, %15, 0x6ca1493b, %9;\n\t"
+        "madc.lo.cc.u32 %10, %15, 0x17c510ea, %10;\n\t"
+        "madc.hi.cc.u32 %11, %15, 0x17c510ea, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(E[0]), "+r"(E[1]), "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]),
+          "+r"(E[8]), "+r"(E[9]), "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(O[0]), "r"(m0));
+    const uint32_t m1 = 0u - E[1];
+    // E[1..13] += m1 (limb 1, p_0 = 1) + 2^64 m1 p_odd (limbs 2..13): E[1] becomes 0
+    asm("add.cc.u32 %0, %0, %13;\n\t"
+        "madc.lo.cc.u32 %1, %13, 0x8508c000, %1;\n\t"
+        "madc.hi.cc.u32 %2, %13, 0x8508c000, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, 0x170b5d44, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, 0x170b5d44, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, 0x1ef3622f, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, 0x1ef3622f, %6;\n\t"
+        "madc.lo.cc.u32 %7, %13, 0x1a22d9f3, %7;\n\t"
+        "madc.hi.cc.u32 %8, %13, 0x1a22d9f3, %8;\n\t"
+        "madc.lo.cc.u32 %9, %13, 0xc63b05c0, %9;\n\t"
+        "madc.hi.cc.u32 %10, %13, 0xc63b05c0, %10;\n\t"
+        "madc.lo.cc.u32 %11, %13, 0x01ae3a46, %11;\n\t"
+        "madc.hi.u32 %12, %13, 0x01ae3a46, %12;"
+        : "+r"(E[1]), "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]), "+r"(E[8]),
+          "+r"(E[9]), "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(m1));
+    // O[2..11] += m1 (p_2 .. p_10) at limbs 3..12, carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %12, 0x30000000, %0;\n\t"
+        "madc.hi.cc.u32 %1, %12, 0x30000000, %1;\n\t"
+        "madc.lo.cc.u32 %2, %12, 0xba094800, %2;\n\t"
+        "madc.hi.cc.u32 %3, %12, 0xba094800, %3;\n\t"
+        "madc.lo.cc.u32 %4, %12, 0x00f5138f, %4;\n\t"
+        "madc.hi.cc.u32 %5, %12, 0x00f5138f, %5;\n\t"
+        "madc.lo.cc.u32 %6, %12, 0x6ca1493b, %6;\n\t"
+        "madc.hi.cc.u32 %7, %12, 0x6ca1493b, %7;\n\t"
+        "madc.lo.cc.u32 %8, %12, 0x17c510ea, %8;\n\t"
+        "madc.hi.cc.u32 %9, %12, 0x17c510ea, %9;\n\t"
+        "addc.cc.u32 %10, %10, 0;\n\t"
+        "addc.u32 %11, %11, 0;"
+        : "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]), "+r"(O[8]), "+r"(O[9]),
+          "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(m1));
+    // limb 1 is zero overall (E[1] = 0 now; O[0] was added into it); O[1] (limb 2)
+    // moves into E[2] with the carry up E
+    asm("add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.cc.u32 %3, %3, 0;\n\t"
+        "addc.cc.u32 %4, %4, 0;\n\t"
+        "addc.cc.u32 %5, %5, 0;\n\t"
+        "addc.cc.u32 %6, %6, 0;\n\t"
+        "addc.cc.u32 %7, %7, 0;\n\t"
+        "addc.cc.u32 %8, %8, 0;\n\t"
+        "addc.cc.u32 %9, %9, 0;\n\t"
+        "addc.cc.u32 %10, %10, 0;\n\t"
+        "addc.u32 %11, %11, 0;"
+        : "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]), "+r"(E[8]), "+r"(E[9]),
+          "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(O[1]));
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        E[k] = E[k + 2];
+        O[k] = O[k + 2];
+    }
+    E[12] = E[13] = 0;
+    O[12] = O[13] = 0;
+}
+
+__device__ __forceinline__ void mul_doublerow(fe& r, const fe& a, const fe& b) {
+    MontAcc2 t = {};
+#pragma unroll
+    for (int i = 0; i < N; i += 2) mont_step2(t, a.v[i], a.v[i + 1], b.v);
+    const uint32_t* e = t.e;
+    const uint32_t* o = t.o;
+    r.v[0] = e[0];
+    asm("add.cc.u32 %0, %11, %22;\n\t"
+        "addc.cc.u32 %1, %12, %23;\n\t"
+        "addc.cc.u32 %2, %13, %24;\n\t"
+        "addc.cc.u32 %3, %14, %25;\n\t"
+        "addc.cc.u32 %4, %15, %26;\n\t"
+        "addc.cc.u32 %5, %16, %27;\n\t"
+        "addc.cc.u32 %6, %17, %28;\n\t"
+        "addc.cc.u32 %7, %18, %29;\n\t"
+        "addc.cc.u32 %8, %19, %30;\n\t"
+        "addc.cc.u32 %9, %20, %31;\n\t"
+        "addc.u32 %10, %21, %32;"
+        : "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]), "=r"(r.v[6]), "=r"(r.v[7]),
+          "=r"(r.v[8]), "=r"(r.v[9]), "=r"(r.v[10]), "=r"(r.v[11])
+        : "r"(e[1]), "r"(e[2]), "r"(e[3]), "r"(e[4]), "r"(e[5]), "r"(e[6]), "r"(e[7]), "r"(e[8]), "r"(e[9]),
+          "r"(e[10]), "r"(e[11]), "r"(o[0]), "r"(o[1]), "r"(o[2]), "r"(o[3]), "r"(o[4]), "r"(o[5]), "r"(o[6]),
+          "r"(o[7]), "r"(o[8]), "r"(o[9]), "r"(o[10]));
+}
+
 // ---------------------------------------------------------------- kernel
 
 template <int V>
@@ -408,6 +630,17 @@ __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t*
                 fb.v[k] = y[k];
             }
             fq::mul_inl(fr, fa, fb);
+            fq::canon(fr, fr);
+#pragma unroll
+            for (int k = 0; k < N; ++k) r[k] = fr.v[k];
+        } else if (V == MSM377_FQMUL_CIOS_DOUBLEROW) {
+            fe fa, fb, fr;
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                fa.v[k] = x[k];
+                fb.v[k] = y[k];
+            }
+            mul_doublerow(fr, fa, fb);
             fq::canon(fr, fr);
 #pragma unroll
             for (int k = 0; k < N; ++k) r[k] = fr.v[k];
@@ -440,7 +673,7 @@ using namespace msm377;
 
 extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n, int variant,
                                     void* stream) {
-    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_CIOS_TWOPASS)
+    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_CIOS_DOUBLEROW)
         return set_error(MSM377_EINVAL, "fq_mul_batch_variant: unknown variant %d", variant);
     if (n == 0) return MSM377_OK;
     if (!a || !b || !out) return set_error(MSM377_EINVAL, "fq_mul_batch_variant: NULL pointer");
@@ -464,8 +697,11 @@ extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32
         case MSM377_FQMUL_CARRYSAVE:
             k_fq_mul_variant<MSM377_FQMUL_CARRYSAVE><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
             break;
-        default:
+        case MSM377_FQMUL_CIOS_TWOPASS:
             k_fq_mul_variant<MSM377_FQMUL_CIOS_TWOPASS><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        default:
+            k_fq_mul_variant<MSM377_FQMUL_CIOS_DOUBLEROW><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
     }
     note_launches(1);
     return check_launch("fq_mul_batch_variant");

@@ -23,6 +23,7 @@ VARIANTS = {
     "karatsuba": (2, lambda x, y: x * y * RINV % fq.P),
     "carrysave": (3, lambda x, y: x * y * RINV % fq.P),
     "cios_twopass": (4, lambda x, y: x * y * RINV % fq.P),
+    "cios_doublerow": (5, lambda x, y: x * y * RINV % fq.P),
 }
 
 
