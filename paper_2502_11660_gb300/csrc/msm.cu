@@ -700,8 +700,8 @@ __global__ void k_sort_scan_digits(uint32_t* __restrict__ dtot) {
 template <int RB>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout, size_t n, int shift, size_t tiles, const uint32_t* __restrict__ hist,
-    const uint32_t* __restrict__ doff) {
+    uint32_t* __restrict__ vout, uint2* __restrict__ kvout, size_t n, int shift, size_t tiles,
+    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ doff) {
     constexpr int R = 1 << RB;
     __shared__ uint32_t wcnt[kSortThreads / 32][R];
     __shared__ uint32_t base[R];
@@ -747,8 +747,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
         if (idx < n) {
             size_t pos = (size_t)base[dig[r]] + wcnt[wid][dig[r]] + rank[r];
             if (pos < n) {  // always true when the counts agree; keeps writes in bounds
-                kout[seg + pos] = key[r];
-                vout[seg + pos] = val[r];
+                if (kvout) {    // last pass: (key, value) pairs, one 8-byte store
+                    kvout[seg + pos] = make_uint2(key[r], val[r]);
+                } else {
+                    kout[seg + pos] = key[r];
+                    vout[seg + pos] = val[r];
+                }
             }
         }
     }
@@ -857,8 +861,8 @@ __global__ void k_scan_add(uint32_t* __restrict__ x, size_t m, const uint32_t* _
 // Each item to the next free slot of its bin (cursor = the bins' offsets, advanced
 // with one warp-aggregated atomic per bin and warp).
 __global__ void k_bin_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t total, size_t np,
-                              uint32_t nb, uint32_t* __restrict__ cursor) {
+                              uint2* __restrict__ kvout, size_t total, size_t np, uint32_t nb,
+                              uint32_t* __restrict__ cursor) {
     const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const bool valid = j < np;
     const size_t i = (size_t)blockIdx.y * np + j;
@@ -871,17 +875,13 @@ __global__ void k_bin_scatter(const uint32_t* __restrict__ kin, const uint32_t* 
     base = __shfl_sync(peers, base, leader);
     if (!valid) return;
     const size_t pos = (size_t)base + __popc(peers & ((1u << lane) - 1u));
-    if (pos < total) {  // always true when the counts agree; keeps writes in bounds
-        kout[pos] = kin[i];
-        vout[pos] = vin[i];
-    }
+    if (pos < total) kvout[pos] = make_uint2(kin[i], vin[i]);  // in bounds when the counts agree
 }
 
 // ---------------------------------------------------------------- stages 4-5
 
 struct AccArgs {
-    const uint32_t* keys;  // [W][n]
-    const uint32_t* vals;  // [W][n]
+    const uint2* kv;       // [W][n] sorted (bucket key, point index | sign << 31)
     const uint4* pts;
     uint4* buckets;        // [W][Bp] XYZZ
     uint4* head;           // [W][cpw] XYZZ
@@ -900,21 +900,21 @@ struct AccArgs {
 template <class M>
 __device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32_t t) {
     const size_t ci = (size_t)w * a.cpw + t;
-    const uint32_t* keys = a.keys + (size_t)w * a.n;
-    const uint32_t* vals = a.vals + (size_t)w * a.n;
+    const uint2* kv = a.kv + (size_t)w * a.n;
     const size_t start = (size_t)t * a.K;
     const size_t end = start + a.K < a.n ? start + a.K : a.n;
-    const uint32_t prev = start > 0 ? keys[start - 1] : kNone;
-    const uint32_t next = end < a.n ? keys[end] : kNone;
+    const uint32_t prev = start > 0 ? kv[start - 1].x : kNone;
+    const uint32_t next = end < a.n ? kv[end].x : kNone;
     a.tailkey[ci] = kNone;
     a.headflag[ci] = 0;
     typename M::acc acc;
     M::set_inf(acc);
     bool inf = true;
-    uint32_t cur = keys[start];
+    uint32_t cur = kv[start].x;
     bool first = true;
     for (size_t g = start; g <= end; ++g) {
-        const uint32_t key = g < end ? keys[g] : kNone;
+        const uint2 e = g < end ? kv[g] : make_uint2(kNone, 0u);
+        const uint32_t key = e.x;
         if (key != cur) {
             if (cur != 0) {  // key 0 = zero digit, contributes nothing
                 const bool sb = first && prev == cur;
@@ -936,7 +936,7 @@ __device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32
             first = false;
         }
         if (key != 0) {
-            const uint32_t v = vals[g];
+            const uint32_t v = e.y;
             if ((v & 0x7fffffffu) >= a.n) continue;  // cannot happen for sorted digit output
             M::madd_at(acc, inf, a.pts, v & 0x7fffffffu, (v >> 31) != 0);
         }
@@ -1007,13 +1007,13 @@ __global__ void k_merge_start(AccArgs a, int32_t* __restrict__ start, int* __res
         start[ci] = -1;
         return;
     }
-    const uint32_t* keys = a.keys + (size_t)w * a.n;
+    const uint2* kv = a.kv + (size_t)w * a.n;
     const size_t first = (size_t)u * a.K;   // u > 0 here: chunk 0 has no earlier run
-    const uint32_t key = keys[first];
+    const uint32_t key = kv[first].x;
     size_t lo = 0, hi = first;              // first index in [0, first] with keys[i] >= key
     while (lo < hi) {
         const size_t mid = (lo + hi) >> 1;
-        if (keys[mid] < key) lo = mid + 1; else hi = mid;
+        if (kv[mid].x < key) lo = mid + 1; else hi = mid;
     }
     const int32_t t0 = (int32_t)(lo / (size_t)a.K);
     start[ci] = t0;
@@ -1272,7 +1272,7 @@ struct Plan {
     int ngroups;
     uint32_t L, G, Q;
     int logG, log2L;
-    size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_hist, off_dtot;
+    size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_kv, off_hist, off_dtot;
     int counting;                      // counting sort (else LSD radix sort)
     size_t nbins, off_bins, off_bsum;  // counting sort: bins (window, key) and scan tile totals
     size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
@@ -1387,8 +1387,12 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->off_points = take(o->flags & MSM377_POINTS_PREPARED ? 0 : np * 16 * (size_t)p->stored_vec);
     p->off_keys0 = take((size_t)p->W * items * 4);
     p->off_vals0 = take((size_t)p->W * items * 4);
-    p->off_keys1 = take((size_t)p->W * items * 4);
-    p->off_vals1 = take((size_t)p->W * items * 4);
+    // the sort's ping-pong buffers (radix passes before the last); the last pass, or
+    // the counting scatter, writes (key, value) pairs to kv
+    const bool pingpong = !p->counting && p->passes > 1;
+    p->off_keys1 = take(pingpong ? (size_t)p->W * items * 4 : 0);
+    p->off_vals1 = take(pingpong ? (size_t)p->W * items * 4 : 0);
+    p->off_kv = take((size_t)p->W * items * 8);
     p->off_hist = take((size_t)p->W * (1u << p->rb) * (p->tiles ? p->tiles : 1) * 4);
     p->off_dtot = take((size_t)p->W * (1u << p->rb) * 4);
     p->nbins = (size_t)p->W * (p->Bp + 1);  // keys 0 .. Bp of every window
@@ -1541,6 +1545,7 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     const size_t np = p.items;  // items per pipeline window
     uint32_t* keys[2] = {at<uint32_t>(workspace, p.off_keys0), at<uint32_t>(workspace, p.off_keys1)};
     uint32_t* vals[2] = {at<uint32_t>(workspace, p.off_vals0), at<uint32_t>(workspace, p.off_vals1)};
+    uint2* kv = at<uint2>(workspace, p.off_kv);
     k_digits<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(scalars), n, p.c, p.Wd,
                                               p.sgn, p.user_bits, p.glv, p.pre, keys[0], vals[0], status);
     note_launches(1);
@@ -1558,9 +1563,8 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
         k_scan_tiles<<<(unsigned)ntiles, kScanBlock, 0, s>>>(bins, p.nbins, bsum);
         k_scan_totals<<<1, kScanBlock, 0, s>>>(bsum, ntiles);
         k_scan_add<<<grid_for(p.nbins, 256), 256, 0, s>>>(bins, p.nbins, bsum);
-        k_bin_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], keys[1], vals[1], total, np, nb, bins);
+        k_bin_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], kv, total, np, nb, bins);
         note_launches(5);
-        cur = 1;
     } else {
         uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
         uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);
@@ -1570,8 +1574,9 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
             k_sort_hist<8><<<g, kSortThreads, 0, s>>>(keys[cur], np, shift, p.tiles, hist);
             k_sort_scan_tiles<8><<<dim3(1u << 8, p.W), kSortThreads, 0, s>>>(hist, p.tiles, dtot);
             k_sort_scan_digits<8><<<p.W, kSortThreads, 0, s>>>(dtot);
-            k_sort_scatter<8><<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], np,
-                                                         shift, p.tiles, hist, dtot);
+            uint2* last = pass == p.passes - 1 ? kv : nullptr;
+            k_sort_scatter<8><<<g, kSortThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], last,
+                                                         np, shift, p.tiles, hist, dtot);
             note_launches(4);
             cur ^= 1;
         }
@@ -1579,8 +1584,7 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     uint4* buckets = at<uint4>(workspace, p.off_buckets);
     MSM_CUDA_TRY(cudaMemsetAsync(buckets, 0, (size_t)p.W * p.Bp * kXyzzBytes, s));
     AccArgs& a = *a_out;
-    a.keys = keys[cur];
-    a.vals = vals[cur];
+    a.kv = kv;
     a.pts = pts;
     a.buckets = buckets;
     a.head = at<uint4>(workspace, p.off_head);
