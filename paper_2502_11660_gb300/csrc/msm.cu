@@ -770,17 +770,23 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
 constexpr int kScanBlock = 1024, kScanPer = 4, kScanTile = kScanBlock * kScanPer;
 
 // Grid (items of a window / 256, windows): item i = w np + j of window w = blockIdx.y.
+// Counts per (window, key) bin; each item keeps its rank among the items of its bin
+// (the warp's share from one atomic per distinct bin, then the lanes' order), so the
+// scatter needs no atomics.
 __global__ void k_bin_count(const uint32_t* __restrict__ keys, size_t np, uint32_t nb,
-                            uint32_t* __restrict__ counts) {
+                            uint32_t* __restrict__ counts, uint32_t* __restrict__ rank) {
     const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const bool valid = j < np;
-    const uint32_t bin = valid ? blockIdx.y * nb + keys[(size_t)blockIdx.y * np + j] : 0xffffffffu;
+    const size_t i = (size_t)blockIdx.y * np + j;
+    const uint32_t bin = valid ? blockIdx.y * nb + keys[i] : 0xffffffffu;
     const uint32_t peers = __match_any_sync(0xffffffffu, bin);
     const int lane = threadIdx.x & 31;
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&counts[bin], (uint32_t)__popc(peers));
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (valid && lane == leader) base = atomicAdd(&counts[bin], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (valid) rank[i] = base + __popc(peers & ((1u << lane) - 1u));
 }
-
-// In place exclusive scan of each tile of kScanTile counts; tile totals to bsum.
 __global__ void __launch_bounds__(kScanBlock) k_scan_tiles(uint32_t* __restrict__ x, size_t m,
                                                            uint32_t* __restrict__ bsum) {
     __shared__ uint32_t warp_tot[kScanBlock / 32];
@@ -861,21 +867,14 @@ __global__ void k_scan_add(uint32_t* __restrict__ x, size_t m, const uint32_t* _
 // Each item to the next free slot of its bin (cursor = the bins' offsets, advanced
 // with one warp-aggregated atomic per bin and warp).
 __global__ void k_bin_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                              uint2* __restrict__ kvout, size_t total, size_t np, uint32_t nb,
-                              uint32_t* __restrict__ cursor) {
+                              const uint32_t* __restrict__ rank, uint2* __restrict__ kvout, size_t total,
+                              size_t np, uint32_t nb, const uint32_t* __restrict__ start) {
     const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const bool valid = j < np;
+    if (j >= np) return;
     const size_t i = (size_t)blockIdx.y * np + j;
-    const uint32_t bin = valid ? blockIdx.y * nb + kin[i] : 0xffffffffu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, bin);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (valid && lane == leader) base = atomicAdd(&cursor[bin], (uint32_t)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    if (!valid) return;
-    const size_t pos = (size_t)base + __popc(peers & ((1u << lane) - 1u));
-    if (pos < total) kvout[pos] = make_uint2(kin[i], vin[i]);  // in bounds when the counts agree
+    const uint32_t key = kin[i];
+    const size_t pos = (size_t)start[blockIdx.y * nb + key] + rank[i];
+    if (pos < total) kvout[pos] = make_uint2(key, vin[i]);  // in bounds when the counts agree
 }
 
 // ---------------------------------------------------------------- stages 4-5
@@ -1272,7 +1271,7 @@ struct Plan {
     int ngroups;
     uint32_t L, G, Q;
     int logG, log2L;
-    size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_kv, off_hist, off_dtot;
+    size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_kv, off_rank, off_hist, off_dtot;
     int counting;                      // counting sort (else LSD radix sort)
     size_t nbins, off_bins, off_bsum;  // counting sort: bins (window, key) and scan tile totals
     size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
@@ -1393,6 +1392,7 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->off_keys1 = take(pingpong ? (size_t)p->W * items * 4 : 0);
     p->off_vals1 = take(pingpong ? (size_t)p->W * items * 4 : 0);
     p->off_kv = take((size_t)p->W * items * 8);
+    p->off_rank = take(p->counting ? (size_t)p->W * items * 4 : 0);  // counting sort: rank within the bin
     p->off_hist = take((size_t)p->W * (1u << p->rb) * (p->tiles ? p->tiles : 1) * 4);
     p->off_dtot = take((size_t)p->W * (1u << p->rb) * 4);
     p->nbins = (size_t)p->W * (p->Bp + 1);  // keys 0 .. Bp of every window
@@ -1556,14 +1556,15 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
         const uint32_t nb = p.Bp + 1;
         uint32_t* bins = at<uint32_t>(workspace, p.off_bins);
         uint32_t* bsum = at<uint32_t>(workspace, p.off_bsum);
+        uint32_t* rank = at<uint32_t>(workspace, p.off_rank);
         const size_t ntiles = (p.nbins + kScanTile - 1) / kScanTile;
         MSM_CUDA_TRY(cudaMemsetAsync(bins, 0, p.nbins * 4, s));
         const dim3 gw(grid_for(np, 256), (unsigned)p.W);
-        k_bin_count<<<gw, 256, 0, s>>>(keys[0], np, nb, bins);
+        k_bin_count<<<gw, 256, 0, s>>>(keys[0], np, nb, bins, rank);
         k_scan_tiles<<<(unsigned)ntiles, kScanBlock, 0, s>>>(bins, p.nbins, bsum);
         k_scan_totals<<<1, kScanBlock, 0, s>>>(bsum, ntiles);
         k_scan_add<<<grid_for(p.nbins, 256), 256, 0, s>>>(bins, p.nbins, bsum);
-        k_bin_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], kv, total, np, nb, bins);
+        k_bin_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], rank, kv, total, np, nb, bins);
         note_launches(5);
     } else {
         uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
