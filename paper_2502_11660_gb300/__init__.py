@@ -25,6 +25,7 @@ PROFILE = 2
 EDWARDS = 4   # the paper's twisted Edwards model; points of the order-r subgroup
 GLV = 8       # endomorphism split, half the windows; points of the order-r subgroup
 PRECOMPUTED = 16  # fixed-base shifted copies 2^(cj) P (Edwards resident sets, explicit c)
+RADIX_SORT = 32   # 8-bit LSD radix passes instead of the default counting sort (comparison)
 MSM_STAGES = ("head", "accumulate", "tail")
 
 __all__ = [
@@ -35,7 +36,7 @@ __all__ = [
     "imad_probe", "lib", "last_error", "profile_last", "launch_count", "MSM_STAGES", "PROFILE",
     "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace", "EDWARDS", "GLV",
     "msm_points_prepared_bytes", "padd_chain", "fq_mul_batch_variant", "FQMUL_CIOS", "FQMUL_BARRETT",
-    "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE", "FQMUL_CIOS_TWOPASS", "FQMUL_CIOS_DOUBLEROW", "PRECOMPUTED", "msm_points_precompute",
+    "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE", "FQMUL_CIOS_TWOPASS", "FQMUL_CIOS_DOUBLEROW", "PRECOMPUTED", "RADIX_SORT", "msm_points_precompute",
     "msm_points_precomputed_bytes",
 ]
 
@@ -153,11 +154,11 @@ def msm_points_prepare(points: torch.Tensor, out: torch.Tensor | None = None, st
 
 
 def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0, profile=False, edwards=False,
-          glv=False, precomputed=False) -> MsmOpts:
+          glv=False, precomputed=False, radix_sort=False) -> MsmOpts:
     """stream=0 for size queries (no CUDA context needed); None = torch's current stream."""
     sv = 0 if (isinstance(stream, int) and stream == 0) else _s(stream).value
     flags = (POINTS_PREPARED if prepared else 0) | (PROFILE if profile else 0) | _model_flags(edwards, glv)
-    flags |= PRECOMPUTED if precomputed else 0
+    flags |= (PRECOMPUTED if precomputed else 0) | (RADIX_SORT if radix_sort else 0)
     return MsmOpts(int(c), 1 if signed else 0, int(scalar_bits), flags, sv)
 
 
@@ -191,8 +192,10 @@ def msm_g1_default_c(n: int, signed: bool = True, edwards: bool = False, glv: bo
 
 
 def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, device="cuda",
-                     edwards: bool = False, glv: bool = False, precomputed: bool = False) -> torch.Tensor:
-    o = _opts(c, signed, scalar_bits, prepared or precomputed, edwards=edwards, glv=glv, precomputed=precomputed)
+                     edwards: bool = False, glv: bool = False, precomputed: bool = False,
+                     radix_sort: bool = False) -> torch.Tensor:
+    o = _opts(c, signed, scalar_bits, prepared or precomputed, edwards=edwards, glv=glv, precomputed=precomputed,
+              radix_sort=radix_sort)
     nbytes = lib().msm_g1_workspace_bytes(n, ctypes.byref(o))
     if nbytes == 0:
         raise MsmError(-1, "bad MSM options")
@@ -202,17 +205,20 @@ def msm_g1_workspace(n: int, c=0, signed=True, scalar_bits=0, prepared=False, de
 def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None = None,
            workspace: torch.Tensor | None = None, c: int = 0, signed: bool = True,
            scalar_bits: int = 0, prepared: bool = False, stream=None, profile: bool = False,
-           edwards: bool = False, glv: bool = False, precomputed: bool = False) -> torch.Tensor:
+           edwards: bool = False, glv: bool = False, precomputed: bool = False,
+           radix_sort: bool = False) -> torch.Tensor:
     """Enqueues sum_i scalars_i * points_i; returns the (24,) int32 device tensor it writes.
     With prepared=True, points is msm_points_prepare(..., edwards=, glv=) output; with
-    precomputed=True (Edwards, explicit c) msm_points_precompute output for the same options."""
+    precomputed=True (Edwards, explicit c) msm_points_precompute output for the same options.
+    radix_sort=True sorts by LSD radix passes instead of the counting sort (same result;
+    the workspace must be sized with the same choice)."""
     n = scalars.shape[0]
     o = _opts(c, signed, scalar_bits, prepared or precomputed, None if stream is None else stream, profile,
-              edwards, glv, precomputed)
+              edwards, glv, precomputed, radix_sort)
     _check_points(points, n, prepared or precomputed, edwards, glv, o)
     if workspace is None:
         workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared or precomputed, points.device, edwards,
-                                     glv, precomputed)
+                                     glv, precomputed, radix_sort)
     out = torch.empty(24, dtype=torch.int32, device=points.device) if out is None else out
     _check_dev(points, scalars, out, workspace)
     check(lib().msm_g1(_p(points), _p(scalars), n, _p(out), _p(workspace), workspace.numel(),

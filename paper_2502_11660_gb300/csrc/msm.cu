@@ -1341,10 +1341,10 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     // the 1024-bin scatter's shared-memory counters cost more than the pass)
     p->rb = 8;
     p->passes = (p->c + p->rb - 1) / p->rb;
-    // Measured on GB300: counting by (window, key) bins beats the radix passes when
-    // the radix sort needs three passes or there are few windows (large bins);
-    // with many small windows the two radix passes are as fast.
-    p->counting = (p->passes >= 3 || p->W <= 8) ? 1 : 0;
+    // Measured on GB300: the counting sort (ranks taken in the counting pass, no
+    // atomics in the scatter) beats the radix passes for every plan; the radix sort
+    // stays available for comparison.
+    p->counting = (o->flags & MSM377_RADIX_SORT) ? 0 : 1;
     p->tiles = (items + kSortTile - 1) / kSortTile;
     // Chunks of K <= 64 items, one per thread, sized so that the chunks over all
     // windows fill whole waves of resident accumulation threads (152 SMs x 3 blocks

@@ -139,6 +139,11 @@ def test_stored_point_sizes_and_mode_flags():
     split = L.msm_g1_workspace_bytes(1 << 16, ctypes.byref(pkg._opts(c=12, scalar_bits=253, glv=True)))
     assert plain > 0 and split > 0
     assert pkg.msm_g1_default_c(1 << 20, glv=True) == pkg.msm_g1_default_c(1 << 21)
+    # the sort choice changes the workspace: counting sort = ranks + (key, value) pairs;
+    # radix sort with two passes = ping-pong key/value arrays + pairs
+    cnt = L.msm_g1_workspace_bytes(1 << 16, ctypes.byref(pkg._opts(c=16, scalar_bits=253)))
+    rdx = L.msm_g1_workspace_bytes(1 << 16, ctypes.byref(pkg._opts(c=16, scalar_bits=253, radix_sort=True)))
+    assert cnt > 0 and rdx > 0 and cnt != rdx
 
 
 def test_window_tables_are_per_mode():

@@ -71,6 +71,29 @@ def test_edge_scalars_and_points():
         assert run(pts, a, c=c, signed=sg, scalar_bits=253) == want
 
 
+@pytest.mark.parametrize("n", [1, 33, 1000, 4099])
+def test_radix_sort_path_matches_the_counting_sort(n):
+    """MSM377_RADIX_SORT (LSD radix passes) gives the same sums as the default
+    counting sort: one, two and three 8-bit passes, signed and unsigned digits, and
+    both curve models."""
+    a, s, pts = msm_inputs(n, tag=300 + n)
+    want = closed_form_limbs(s, a)
+    for c, sg in [(4, False), (8, True), (13, True), (16, True), (18, False)]:
+        assert run(pts, a, c=c, signed=sg, scalar_bits=253, radix_sort=True) == want
+    assert run(pts, a, c=11, scalar_bits=253, edwards=True, glv=True, radix_sort=True) == want
+
+
+def test_radix_sort_edge_scalars_and_heavy_bucket():
+    n = 3000
+    a, s, pts = msm_inputs(n, tag=11)
+    a = a.copy()
+    a[0:100] = 0
+    a[100:2100] = a[100]          # one bucket per window holds 2000 points
+    want = closed_form_limbs(s, a)
+    for c in (6, 16):
+        assert run(pts, a, c=c, signed=True, scalar_bits=253, radix_sort=True) == want
+
+
 def test_heavy_bucket_all_equal_scalars():
     """All scalars equal: every window has one bucket holding all n points."""
     n = 5000
