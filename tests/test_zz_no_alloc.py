@@ -22,8 +22,8 @@ pytestmark = pytest.mark.gpu
 pkg = pytest.importorskip("paper_2502_11660_gb300")
 
 
-def _noalloc(points, scalars, out, c, signed, scalar_bits):
-    o = pkg.MsmOpts(c, 1 if signed else 0, scalar_bits, 0, torch.cuda.current_stream().cuda_stream)
+def _noalloc(points, scalars, out, c, signed, scalar_bits, flags=0):
+    o = pkg.MsmOpts(c, 1 if signed else 0, scalar_bits, flags, torch.cuda.current_stream().cuda_stream)
     return pkg.lib().msm_g1_noalloc(ctypes.c_void_p(points.data_ptr()), ctypes.c_void_p(scalars.data_ptr()),
                                     points.shape[0], ctypes.c_void_p(out.data_ptr()), ctypes.byref(o))
 
@@ -42,6 +42,22 @@ def test_noalloc_matches_msm_g1_on_two_calls_in_a_row(c, signed):
         assert np.array_equal(got, pkg.to_host(ref))
         from oracle import g1
         assert g1.from_limbs(got) == closed_form_limbs(s, a)
+
+
+@pytest.mark.parametrize("flags", ["edwards_glv", "radix_sort"])
+def test_noalloc_curve_models_and_sort_choice(flags):
+    """The scratch also holds the Edwards + GLV stored points the call prepares, and the
+    radix sort's buffers; both give the closed form."""
+    from oracle import g1
+    f = (pkg.EDWARDS | pkg.GLV) if flags == "edwards_glv" else pkg.RADIX_SORT
+    n = 2048
+    a, s, pts = msm_inputs(n, 303)
+    dp, da = pkg.to_device(pts), pkg.to_device(a)
+    out = torch.full((24,), -1, dtype=torch.int32, device="cuda")
+    rc = _noalloc(dp, da, out, 0, True, 253, f)
+    assert rc == 0, pkg.last_error()
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == closed_form_limbs(s, a)
 
 
 def test_noalloc_refuses_requests_beyond_its_scratch():
