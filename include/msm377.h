@@ -295,7 +295,7 @@ int msm_g1_host(const uint32_t *points_host, const uint32_t *scalars_host, size_
  * exits; it calls no cudaMalloc, cudaFree or other allocating routine.
  * - Size limit: n and the options must need at most MSM377_NOALLOC_SCRATCH_BYTES
  *   of workspace (msm_g1_workspace_bytes); with the default options that holds
- *   up to n = 2^14. Larger requests fail with MSM377_EINVAL and a message.
+ *   up to n = 2^15. Larger requests fail with MSM377_EINVAL and a message.
  * - The first call on each device looks up the scratch address (a one-time
  *   set-up per device); make that first call before any stream capture.
  * - Every call on a device shares the one scratch array and it keeps the last
