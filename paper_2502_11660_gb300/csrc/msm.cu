@@ -263,11 +263,12 @@ __device__ __forceinline__ fe shfl_fe(const fe& a, int src) {
 // the whole warp: prefix and suffix products over the lanes' chunk products hand
 // every lane the inverse of its own product, from which it walks back through its
 // chunk. Every lane of the warp must call it (m may be 0; lanes carry 1 then).
-__device__ __forceinline__ void warp_batch_inverse(fe (&den)[kEdChunk], const bool (&ok)[kEdChunk], int m) {
+template <int K>
+__device__ __forceinline__ void warp_batch_inverse(fe (&den)[K], const bool (&ok)[K], int m) {
     const int lane = threadIdx.x & 31;
     fe one;
     fq::set_one(one);
-    fe prefix[kEdChunk];
+    fe prefix[K];
     fe acc = one;
     for (int j = 0; j < m; ++j) {
         prefix[j] = acc;                   // product of the valid den[0..j-1]
@@ -321,10 +322,55 @@ __device__ __forceinline__ void store_ed_identity(uint4* o) {
 // of the warp must call it (one inversion per warp).
 __device__ __forceinline__ void ed_affine_chunk(const uint4* __restrict__ in, size_t n, size_t np, size_t i0, int m,
                                                 fe (&xe)[kEdChunk], fe (&ye)[kEdChunk], bool (&ok)[kEdChunk]) {
-    fe xs[kEdChunk], ys[kEdChunk], den[kEdChunk];
     fe one, sp;
     fq::set_one(one);
     ed::load_const(sp, ed::kS);
+    if (np != n && (i0 & 1) == 0 && (m & 1) == 0) {
+        // GLV rows in pairs (P, phi(P)) = ((x, y), (beta x, y)): the pair shares y, so
+        // it inverts y, a + s and a' + s (a = x + 1, a' = beta x + 1) instead of the
+        // two products y (a + s), y (a' + s); x_e = c1 a / y, y_e = (a - s) / (a + s).
+        constexpr int kPairs = kEdChunk / 2;
+        fe xs[kEdChunk], inv[3 * kPairs];
+        bool okv[3 * kPairs];
+        fe y[kPairs];
+        for (int q = 0; q < m / 2; ++q) {
+            fe x0;
+            glv_source(x0, y[q], in, i0 + 2 * q, n, np);
+            const bool id = fq::is_zero_raw(x0) && fq::is_zero_raw(y[q]);
+            fe b;
+            ed::load_const(b, kBeta);
+            fq::mul(xs[2 * q + 1], x0, b);
+            fq::canon(xs[2 * q + 1], xs[2 * q + 1]);
+            xs[2 * q] = x0;
+            inv[3 * q] = y[q];
+            fq::add(inv[3 * q + 1], xs[2 * q], one);
+            fq::add(inv[3 * q + 1], inv[3 * q + 1], sp);
+            fq::add(inv[3 * q + 2], xs[2 * q + 1], one);
+            fq::add(inv[3 * q + 2], inv[3 * q + 2], sp);
+            okv[3 * q] = !id && !fq::is_zero(inv[3 * q]);
+            okv[3 * q + 1] = !id && !fq::is_zero(inv[3 * q + 1]);
+            okv[3 * q + 2] = !id && !fq::is_zero(inv[3 * q + 2]);
+        }
+        warp_batch_inverse(inv, okv, 3 * (m / 2));
+        fe c1;
+        ed::load_const(c1, ed::kC1);
+        for (int q = 0; q < m / 2; ++q) {
+            fe cy;
+            if (okv[3 * q]) fq::mul(cy, c1, inv[3 * q]);   // c1 / y
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * q + h;
+                ok[j] = okv[3 * q] && okv[3 * q + 1 + h];
+                if (!ok[j]) continue;
+                fe a, d;
+                fq::add(a, xs[j], one);
+                fq::mul(xe[j], a, cy);                        // c1 a / y
+                fq::sub(d, a, sp);
+                fq::mul(ye[j], d, inv[3 * q + 1 + h]);        // (a - s) / (a + s)
+            }
+        }
+        return;
+    }
+    fe xs[kEdChunk], ys[kEdChunk], den[kEdChunk];
     for (int j = 0; j < m; ++j) {
         glv_source(xs[j], ys[j], in, i0 + j, n, np);
         ok[j] = !(fq::is_zero_raw(xs[j]) && fq::is_zero_raw(ys[j]));
@@ -366,7 +412,7 @@ __device__ __forceinline__ void store_ed_stored(uint4* o, fe x, fe y) {
 // One warp covers 32 * kEdChunk consecutive stored points of rows [lo, hi); every
 // lane of every launched warp takes part in the shuffles (lanes past hi carry the
 // product 1).
-__global__ void __launch_bounds__(128) k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n,
+__global__ void __launch_bounds__(128, 4) k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n,
                                                     size_t np, size_t lo, size_t hi) {
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t i0 = lo + t * kEdChunk;
@@ -390,7 +436,7 @@ __global__ void __launch_bounds__(128) k_prepare_ed(const uint4* __restrict__ in
 // window and normalises it with one inversion per warp and window. With these,
 // every window of an MSM adds into the same buckets:
 // sum_j 2^(cj) sum_b b B_jb = sum_b b sum_j B'_jb with B' over the shifted points.
-__global__ void __launch_bounds__(128) k_precompute_ed(const uint4* __restrict__ in, uint4* __restrict__ out,
+__global__ void __launch_bounds__(128, 3) k_precompute_ed(const uint4* __restrict__ in, uint4* __restrict__ out,
                                                        size_t n, size_t np, int c, int Wd) {
     const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t i0 = t * kEdChunk;
