@@ -320,12 +320,16 @@ __device__ __forceinline__ void store_ed_identity(uint4* o) {
 // standard-form input, GLV rows included); ok[j] is false for the affine identity
 // and points outside the map's domain, whose (x, y) is then left unset. Every lane
 // of the warp must call it (one inversion per warp).
+// pairs: GLV rows taken as (P, phi(P)) pairs. The caller decides it for the whole
+// launch (every lane must reach the same warp_batch_inverse): a GLV row range with
+// an even start and end, so every lane's i0 and m are even.
 __device__ __forceinline__ void ed_affine_chunk(const uint4* __restrict__ in, size_t n, size_t np, size_t i0, int m,
-                                                fe (&xe)[kEdChunk], fe (&ye)[kEdChunk], bool (&ok)[kEdChunk]) {
+                                                bool pairs, fe (&xe)[kEdChunk], fe (&ye)[kEdChunk],
+                                                bool (&ok)[kEdChunk]) {
     fe one, sp;
     fq::set_one(one);
     ed::load_const(sp, ed::kS);
-    if (np != n && (i0 & 1) == 0 && (m & 1) == 0) {
+    if (pairs) {
         // GLV rows in pairs (P, phi(P)) = ((x, y), (beta x, y)): the pair shares y, so
         // it inverts y, a + s and a' + s (a = x + 1, a' = beta x + 1) instead of the
         // two products y (a + s), y (a' + s); x_e = c1 a / y, y_e = (a - s) / (a + s).
@@ -419,7 +423,8 @@ __global__ void __launch_bounds__(128, 4) k_prepare_ed(const uint4* __restrict__
     const int m = i0 >= hi ? 0 : (int)(hi - i0 < (size_t)kEdChunk ? hi - i0 : (size_t)kEdChunk);
     fe xe[kEdChunk], ye[kEdChunk];
     bool ok[kEdChunk];
-    ed_affine_chunk(in, n, np, i0, m, xe, ye, ok);
+    const bool pairs = np != n && (lo & 1) == 0 && (hi & 1) == 0;  // the same for the whole launch
+    ed_affine_chunk(in, n, np, i0, m, pairs, xe, ye, ok);
     for (int j = 0; j < m; ++j) {
         uint4* o = out + (size_t)ModelEdwards::kStored * (i0 + j);
         if (ok[j])
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(128, 3) k_precompute_ed(const uint4* __restric
     ed::ext P[kEdChunk];
     {
         fe xe[kEdChunk], ye[kEdChunk];
-        ed_affine_chunk(in, n, np, i0, m, xe, ye, ok);
+        ed_affine_chunk(in, n, np, i0, m, np != n && (np & 1) == 0, xe, ye, ok);  // rows [0, np): launch-wide
         for (int q = 0; q < m; ++q) {
             uint4* o = out + (size_t)ModelEdwards::kStored * ((i0 + q) * (size_t)Wd);
             if (ok[q]) {
