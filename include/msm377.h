@@ -16,12 +16,14 @@
  * - Scalars: 8 little-endian 32-bit limbs (any 256-bit value is accepted).
  * - Ownership: the caller allocates and frees every buffer. Pointers are device
  *   pointers unless the name ends in _host. No call keeps a pointer after it
- *   returns.
+ *   returns. The exception is a resident set (msm_points_create): a copy of the
+ *   caller's points in the library's own device memory until msm_points_destroy.
  * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream). Calls only enqueue work on it and return, except those marked
  *   "synchronous".
  * - Inputs out of their stated range (coordinates >= p, points off the curve)
- *   produce unspecified output values but never out-of-bounds accesses.
+ *   produce unspecified output values but never out-of-bounds accesses, unless
+ *   the call is asked to check them (MSM377_VALIDATE, msm_points_validate).
  * - Every call returns a status code below; on MSM377_ECUDA and MSM377_EINVAL,
  *   msm377_last_error() holds a message.
  */
@@ -40,7 +42,10 @@ extern "C" {
 #define MSM377_ENOMEM (-2)   /* the workspace passed is smaller than required */
 #define MSM377_ECUDA (-3)    /* a CUDA runtime call failed */
 #define MSM377_ETIMEOUT (-4) /* a bounded device-side wait gave up */
-#define MSM377_ERANGE (-5)   /* a scalar had bits at or above opts.scalar_bits */
+#define MSM377_ENOTONCURVE (-5) /* MSM377_VALIDATE: an input point is not on y^2 = x^3 + 1 (or has a
+                                   coordinate >= p), or, where the curve model needs it, is not in the
+                                   order-r subgroup */
+#define MSM377_ERANGE (-6)   /* a scalar had bits at or above opts.scalar_bits */
 
 #define MSM377_FORM_STANDARD 0
 #define MSM377_FORM_MONTGOMERY 1
@@ -159,6 +164,15 @@ int g1_generator_mul(const uint32_t *seeds, size_t n, uint32_t *out, void *strea
  * a scan, one scatter). Same result; kept for comparison (the counting sort measured
  * faster for every plan on GB300). */
 #define MSM377_RADIX_SORT 32u
+/* Check the input points before using them (Sec. I / II-C: the problem is a sum over
+ * points of the BLS12-377 G1 group): every coordinate below p, every point on
+ * y^2 = x^3 + 1 ((0, 0) is O), and with MSM377_EDWARDS or MSM377_GLV (whose maps are
+ * exact on the order-r subgroup only) also r P = O, by double-and-add per point (about
+ * 3,200 field multiplications per point: opt-in, for data of unknown origin).
+ * msm_g1 (standard-form points only; with MSM377_POINTS_PREPARED the call fails with
+ * MSM377_EINVAL) and msm_g1_host report MSM377_ENOTONCURVE through the device status;
+ * msm_points_create returns it. Not accepted by msm_g1_batched and msm_g1_noalloc. */
+#define MSM377_VALIDATE 64u
 
 typedef struct msm_opts {
     int32_t c;             /* window width in bits, 2..20; 0 = chosen from n */
@@ -168,7 +182,7 @@ typedef struct msm_opts {
                               0 = 256. A larger scalar makes the call fail with
                               MSM377_ERANGE (reported through the workspace status). */
     uint32_t flags;        /* MSM377_POINTS_PREPARED | MSM377_PROFILE | MSM377_EDWARDS | MSM377_GLV |
-                              MSM377_PRECOMPUTED | MSM377_RADIX_SORT */
+                              MSM377_PRECOMPUTED | MSM377_RADIX_SORT | MSM377_VALIDATE */
     void *stream;          /* cudaStream_t */
 } msm_opts;
 
@@ -234,6 +248,55 @@ int msm_g1(const uint32_t *points, const uint32_t *scalars, size_t n, uint32_t *
            void *workspace, size_t workspace_bytes, const msm_opts *opts);
 
 /* ------------------------------------------------------------------------
+ * Point validation and resident point sets. A prover commits to the same point
+ * set (the "bases" of the sum of Sec. I / II-C) over and over with fresh scalars;
+ * a resident set holds their stored form in library-owned device memory.
+ */
+
+/* Checks n affine standard-form points (device, 24 u32 each, 16-byte aligned) as
+ * MSM377_VALIDATE describes; flags: MSM377_EDWARDS / MSM377_GLV / MSM377_PRECOMPUTED
+ * ask for the subgroup check as well (MSM377_VALIDATE itself is allowed and ignored).
+ * Synchronous on stream. Returns MSM377_OK or MSM377_ENOTONCURVE. */
+int msm_points_validate(const uint32_t *points_std, size_t n, uint32_t flags, void *stream);
+
+/* Opaque handle of a resident set. */
+typedef struct msm_points_set *msm_points_t;
+
+/* Makes a resident set from n >= 1 affine standard-form points (device, 24 u32 per
+ * point, 16-byte aligned; read during the call only). opts->flags: the curve model
+ * (MSM377_EDWARDS, MSM377_GLV; MSM377_PRECOMPUTED with MSM377_EDWARDS and an explicit
+ * opts->c makes a fixed-base set for that c, opts->scalar_bits and digit kind) and
+ * optionally MSM377_VALIDATE (then the points are checked first, synchronously, and
+ * a failing set returns MSM377_ENOTONCURVE and no handle). The set owns device
+ * memory (cudaMalloc) for the stored rows until msm_points_destroy; the stored
+ * form is filled asynchronously on opts->stream. *handle is NULL on failure. */
+int msm_points_create(const uint32_t *points_std, size_t n, const msm_opts *opts, msm_points_t *handle);
+
+/* Frees the set's device memory (cudaFree: waits for the device). NULL is a no-op. */
+int msm_points_destroy(msm_points_t handle);
+
+/* Number of input points the set holds (0 for NULL). */
+size_t msm_points_count(msm_points_t handle);
+
+/* Device pointer to the stored rows of input point `offset` (offset <= count), for
+ * msm_job.points of a batched call with MSM377_POINTS_PREPARED and the set's own
+ * model flags; NULL for a bad handle or offset. Valid until msm_points_destroy. */
+const uint32_t *msm_points_data(msm_points_t handle, size_t offset);
+
+/* Workspace bytes of msm_g1_resident for n points of the set (0 on bad options). */
+size_t msm_g1_resident_workspace_bytes(msm_points_t handle, size_t n, const msm_opts *opts);
+
+/* msm_g1 over the set's input points [offset, offset + n) (Sec. II-C):
+ * out = sum_{i < n} scalars_i * P_{offset + i}. The set supplies the curve model
+ * (opts->flags may repeat it or leave it out; another model is MSM377_EINVAL); a
+ * fixed-base set also fixes c, scalar_bits and the digit kind (opts->c and
+ * opts->scalar_bits 0 or equal). Allowed extra flags: MSM377_PROFILE,
+ * MSM377_RADIX_SORT. scalars, out, workspace and the status word as for msm_g1.
+ * Asynchronous on opts->stream. */
+int msm_g1_resident(msm_points_t handle, size_t offset, size_t n, const uint32_t *scalars, uint32_t *out,
+                    void *workspace, size_t workspace_bytes, const msm_opts *opts);
+
+/* ------------------------------------------------------------------------
  * Batched MSM: many independent MSMs of uneven size in one call. The per-job
  * preparation, digits and sort run on library-owned helper streams; the bucket
  * accumulation of all jobs is one persistent kernel that drains a queue of
@@ -296,15 +359,17 @@ int msm_g1_host(const uint32_t *points_host, const uint32_t *scalars_host, size_
  * - Size limit: n and the options must need at most MSM377_NOALLOC_SCRATCH_BYTES
  *   of workspace (msm_g1_workspace_bytes); with the default options that holds
  *   up to n = 2^15. Larger requests fail with MSM377_EINVAL and a message.
- * - The first call on each device looks up the scratch address (a one-time
- *   set-up per device); make that first call before any stream capture.
+ * - The first call on each device (and in each CUDA context: a driver-API
+ *   context, or the primary context again after cudaDeviceReset) looks up the
+ *   scratch address (a one-time set-up there); make that first call before any
+ *   stream capture.
  * - Every call on a device shares the one scratch array and it keeps the last
  *   call's contents (each call clears what must start at zero). Calls whose
  *   work overlaps on the GPU (different streams, or different host threads)
  *   race on it and give wrong results: serialise them.
  * - The device status word (MSM377_ERANGE for scalars at or above
  *   opts->scalar_bits) is not reported here; leave scalar_bits at 0 (256) to
- *   rule that error out. MSM377_PROFILE is rejected.
+ *   rule that error out. MSM377_PROFILE and MSM377_VALIDATE are rejected.
  * Asynchronous on opts->stream, like msm_g1. */
 #define MSM377_NOALLOC_SCRATCH_BYTES (64u << 20)
 int msm_g1_noalloc(const uint32_t *points, const uint32_t *scalars, size_t n, uint32_t *out,

@@ -26,7 +26,9 @@ EDWARDS = 4   # the paper's twisted Edwards model; points of the order-r subgrou
 GLV = 8       # endomorphism split, half the windows; points of the order-r subgroup
 PRECOMPUTED = 16  # fixed-base shifted copies 2^(cj) P (Edwards resident sets, explicit c)
 RADIX_SORT = 32   # 8-bit LSD radix passes instead of the default counting sort (comparison)
+VALIDATE = 64     # check input points (on the curve; in the subgroup for Edwards / GLV)
 MSM_STAGES = ("head", "accumulate", "tail")
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTONCURVE, ERANGE = 0, -1, -2, -3, -4, -5, -6
 
 __all__ = [
     "MsmError", "MsmOpts", "FORM_STANDARD", "FORM_MONTGOMERY", "POINTS_PREPARED",
@@ -37,7 +39,7 @@ __all__ = [
     "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace", "EDWARDS", "GLV",
     "msm_points_prepared_bytes", "padd_chain", "fq_mul_batch_variant", "FQMUL_CIOS", "FQMUL_BARRETT",
     "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE", "FQMUL_CIOS_TWOPASS", "FQMUL_CIOS_DOUBLEROW", "PRECOMPUTED", "RADIX_SORT", "msm_points_precompute",
-    "msm_points_precomputed_bytes",
+    "msm_points_precomputed_bytes", "VALIDATE", "ENOTONCURVE", "ERANGE", "ResidentSet", "msm_points_validate",
 ]
 
 
@@ -154,11 +156,12 @@ def msm_points_prepare(points: torch.Tensor, out: torch.Tensor | None = None, st
 
 
 def _opts(c=0, signed=True, scalar_bits=0, prepared=False, stream=0, profile=False, edwards=False,
-          glv=False, precomputed=False, radix_sort=False) -> MsmOpts:
+          glv=False, precomputed=False, radix_sort=False, validate=False) -> MsmOpts:
     """stream=0 for size queries (no CUDA context needed); None = torch's current stream."""
     sv = 0 if (isinstance(stream, int) and stream == 0) else _s(stream).value
     flags = (POINTS_PREPARED if prepared else 0) | (PROFILE if profile else 0) | _model_flags(edwards, glv)
     flags |= (PRECOMPUTED if precomputed else 0) | (RADIX_SORT if radix_sort else 0)
+    flags |= VALIDATE if validate else 0
     return MsmOpts(int(c), 1 if signed else 0, int(scalar_bits), flags, sv)
 
 
@@ -206,7 +209,7 @@ def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None
            workspace: torch.Tensor | None = None, c: int = 0, signed: bool = True,
            scalar_bits: int = 0, prepared: bool = False, stream=None, profile: bool = False,
            edwards: bool = False, glv: bool = False, precomputed: bool = False,
-           radix_sort: bool = False) -> torch.Tensor:
+           radix_sort: bool = False, validate: bool = False) -> torch.Tensor:
     """Enqueues sum_i scalars_i * points_i; returns the (24,) int32 device tensor it writes.
     With prepared=True, points is msm_points_prepare(..., edwards=, glv=) output; with
     precomputed=True (Edwards, explicit c) msm_points_precompute output for the same options.
@@ -214,7 +217,7 @@ def msm_g1(points: torch.Tensor, scalars: torch.Tensor, out: torch.Tensor | None
     the workspace must be sized with the same choice)."""
     n = scalars.shape[0]
     o = _opts(c, signed, scalar_bits, prepared or precomputed, None if stream is None else stream, profile,
-              edwards, glv, precomputed, radix_sort)
+              edwards, glv, precomputed, radix_sort, validate)
     _check_points(points, n, prepared or precomputed, edwards, glv, o)
     if workspace is None:
         workspace = msm_g1_workspace(n, c, signed, scalar_bits, prepared or precomputed, points.device, edwards,
@@ -297,12 +300,13 @@ def msm_g1_status(workspace: torch.Tensor, stream=None) -> int:
 
 def msm_g1_host(points: np.ndarray, scalars: np.ndarray, workspace: torch.Tensor | None = None,
                 c: int = 0, signed: bool = True, scalar_bits: int = 0, stream=None, edwards: bool = False,
-                glv: bool = False) -> np.ndarray:
+                glv: bool = False, validate: bool = False) -> np.ndarray:
     """Synchronous MSM on host arrays (copies in and out inside the call)."""
     pts = np.ascontiguousarray(points, dtype=np.uint32)
     sc = np.ascontiguousarray(scalars, dtype=np.uint32)
     n = pts.shape[0]
-    o = _opts(c, signed, scalar_bits, False, None if stream is None else stream, edwards=edwards, glv=glv)
+    o = _opts(c, signed, scalar_bits, False, None if stream is None else stream, edwards=edwards, glv=glv,
+              validate=validate)
     need = lib().msm_g1_host_workspace_bytes(n, ctypes.byref(o))
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
@@ -347,3 +351,80 @@ def imad_probe(iters: int = 20000, stream=None) -> float:
     v = ctypes.c_double(0.0)
     check(lib().msm377_imad_probe(iters, ctypes.byref(v), _s(stream)))
     return v.value
+
+
+def msm_points_validate(points: torch.Tensor, edwards: bool = False, glv: bool = False, subgroup: bool = False,
+                        stream=None) -> int:
+    """0 if every (n, 24) standard-form point is on the curve (and in the order-r subgroup
+    when edwards, glv or subgroup asks for it), else ENOTONCURVE. Synchronous."""
+    _check_dev(points)
+    flags = _model_flags(edwards, glv) | (PRECOMPUTED if subgroup else 0)
+    rc = lib().msm_points_validate(_p(points), points.shape[0], flags, _s(stream))
+    if rc not in (OK, ENOTONCURVE):
+        check(rc)
+    return rc
+
+
+class ResidentSet:
+    """A resident point set owned by the library (msm_points_create / msm_points_destroy):
+    the stored form of n standard-form points for one curve model (Edwards, GLV, or a
+    fixed-base set for one window width c), reused by many msm() calls over slices."""
+
+    def __init__(self, points: torch.Tensor, edwards: bool = False, glv: bool = False, precompute_c: int = 0,
+                 scalar_bits: int = 0, signed: bool = True, validate: bool = False, stream=None):
+        _check_dev(points)
+        self.device = points.device
+        self.n = points.shape[0]
+        self.edwards, self.glv, self.c = edwards or precompute_c > 0, glv, precompute_c
+        self.scalar_bits, self.signed = scalar_bits, signed
+        o = _opts(precompute_c, signed, scalar_bits, False, None if stream is None else stream,
+                  edwards=self.edwards, glv=glv, precomputed=precompute_c > 0, validate=validate)
+        h = ctypes.c_void_p(0)
+        self._h = None
+        check(lib().msm_points_create(_p(points), self.n, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def data_ptr(self, offset: int = 0) -> int:
+        return int(lib().msm_points_data(self._h, offset) or 0)
+
+    def _opts(self, stream, profile=False, radix_sort=False) -> MsmOpts:
+        return _opts(0, self.signed, self.scalar_bits, True, stream, profile, self.edwards, self.glv, self.c > 0,
+                     radix_sort)
+
+    def workspace(self, n: int) -> torch.Tensor:
+        nbytes = lib().msm_g1_resident_workspace_bytes(self._h, n, ctypes.byref(self._opts(0)))
+        if nbytes == 0:
+            raise MsmError(EINVAL, "bad resident MSM options")
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def workspace_bytes(self, n: int) -> int:
+        return int(lib().msm_g1_resident_workspace_bytes(self._h, n, ctypes.byref(self._opts(0))))
+
+    def msm(self, scalars: torch.Tensor, offset: int = 0, out: torch.Tensor | None = None,
+            workspace: torch.Tensor | None = None, stream=None, profile: bool = False,
+            radix_sort: bool = False) -> torch.Tensor:
+        """Enqueues sum_i scalars_i P_{offset + i} over the set (msm_g1_resident)."""
+        n = scalars.shape[0]
+        if workspace is None:
+            workspace = self.workspace(n)
+        out = torch.empty(24, dtype=torch.int32, device=self.device) if out is None else out
+        _check_dev(scalars, out, workspace)
+        o = self._opts(None if stream is None else stream, profile, radix_sort)
+        check(lib().msm_g1_resident(self._h, offset, n, _p(scalars), _p(out), _p(workspace), workspace.numel(),
+                                    ctypes.byref(o)))
+        return out
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            check(lib().msm_points_destroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,6 +6,9 @@ into the library (msm_g1_set_window_table), so every later call with c = 0 --
 single, batched or served -- uses the measured choice. The library keeps one
 table per curve model / GLV combination; tune and install the one you run.
 Tables can be saved to and loaded from a JSON file keyed by the device name.
+
+One synthetic point set of the largest size tuned is generated on the device and
+prepared once per curve model; smaller sizes time a prefix of it.
 """
 from __future__ import annotations
 
@@ -20,18 +23,43 @@ from . import (PRECOMPUTED, _model_flags, g1_generator_mul, lib, msm_g1, msm_g1_
                msm_points_precompute, msm_points_prepare, to_device)
 from ._lib import check
 
+# variable-base window widths searched at large n (the BLS12-377 MSM configuration
+# of 2^20 and 2^22 points: c from 12 to 17)
+LARGE_C = tuple(range(12, 18))
+# fixed-base sets: every window adds into one bucket set, so wider windows pay
+PRECOMPUTED_C = tuple(range(15, 21))
+
+_SETS: dict = {}
+
+
+def _point_set(n: int, device, seed: int, edwards: bool, glv: bool):
+    """Stored points for n (a prefix of one cached set per model and device)."""
+    dev = torch.device(device)
+    key = (str(dev), seed, bool(edwards), bool(glv))
+    have = _SETS.get(key)
+    if have is None or have[0] < n:
+        import synth
+        std = g1_generator_mul(to_device(synth.scalars(seed, n), dev))
+        _SETS[key] = (n, std, msm_points_prepare(std, edwards=edwards, glv=glv))
+    _, std, prep = _SETS[key]
+    rows = prep.shape[0] // std.shape[0]
+    return std[:n], prep[:rows * n]
+
+
+def clear_cache() -> None:
+    _SETS.clear()
+
 
 def time_msm(n: int, c: int, reps: int = 3, device="cuda", seed: int = 11, edwards: bool = False,
              glv: bool = False, precomputed: bool = False) -> float:
     """Median milliseconds of one msm_g1 call with window c at size n (a precomputed
     set is built for each c, outside the timing)."""
     import synth
-    std = g1_generator_mul(to_device(synth.scalars(seed, n), device))
+    std, prep = _point_set(n, device, seed, edwards or precomputed, glv)
     if precomputed:
         pts = msm_points_precompute(std, c=c, scalar_bits=253, glv=glv)
     else:
-        pts = msm_points_prepare(std, edwards=edwards, glv=glv)
-    del std
+        pts = prep
     sc = to_device(synth.scalars(seed + 1, n), device)
     kw = dict(c=c, scalar_bits=253, prepared=True, edwards=edwards or precomputed, glv=glv,
               precomputed=precomputed)
@@ -46,17 +74,16 @@ def time_msm(n: int, c: int, reps: int = 3, device="cuda", seed: int = 11, edwar
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    del ws, pts
     return float(np.median(times))
 
 
 def candidates(log2n: int, glv: bool = False, precomputed: bool = False) -> list[int]:
-    """Around the built-in rule; 12..17 for the large sizes (13..18 with GLV: 2n points per window;
-    15..20 precomputed: all windows share one bucket set, so wider windows pay)."""
+    """Window widths to time at n = 2^log2n: 12..17 for the large sizes (15..20 for
+    fixed-base sets); around the built-in rule below 2^16."""
     if log2n >= 16:
-        if precomputed:
-            return list(range(15, 21))
-        return list(range(13, 19)) if glv else list(range(12, 18))
-    base = max(4, log2n - 4)
+        return list(PRECOMPUTED_C if precomputed else LARGE_C)
+    base = max(4, log2n - 4 + (1 if glv else 0))
     return sorted({max(3, base - 2), max(3, base - 1), base, base + 1, base + 2})
 
 

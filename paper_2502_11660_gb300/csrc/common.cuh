@@ -28,6 +28,12 @@ void note_launches(unsigned k);
 int profile_begin(cudaStream_t s);
 int profile_mark(cudaStream_t s);
 
+// Enqueues the check of n affine standard-form points (24 u32 each, 16-byte
+// aligned) on s: coordinates below p and on y^2 = x^3 + 1 ((0, 0) is O), and with
+// `subgroup` also r P = O. The first failing point stores MSM377_ENOTONCURVE into
+// *status (device memory) unless it already holds an error.
+int launch_validate(const uint32_t* points_std, size_t n, bool subgroup, int* status, cudaStream_t s);
+
 inline unsigned grid_for(size_t n, unsigned block) {
     return static_cast<unsigned>((n + block - 1) / block);
 }

@@ -644,7 +644,7 @@ __global__ void k_digits(const uint4* __restrict__ scalars, size_t n, int c, int
                          : (bits - lo_bit >= 32 ? 0u : ~((1u << (bits - lo_bit)) - 1u));
             over |= s[k] & m;
         }
-        if (over) atomicExch(status, MSM377_ERANGE);
+        if (over) atomicCAS(status, 0, MSM377_ERANGE);   // the first error of the call stays
     }
     if (!glv) {
         emit_digits(s, c, W, sgn, i, n, pre, keys, vals);
@@ -1582,12 +1582,19 @@ namespace {
 
 // Phase 1-3 of one MSM on stream s: status reset, preparation, digits, sort,
 // bucket reset. Fills `a` with the job's accumulation arguments.
+// reset_status = false: the caller has cleared the status word and the merge
+// counter already (msm_g1_host validates point chunks on a helper stream first).
 int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars, void* workspace,
-                 const msm_opts* opts, cudaStream_t s, AccArgs* a_out) {
+                 const msm_opts* opts, cudaStream_t s, AccArgs* a_out, bool reset_status = true) {
     const size_t n = p.n;
     int* status = at<int>(workspace, p.off_status);
-    MSM_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));  // status word, longest run of heads
+    if (reset_status)
+        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));  // status word, longest run of heads
     const uint4* pts = reinterpret_cast<const uint4*>(points);
+    if ((opts->flags & MSM377_VALIDATE) && !(opts->flags & MSM377_POINTS_PREPARED)) {
+        const int r = launch_validate(points, n, (opts->flags & (MSM377_EDWARDS | MSM377_GLV)) != 0, status, s);
+        if (r) return r;
+    }
     if (!(opts->flags & MSM377_POINTS_PREPARED)) {
         uint4* prep = at<uint4>(workspace, p.off_points);
         launch_prepare(pts, prep, n, opts->flags, s);
@@ -1784,6 +1791,9 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
         return set_error(MSM377_EINVAL, "msm_g1: workspace NULL or not 256-byte aligned");
     if (workspace_bytes < p.total)
         return set_error(MSM377_ENOMEM, "msm_g1: workspace %zu bytes, need %zu", workspace_bytes, p.total);
+    if ((opts->flags & MSM377_VALIDATE) && (opts->flags & MSM377_POINTS_PREPARED))
+        return set_error(MSM377_EINVAL, "msm_g1: MSM377_VALIDATE checks standard-form input points; stored "
+                         "(prepared) points are validated when the set is made (msm_points_create)");
     const bool prof = (opts->flags & MSM377_PROFILE) != 0;
     if (prof) {
         int pr = profile_begin(s);
@@ -1840,8 +1850,9 @@ extern "C" int msm_g1_batched(const msm_job* jobs, size_t njobs, void* workspace
     if (njobs == 0) return MSM377_OK;
     if (njobs > (size_t)kMaxBatch)
         return set_error(MSM377_EINVAL, "msm_g1_batched: %zu jobs, at most %d per call", njobs, kMaxBatch);
-    if (opts->flags & MSM377_PROFILE)
-        return set_error(MSM377_EINVAL, "msm_g1_batched: MSM377_PROFILE is not supported");
+    if (opts->flags & (MSM377_PROFILE | MSM377_VALIDATE))
+        return set_error(MSM377_EINVAL, "msm_g1_batched: MSM377_PROFILE and MSM377_VALIDATE are not supported "
+                         "(validate point sets once with msm_points_validate or msm_points_create)");
     Plan plans[kMaxBatch];
     size_t total = 0;
     if (!batch_plans(jobs, njobs, opts, plans, &total))
@@ -1921,6 +1932,9 @@ extern "C" int msm_g1_status(const void* workspace, const msm_opts* opts) {
     MSM_CUDA_TRY(cudaMemcpyAsync(&st, workspace, sizeof(int), cudaMemcpyDeviceToHost, s));
     MSM_CUDA_TRY(cudaStreamSynchronize(s));
     if (st == MSM377_ERANGE) return set_error(MSM377_ERANGE, "msm_g1: a scalar exceeds scalar_bits");
+    if (st == MSM377_ENOTONCURVE)
+        return set_error(MSM377_ENOTONCURVE, "msm_g1: an input point is not on the curve (or, with "
+                         "MSM377_EDWARDS / MSM377_GLV, not in the order-r subgroup)");
     return st;
 }
 
@@ -1966,6 +1980,7 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
     int r = device_aux(&aux);
     if (r) return r;
     cudaStream_t sc = aux->st[0], sp = aux->st[1];
+    MSM_CUDA_TRY(cudaMemsetAsync(at<int>(workspace, p.off_status), 0, 2 * sizeof(int), s));  // before the fork
     r = fork_from(aux, s, 2);
     if (r) return r;
     uint4* prep = at<uint4>(workspace, p.off_points);
@@ -1976,13 +1991,18 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
         MSM_CUDA_TRY(cudaMemcpyAsync(d_pts + 24 * a, points_host + 24 * a, (b - a) * 96, cudaMemcpyHostToDevice, sc));
         MSM_CUDA_TRY(cudaEventRecord(aux->chunk[k], sc));
         MSM_CUDA_TRY(cudaStreamWaitEvent(sp, aux->chunk[k], 0));
+        if (o.flags & MSM377_VALIDATE) {
+            r = launch_validate(d_pts + 24 * a, b - a, (o.flags & (MSM377_EDWARDS | MSM377_GLV)) != 0,
+                                at<int>(workspace, p.off_status), sp);
+            if (r) return r;
+        }
         launch_prepare_range(reinterpret_cast<const uint4*>(d_pts), prep, n, a, b, o.flags, sp);
     }
     MSM_CUDA_TRY(cudaMemcpyAsync(d_sc, scalars_host, n * 32, cudaMemcpyHostToDevice, s));
     msm_opts op = o;
     op.flags |= MSM377_POINTS_PREPARED;  // the plan above keeps the prepared region in the workspace
     AccArgs acc;
-    r = enqueue_head(p, reinterpret_cast<const uint32_t*>(prep), d_sc, workspace, &op, s, &acc);
+    r = enqueue_head(p, reinterpret_cast<const uint32_t*>(prep), d_sc, workspace, &op, s, &acc, false);
     if (r) return r;
     r = join_into(aux, s, 2);
     if (r) return r;

@@ -5,8 +5,12 @@
 // The array is a file-scope __device__ variable: every GPU on which this module
 // is loaded holds MSM377_NOALLOC_SCRATCH_BYTES of it until the process exits.
 // In host code its name is only a host-side stand-in, never a device address,
-// so the address is looked up once per device with cudaGetSymbolAddress (the
-// first call on a device does that lookup) and cached.
+// so the address is looked up with cudaGetSymbolAddress, once per device and CUDA
+// context, by the first call made there, and cached together with that context.
+// A module's globals live in each context that loads the module: a call made from
+// another context (a driver-API context, or the primary context re-created after
+// cudaDeviceReset) looks the address up again instead of using a stale one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -18,7 +22,29 @@ static __device__ __align__(256) unsigned char g_msm_noalloc_scratch[MSM377_NOAL
 namespace {
 constexpr int kMaxDevices = 256;
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct Scratch {
+    CUcontext ctx = nullptr;  // context the address belongs to
+    void* ptr = nullptr;
+};
+Scratch g_scratch[kMaxDevices];
+
+// cuCtxGetCurrent through the runtime's driver entry-point lookup (no link
+// dependency on the driver library).
+typedef CUresult (*CtxGetCurrent)(CUcontext*);
+CtxGetCurrent g_ctx_get = nullptr;
+
+int current_context(CUcontext* ctx) {
+    if (!g_ctx_get) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return msm377::set_error(MSM377_ECUDA, "msm_g1_noalloc: cuCtxGetCurrent not available");
+        g_ctx_get = reinterpret_cast<CtxGetCurrent>(fn);
+    }
+    if (g_ctx_get(ctx) != CUDA_SUCCESS) return msm377::set_error(MSM377_ECUDA, "msm_g1_noalloc: cuCtxGetCurrent failed");
+    return MSM377_OK;
+}
 }  // namespace
 
 using namespace msm377;
@@ -26,8 +52,9 @@ using namespace msm377;
 extern "C" int msm_g1_noalloc(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out,
                               const msm_opts* opts) {
     if (!opts) return set_error(MSM377_EINVAL, "msm_g1_noalloc: opts is NULL");
-    if (opts->flags & MSM377_PROFILE)
-        return set_error(MSM377_EINVAL, "msm_g1_noalloc: MSM377_PROFILE is not available on this entry point");
+    if (opts->flags & (MSM377_PROFILE | MSM377_VALIDATE))
+        return set_error(MSM377_EINVAL, "msm_g1_noalloc: MSM377_PROFILE and MSM377_VALIDATE are not available on "
+                         "this entry point (it reports no device status)");
     const size_t need = msm_g1_workspace_bytes(n, opts);
     if (need == 0)
         return set_error(MSM377_EINVAL, "msm_g1_noalloc: bad options (c=%d scalar_bits=%d) or n too large",
@@ -44,14 +71,23 @@ extern "C" int msm_g1_noalloc(const uint32_t* points, const uint32_t* scalars, s
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_ptr[dev]) {
+        CUcontext ctx = nullptr;
+        int r = current_context(&ctx);
+        if (r) return r;
+        Scratch& sc = g_scratch[dev];
+        if (!sc.ptr || !ctx || ctx != sc.ctx) {
+            // set-up for this device and context (the lookup also makes the
+            // device's primary context current when no context is yet)
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_msm_noalloc_scratch);
             if (e != cudaSuccess)
                 return set_error(MSM377_ECUDA, "msm_g1_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            g_scratch_ptr[dev] = p;
+            r = current_context(&ctx);
+            if (r) return r;
+            sc.ctx = ctx;
+            sc.ptr = p;
         }
-        scratch = g_scratch_ptr[dev];
+        scratch = sc.ptr;
     }
     return msm_g1(points, scalars, n, out, scratch, (size_t)MSM377_NOALLOC_SCRATCH_BYTES, opts);
 }

@@ -3,8 +3,8 @@
 Requests name a resident point set, an offset into it and a length n; each
 brings fresh scalars. The host loop admits arrived requests while a slot (a CUDA
 stream) is free and the HBM footprint of everything in flight (workspace +
-scalars) stays within a budget, enqueues msm_g1 on the slot's stream over the
-resident prepared points, and retires requests whose completion event has
+scalars) stays within a budget, enqueues msm_g1_resident on the slot's stream over
+the resident set, and retires requests whose completion event has
 fired. Requests that arrive while others run are admitted as soon as a slot and
 memory free up, so their work overlaps on the device. Latency is measured from
 a request's arrival to the host seeing its completion event.
@@ -23,8 +23,7 @@ import time
 import numpy as np
 import torch
 
-from . import (msm_g1, msm_g1_workspace, msm_points_precompute, msm_points_prepare, g1_generator_mul,
-               to_device, to_host)
+from . import ResidentSet, g1_generator_mul, to_device, to_host
 
 
 @dataclasses.dataclass
@@ -55,64 +54,55 @@ def device_scalars(n: int, seed: int, device) -> torch.Tensor:
 
 
 class ResidentSets:
-    """Resident point sets P_i = s_i G in prepared form on the device (XYZZ Montgomery
-    affine, or the Edwards stored form; with GLV interleaved with phi(P_i))."""
+    """Resident point sets P_i = s_i G held by the library (msm_points_create): the
+    stored form for one curve model (XYZZ Montgomery affine, or the Edwards stored form;
+    with GLV interleaved with phi(P_i); or fixed-base copies for one window width)."""
 
     def __init__(self, seeds: list[np.ndarray], device="cuda", edwards: bool = False, glv: bool = False,
-                 precompute_c: int = 0):
+                 precompute_c: int = 0, validate: bool = False):
         """precompute_c > 0: fixed-base sets (Edwards, 2^(c j) P_i for every window j) made for
         that window width, which every request then uses."""
         self.edwards, self.glv, self.c = edwards or precompute_c > 0, glv, precompute_c
-        self.sets = []
+        self.sets: list[ResidentSet] = []
         for s in seeds:
             pts = g1_generator_mul(to_device(s, device))
-            if precompute_c:
-                self.sets.append(msm_points_precompute(pts, c=precompute_c, scalar_bits=253, glv=glv))
-            else:
-                self.sets.append(msm_points_prepare(pts, edwards=edwards, glv=glv))
+            self.sets.append(ResidentSet(pts, edwards=edwards, glv=glv, precompute_c=precompute_c,
+                                         scalar_bits=253, validate=validate))
             del pts
         torch.cuda.synchronize(device)
-        n0 = seeds[0].shape[0] if seeds else 0
-        self.rows_per_point = (self.sets[0].shape[0] // n0) if (seeds and n0) else 1
 
-    def slice(self, set_id: int, offset: int, n: int) -> torch.Tensor:
-        # stored rows are point-major (GLV halves and precomputed windows of a point are adjacent)
-        r = self.rows_per_point
-        return self.sets[set_id][r * offset:r * (offset + n)]
+    def set(self, set_id: int) -> ResidentSet:
+        return self.sets[set_id]
+
+    def close(self) -> None:
+        for s in self.sets:
+            s.close()
+        self.sets = []
 
 
 class MsmServer:
-    def __init__(self, sets: ResidentSets, slots: int = 8, mem_budget: int | None = None, c: int = 0,
-                 device="cuda"):
+    def __init__(self, sets: ResidentSets, slots: int = 8, mem_budget: int | None = None, device="cuda"):
         self.sets = sets
-        if sets.c:
-            c = sets.c          # precomputed sets fix the window width
         self.device = torch.device(device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
         if mem_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             mem_budget = int(free * 0.5)
         self.mem_budget = mem_budget
-        self.c = c
 
     def footprint(self, n: int) -> int:
-        from . import _opts, lib
-        import ctypes
-        o = _opts(self.c, True, 253, True, edwards=self.sets.edwards, glv=self.sets.glv,
-                  precomputed=self.sets.c > 0)
-        return int(lib().msm_g1_workspace_bytes(n, ctypes.byref(o))) + 32 * n + 96
+        """Device bytes a request of n points holds while in flight: its workspace, its
+        scalars and its result."""
+        return self.sets.set(0).workspace_bytes(n) + 32 * n + 96
 
     def _launch(self, req: Request, slot: int):
         st = self.streams[slot]
         with torch.cuda.stream(st):
             sc = device_scalars(req.n, req.seed, self.device)
-            ed, gl, pre = self.sets.edwards, self.sets.glv, self.sets.c > 0
-            ws = msm_g1_workspace(req.n, c=self.c, scalar_bits=253, prepared=True, device=self.device,
-                                  edwards=ed, glv=gl, precomputed=pre)
+            rs = self.sets.set(req.set_id)
+            ws = rs.workspace(req.n)
             out = torch.empty(24, dtype=torch.int32, device=self.device)
-            pts = self.sets.slice(req.set_id, req.offset, req.n)
-            msm_g1(pts, sc, out=out, workspace=ws, c=self.c, scalar_bits=253, prepared=True, stream=st,
-                   edwards=ed, glv=gl, precomputed=pre)
+            rs.msm(sc, offset=req.offset, out=out, workspace=ws, stream=st)
             ev = torch.cuda.Event()
             ev.record(st)
         return {"req": req, "slot": slot, "event": ev, "out": out, "tensors": (sc, ws),

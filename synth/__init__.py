@@ -157,12 +157,18 @@ class workloads:
         sa = scalars(stream_seed(tag, n, 5), n)
         sq = scalars(stream_seed(tag, n, 6), n)
         lam = field_elems(stream_seed(tag, n, 7), n)
+        return sa, sq, lam, workloads.padd_cases(n, tag, edge_rate)
+
+    @staticmethod
+    def padd_cases(n: int, tag: int, edge_rate: float = 0.01):
+        """The case code of each of n mixed additions: 0 generic, 1 Q = acc (doubling),
+        2 Q = -acc, 3 acc = O, 4 Q = O; each special case at `edge_rate`."""
         u = uniform01(stream_seed(tag, n, 8), n)
         case = np.zeros(n, dtype=np.int8)
         for k in range(4):
             lo, hi = k * edge_rate, (k + 1) * edge_rate
             case[(u >= lo) & (u < hi)] = k + 1
-        return sa, sq, lam, case
+        return case
 
     @staticmethod
     def batch_sizes(njobs: int = 64, lo_log2: float = 10.0, hi_log2: float = 20.0, tag: int = 3):

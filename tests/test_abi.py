@@ -12,13 +12,16 @@ HEADER = os.path.join(ROOT, "include", "msm377.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"^\s*(?:int|size_t|void)\s+\**\s*([a-z_0-9]+)\s*\(", text, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|size_t|void|uint32_t|uint64_t)\s+\**\s*([a-z_0-9]+)\s*\(",
+                       text, flags=re.M)
     return sorted(set(names))
 
 
 def test_header_declares_the_named_calls():
     names = declared_functions()
-    for required in ("fq_mul_batch", "padd_batch", "msm_g1", "msm_g1_workspace_bytes"):
+    for required in ("fq_mul_batch", "padd_batch", "msm_g1", "msm_g1_workspace_bytes", "msm_g1_batched",
+                     "msm_points_create", "msm_points_destroy", "msm_g1_resident", "msm_points_validate",
+                     "msm_points_data", "msm377_launch_count"):
         assert required in names
 
 
@@ -189,3 +192,46 @@ def test_precomputed_options():
     assert L.msm_g1_workspace_bytes(n, ctypes.byref(o2)) == 0
     assert L.msm_points_precompute(None, n, None, ctypes.byref(pkg._opts(c=0, edwards=True,
                                                                           precomputed=True))) == -1
+
+
+def test_resident_and_validation_calls_reject_bad_arguments_on_the_host():
+    import paper_2502_11660_gb300 as pkg
+    L = pkg.lib()
+    h = ctypes.c_void_p(0)
+    assert L.msm_points_create(None, 10, None, ctypes.byref(h)) == pkg.EINVAL
+    assert L.msm_points_create(None, 10, ctypes.byref(pkg._opts()), ctypes.byref(h)) == pkg.EINVAL
+    assert not h.value
+    bad = pkg._opts(edwards=True, precomputed=True)          # fixed-base sets need an explicit c
+    assert L.msm_points_create(ctypes.c_void_p(256), 10, ctypes.byref(bad), ctypes.byref(h)) == pkg.EINVAL
+    flags = pkg._opts(profile=True)                          # not a set property
+    assert L.msm_points_create(ctypes.c_void_p(256), 10, ctypes.byref(flags), ctypes.byref(h)) == pkg.EINVAL
+    assert L.msm_points_destroy(None) == 0
+    assert L.msm_points_count(None) == 0
+    assert not L.msm_points_data(None, 0)
+    assert L.msm_g1_resident_workspace_bytes(None, 10, ctypes.byref(pkg._opts())) == 0
+    assert L.msm_g1_resident(None, 0, 10, None, None, None, 0, ctypes.byref(pkg._opts())) == pkg.EINVAL
+    assert L.msm_points_validate(None, 10, 1 << 12, None) == pkg.EINVAL
+    assert L.msm_points_validate(None, 0, 0, None) == 0     # nothing to check
+    # stored points cannot be validated by msm_g1 (their sets are checked when made)
+    o = pkg._opts(c=8, prepared=True, validate=True)
+    ws = L.msm_g1_workspace_bytes(10, ctypes.byref(o))
+    rc = L.msm_g1(ctypes.c_void_p(256), ctypes.c_void_p(256), 10, ctypes.c_void_p(256), ctypes.c_void_p(256), ws,
+                  ctypes.byref(o))
+    assert rc == pkg.EINVAL and "VALIDATE" in pkg.last_error()
+    assert L.msm_g1_noalloc(None, None, 10, None, ctypes.byref(pkg._opts(validate=True))) == pkg.EINVAL
+
+
+def test_status_codes_and_validation_constant_match():
+    """The header's status codes are the binding's, and the validation kernel's r is the
+    oracle's group order."""
+    import paper_2502_11660_gb300 as pkg
+    from oracle import fq
+    text = open(HEADER).read()
+    for name in ("EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "ENOTONCURVE", "ERANGE"):
+        m = re.search(r"#define MSM377_%s \((-\d+)\)" % name, text)
+        assert m and int(m.group(1)) == getattr(pkg, name), name
+    assert int(re.search(r"#define MSM377_VALIDATE (\d+)u", text).group(1)) == pkg.VALIDATE
+    src = open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", "resident.cu")).read()
+    body = re.search(r"kOrderR\[8\] = \{([^}]*)\}", src).group(1)
+    words = [int(w.strip().rstrip("u"), 16) for w in body.split(",")]
+    assert sum(w << (32 * k) for k, w in enumerate(words)) == fq.R

@@ -95,7 +95,7 @@ def test_prepared_host_and_range_check(edw, split):
     ws = pkg.msm_g1_workspace(n, c=5, scalar_bits=253, edwards=edw, glv=split)
     pkg.msm_g1(pkg.to_device(pts), pkg.to_device(bad), workspace=ws, c=5, scalar_bits=253, edwards=edw,
                glv=split)
-    assert pkg.msm_g1_status(ws) == -5
+    assert pkg.msm_g1_status(ws) == pkg.ERANGE
 
 
 def _mont_ints(block: np.ndarray) -> list[int]:
@@ -127,6 +127,62 @@ def test_stored_forms_match_the_oracle_maps():
         assert _mont_ints(both[2 * i].reshape(3, 12)) == want
         assert _mont_ints(both[2 * i + 1].reshape(3, 12)) == list(
             edwards.stored_point(edwards.from_weierstrass(ph)))
+
+
+# ---------------------------------------------------------------- full sizes, every window the
+# autotuner may pick (variable base: 12..17; fixed base: 15..20)
+
+ALL_MODES = [(False, False), (True, False), (False, True), (True, True)]
+ALL_IDS = ["xyzz", "edwards", "glv", "edwards+glv"]
+_SETS: dict = {}
+
+
+def _resident(n, tag, edw, split):
+    """Prepared device set and the closed form for the 2^n workload (cached per mode)."""
+    a, s, pts = msm_inputs(n, tag)
+    want = closed_form_limbs(s, a, key=("full", n, tag))
+    key = (n, tag, edw, split)
+    if key not in _SETS:
+        _SETS.clear()
+        _SETS[key] = pkg.msm_points_prepare(pkg.to_device(pts), edwards=edw, glv=split)
+    return _SETS[key], pkg.to_device(a), want
+
+
+@pytest.mark.parametrize("c", list(range(12, 18)))
+@pytest.mark.parametrize("edw,split", ALL_MODES, ids=ALL_IDS)
+def test_full_size_2e20_every_tuned_c(edw, split, c):
+    n = 1 << 20
+    prep, da, want = _resident(n, 2, edw, split)
+    ws = pkg.msm_g1_workspace(n, c=c, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+    out = pkg.msm_g1(prep, da, workspace=ws, c=c, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == want
+    assert pkg.msm_g1_status(ws) == 0
+
+
+@pytest.mark.parametrize("edw,split,c", [(True, True, 15), (True, True, 16), (True, True, 17),
+                                         (False, False, 16), (False, False, 17), (True, False, 16),
+                                         (False, True, 16)])
+def test_full_size_2e22_tuned_c(edw, split, c):
+    n = 1 << 22
+    prep, da, want = _resident(n, 2, edw, split)
+    out = pkg.msm_g1(prep, da, c=c, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == want
+
+
+@pytest.mark.parametrize("c", list(range(15, 21)))
+@pytest.mark.parametrize("split", [False, True], ids=["plain", "glv"])
+def test_precomputed_full_size_2e20_every_tuned_c(split, c):
+    n = 1 << 20
+    a, s, pts = msm_inputs(n, tag=2)
+    want = closed_form_limbs(s, a, key=("full", n, 2))
+    pre = pkg.msm_points_precompute(pkg.to_device(pts), c=c, scalar_bits=253, glv=split)
+    out = pkg.msm_g1(pre, pkg.to_device(a), c=c, scalar_bits=253, edwards=True, glv=split, precomputed=True)
+    torch.cuda.synchronize()
+    assert g1.from_limbs(pkg.to_host(out)) == want
+    del pre
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("edw,split", MODES, ids=MODE_IDS)

@@ -123,7 +123,7 @@ def test_scalar_bits_violation_is_reported():
     a[3, 7] = 0x80000000    # bit 255 set, above scalar_bits = 253
     ws = pkg.msm_g1_workspace(n, c=5, scalar_bits=253)
     pkg.msm_g1(pkg.to_device(pts), pkg.to_device(a), workspace=ws, c=5, scalar_bits=253)
-    assert pkg.msm_g1_status(ws) == -5
+    assert pkg.msm_g1_status(ws) == pkg.ERANGE
 
 
 def test_prepared_points_and_host_api_agree():

@@ -3,6 +3,7 @@ import random
 
 import numpy as np
 import pytest
+import torch
 
 import synth
 from oracle import fq, g1
@@ -92,3 +93,44 @@ def test_padd_two_torsion_and_identities():
     q = np.stack([soa_of_ints([0 if b is None else b[c] for _, b in cases]) for c in range(2)])
     res = pkg.to_host(pkg.padd_batch(pkg.to_device(acc), pkg.to_device(q)))
     _check(res, [g1.add(a, b) for a, b in cases])
+
+
+def test_padd_full_size_2e24_sampled_with_edge_cases():
+    """2^24 mixed additions in one call, the size the bench times (every thread runs many
+    grid-stride rounds), with 1 % each of P + P, P + (-P), acc = O and Q = O; sampled
+    rows, every special case among them, against the chord/tangent rule. Operands come
+    from oracle pools: affine points, their negations and XYZZ representatives in a
+    random scaling (l^2 x, l^3 y, l^2, l^3)."""
+    n, m = 1 << 24, 4096
+    pool = oracle_points(synth.scalars(synth.stream_seed(24, m, 1), m), key=("padd_pool", m))
+    lam = synth.field_elems(synth.stream_seed(24, m, 2), m)
+    pts = [g1.from_limbs(pool[j]) for j in range(m)]
+    accs = [_scaled(P, synth.limbs_to_int(lam[j]) or 1) for j, P in enumerate(pts)]
+    acc_pool = np.stack([soa_of_ints([a[c] for a in accs]) for c in range(4)])       # (4, 12, m)
+    neg = np.array([g1.to_limbs(g1.neg(P)) for P in pts], dtype=np.uint32)
+    q_pool = np.concatenate([pool, neg])                                              # (2m, 24)
+    case = synth.workloads.padd_cases(n, tag=24, edge_rate=0.01)
+    ia = synth.small_ints(synth.stream_seed(24, n, 3), n, m).astype(np.int64)
+    iq = synth.small_ints(synth.stream_seed(24, n, 4), n, m).astype(np.int64)
+    iq = np.where(case == 1, ia, iq)
+    iq = np.where(case == 2, ia + m, iq)
+    dia, diq = torch.from_numpy(ia).cuda(), torch.from_numpy(iq).cuda()
+    dcase = torch.from_numpy(case).cuda()
+    acc = pkg.to_device(acc_pool)[:, :, dia]
+    Q = pkg.to_device(q_pool)[diq]
+    q = torch.stack([Q[:, :12].T.contiguous(), Q[:, 12:].T.contiguous()])
+    del Q
+    acc[:, :, dcase == 3] = 0
+    q[:, :, dcase == 4] = 0
+    out = pkg.padd_batch(acc, q)
+    torch.cuda.synchronize()
+    rng = random.Random(24)
+    rows = sorted(set(rng.sample(range(n), 3000)) |
+                  {int(i) for k in (1, 2, 3, 4) for i in np.nonzero(case == k)[0][:200]})
+    sub = pkg.to_host(out[:, :, torch.tensor(rows, device="cuda")].contiguous())
+    for col, i in enumerate(rows):
+        A = None if case[i] == 3 else pts[ia[i]]
+        Qi = None if case[i] == 4 else (pts[iq[i]] if iq[i] < m else g1.neg(pts[iq[i] - m]))
+        X, Y, ZZ, ZZZ = (synth.limbs_to_int(sub[c, :, col]) for c in range(4))
+        assert xyzz_to_affine_int(X, Y, ZZ, ZZZ) == g1.add(A, Qi), f"op {i} case {case[i]}"
+    assert {int(case[i]) for i in rows} == {0, 1, 2, 3, 4}

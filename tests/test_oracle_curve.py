@@ -119,3 +119,33 @@ def test_c_oracle_scalar_mul_and_generator_table():
     pts = coracle.gen_points(arr, nthreads=2)
     for s, row in zip(seeds, pts):
         assert g1.from_limbs(row) == g1.mul(s, g1.G)
+
+
+def test_c_oracle_padd_stream_matches_python_pairwise():
+    """orc_padd_stream (the CPU mixed-PADD task rate) adds pair i alone, for every i,
+    including P + P, P + (-P) and the identity in either slot."""
+    rows_a, rows_q, want = [], [], []
+    for k in range(40):
+        P, Q = rand_sub(), rand_sub()
+        pair = [(P, Q), (P, P), (P, g1.neg(P)), (None, Q), (P, None)][k % 5]
+        rows_a.append(_lim(pair[0]))
+        rows_q.append(_lim(pair[1]))
+        want.append(g1.add(*pair))
+    out = coracle.padd_stream(np.stack(rows_a), np.stack(rows_q))
+    assert [g1.from_limbs(r) for r in out] == want
+
+
+def test_closed_form_fast_dot_matches_term_by_term():
+    """The exact float64-chunked sum used for large closed forms equals the plain sum,
+    at extreme limb values and across a chunk boundary."""
+    import synth
+    from tests.util import dot_fast, dot_plain
+    n = (1 << 18) + 37
+    a = synth.scalars_full(5, n)
+    s = synth.scalars_full(6, n)
+    a[:100] = 0xFFFFFFFF
+    s[:100] = 0xFFFFFFFF
+    s[(1 << 18) - 3:(1 << 18) + 3] = 0xFFFFFFFF
+    idx = list(range(0, 200)) + list(range((1 << 18) - 50, (1 << 18) + 37))
+    assert dot_fast(a[idx], s[idx]) == dot_plain(a[idx], s[idx])
+    assert dot_fast(a, s) == dot_plain(a, s)

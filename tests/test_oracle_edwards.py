@@ -98,3 +98,18 @@ def test_stored_point_and_extended_form():
     X, Y, Z, T = ed.extended(Pe, z)
     assert T * Z % P == X * Y % P
     assert ed.from_extended((X, Y, Z, T)) == Pe
+
+
+def test_weierstrass_subgroup_membership():
+    """r P = O decides membership of the order-r subgroup: the generator, its multiples,
+    O and cofactor-cleared points are members; the 2-torsion point and a generic curve
+    point (order divisible by a cofactor prime) are not."""
+
+    assert ed.weierstrass_is_subgroup(g1.G)
+    assert ed.weierstrass_is_subgroup(g1.mul(123456789, g1.G))
+    assert ed.weierstrass_is_subgroup(None)
+    assert not ed.weierstrass_is_subgroup((fq.P - 1, 0))
+    Q = g1.random_point(0xC0FFEE)
+    assert g1.on_curve(Q)
+    assert not ed.weierstrass_is_subgroup(Q)
+    assert ed.weierstrass_is_subgroup(g1.mul(fq.COFACTOR, Q))
