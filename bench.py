@@ -758,7 +758,8 @@ def batch_ops(h, peak, hbm_peak):
     variants = {}
     for name, v in (("cios", pkg.FQMUL_CIOS), ("barrett", pkg.FQMUL_BARRETT),
                     ("karatsuba", pkg.FQMUL_KARATSUBA), ("carrysave", pkg.FQMUL_CARRYSAVE),
-                    ("cios_twopass", pkg.FQMUL_CIOS_TWOPASS), ("cios_doublerow", pkg.FQMUL_CIOS_DOUBLEROW)):
+                    ("cios_twopass", pkg.FQMUL_CIOS_TWOPASS), ("cios_doublerow", pkg.FQMUL_CIOS_DOUBLEROW),
+                    ("warp_per_product", pkg.FQMUL_WARP)):
         ms_v = timed(lambda v=v: pkg.fq_mul_batch_variant(mA, mB, v, out=out))
         variants[name] = {"ms_2^24": ms_v, "mul_per_s": n / (ms_v / 1e3)}
     del mA, mB, out
@@ -794,7 +795,8 @@ def latency_chain(h, pts_std, n=1 << 18):
     pkg, torch, dev, stream = h.pkg, h.torch, h.dev, h.stream
     src = pts_std[:n]
     res = {"n": n, "paper_context_us": {"AIE med-ind (VCK190)": 1.05, "VCK190 CPU (GMP)": 9.69}}
-    for name, edw, lanes in (("xyzz_1_lane", False, 1), ("edwards_1_lane", True, 1), ("edwards_4_lanes", True, 4)):
+    for name, edw, lanes in (("xyzz_1_lane", False, 1), ("edwards_1_lane", True, 1), ("edwards_4_lanes", True, 4),
+                             ("edwards_4_warps", True, 128)):
         st = pkg.msm_points_prepare(src, edwards=edw)
         out = torch.empty(24, dtype=torch.int32, device=dev)
         pkg.padd_chain(st[:1024], 1024, edwards=edw, lanes=lanes, out=out, stream=stream)

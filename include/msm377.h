@@ -91,6 +91,11 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
  *                          halves of the even- and odd-indexed limbs' products)
  *   MSM377_FQMUL_CIOS_DOUBLEROW a b 2^-384 mod p, the same product two rows and two
  *                          quotient digits per step (accumulators shift two limbs)
+ *   MSM377_FQMUL_WARP      a b 2^-384 mod p with one warp per product: lane j holds
+ *                          limb j, three column products (a b, the Montgomery
+ *                          quotient, its multiple of p) with warp-wide carry
+ *                          resolution; the low-latency form the MSM's window chains
+ *                          use. Operands may be any values below 8p here.
  * MSM377_EINVAL for another variant. */
 #define MSM377_FQMUL_CIOS 0
 #define MSM377_FQMUL_BARRETT 1
@@ -98,6 +103,7 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
 #define MSM377_FQMUL_CARRYSAVE 3
 #define MSM377_FQMUL_CIOS_TWOPASS 4
 #define MSM377_FQMUL_CIOS_DOUBLEROW 5
+#define MSM377_FQMUL_WARP 6
 int fq_mul_batch_variant(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, int variant,
                          void *stream);
 
@@ -381,9 +387,11 @@ int msm_g1_noalloc(const uint32_t *points, const uint32_t *scalars, size_t n, ui
  * for the previous one, so time / n is the latency of one PADD.
  * points: device, the stored form of msm_points_prepare_ex(points, n, ., flags)
  *   with flags = 0 (XYZZ model, Montgomery affine) or MSM377_EDWARDS (no GLV).
- * lanes: 1 (one thread performs every multiplication) or 4 (Edwards only: the
+ * lanes: 1 (one thread performs every multiplication), 4 (Edwards only: the
  *   independent multiplications of each addition run on four lanes of a warp, the
- *   analogue of the paper's multi-tile med-ind mapping).
+ *   analogue of the paper's multi-tile med-ind mapping) or 128 (Edwards only: four
+ *   warps, one product of each level per warp, every product spread over the 32
+ *   lanes of its warp).
  * out: device, 24 u32, affine standard form, (0, 0) for O. Asynchronous on stream.
  * MSM377_EINVAL for other flags or lanes. The Edwards model needs subgroup points. */
 int padd_chain(const uint32_t *points, size_t n, uint32_t *out, uint32_t flags, int lanes, void *stream);

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "wfq.cuh"
 #include "fq.cuh"
 
 namespace {
@@ -667,13 +668,29 @@ __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t*
     }
 }
 
+// One warp per product (the chains' latency form, wfq.cuh): lanes hold the limbs,
+// three column products and warp-wide carry resolution. Operands below 8p.
+__global__ void k_fq_mul_warp(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                              uint32_t* __restrict__ out, size_t n) {
+    wfq::Consts K;
+    wfq::init(K);
+    const int l = wfq::lane();
+    const size_t warps = (size_t)gridDim.x * (blockDim.x >> 5);
+    for (size_t i = blockIdx.x * (size_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const uint32_t x = l < 12 ? a[(size_t)l * n + i] : 0u;
+        const uint32_t y = l < 12 ? b[(size_t)l * n + i] : 0u;
+        const uint32_t r = wfq::canon(wfq::mul(x, y, K), K);
+        if (l < 12) out[(size_t)l * n + i] = r;
+    }
+}
+
 }  // namespace
 
 using namespace msm377;
 
 extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n, int variant,
                                     void* stream) {
-    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_CIOS_DOUBLEROW)
+    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_WARP)
         return set_error(MSM377_EINVAL, "fq_mul_batch_variant: unknown variant %d", variant);
     if (n == 0) return MSM377_OK;
     if (!a || !b || !out) return set_error(MSM377_EINVAL, "fq_mul_batch_variant: NULL pointer");
@@ -700,6 +717,12 @@ extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32
         case MSM377_FQMUL_CIOS_TWOPASS:
             k_fq_mul_variant<MSM377_FQMUL_CIOS_TWOPASS><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
             break;
+        case MSM377_FQMUL_WARP: {
+            size_t wb = (n + 3) / 4;   // four warps (products) per block
+            if (wb > cap * 4) wb = cap * 4;
+            k_fq_mul_warp<<<(unsigned)wb, 128, 0, s>>>(a, b, out, n);
+            break;
+        }
         default:
             k_fq_mul_variant<MSM377_FQMUL_CIOS_DOUBLEROW><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
     }

@@ -7,14 +7,16 @@
 // multiplication latencies per addition instead of seven).
 //
 // Variants (padd_chain): XYZZ on one thread (10 multiplications in sequence per
-// mixed addition, with the special-case branches), Edwards on one thread, and
-// Edwards on four lanes. Inputs are stored points (msm_points_prepare_ex), so the
-// timed kernel is the chain alone.
+// mixed addition, with the special-case branches), Edwards on one thread, Edwards
+// on four lanes, and Edwards on four warps (128 threads: each product of an
+// addition on its own warp and spread over that warp's lanes, wpt.cuh). Inputs are
+// stored points (msm_points_prepare_ex), so the timed kernel is the chain alone.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 #include "ec.cuh"
 #include "ed.cuh"
+#include "wpt.cuh"
 
 namespace {
 
@@ -104,6 +106,34 @@ __global__ void __launch_bounds__(32) k_chain_ed4(const uint4* __restrict__ pts,
     store_affine_std(out, A);
 }
 
+// Four warps per addition: level 1 {A, B, C} and level 2 {X3, Y3, T3, Z3} on one
+// warp each, every product spread over the lanes of its warp.
+__global__ void __launch_bounds__(128) k_chain_edw(const uint4* __restrict__ pts, size_t n, uint32_t* __restrict__ out) {
+    __shared__ uint32_t slots[wpt::kSlots * 12];
+    wpt::Group g;
+    wpt::init(g, slots);
+    wpt::ed_set_inf(g);
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(pts);
+    wpt::Operand next = {};
+    if (n) next = wpt::load_operand(p, 3);
+    for (size_t i = 0; i < n; ++i) {
+        const wpt::Operand q = next;    // the next point's loads overlap this addition
+        if (i + 1 < n) next = wpt::load_operand(p + 36 * (i + 1), 3);
+        wpt::ed_madd(g, q);
+    }
+    if (threadIdx.x != 0) return;
+    fe c[4];
+    wpt::read_acc(g, c);
+    ed::ext P;
+    P.X = c[0];
+    P.Y = c[1];
+    P.Z = c[2];
+    P.T = c[3];
+    affine A;
+    ed::to_weierstrass(A, P);
+    store_affine_std(out, A);
+}
+
 }  // namespace
 
 using namespace msm377;
@@ -111,16 +141,18 @@ using namespace msm377;
 extern "C" int padd_chain(const uint32_t* points, size_t n, uint32_t* out, uint32_t flags, int lanes, void* stream) {
     if (flags & ~(uint32_t)MSM377_EDWARDS)
         return set_error(MSM377_EINVAL, "padd_chain: flags 0x%x (0 or MSM377_EDWARDS)", flags);
-    if (lanes != 1 && lanes != 4)
-        return set_error(MSM377_EINVAL, "padd_chain: lanes = %d (1 or 4)", lanes);
-    if (lanes == 4 && !(flags & MSM377_EDWARDS))
-        return set_error(MSM377_EINVAL, "padd_chain: four lanes need the Edwards model");
+    if (lanes != 1 && lanes != 4 && lanes != 128)
+        return set_error(MSM377_EINVAL, "padd_chain: lanes = %d (1, 4 or 128)", lanes);
+    if (lanes != 1 && !(flags & MSM377_EDWARDS))
+        return set_error(MSM377_EINVAL, "padd_chain: %d lanes need the Edwards model", lanes);
     if (!out || (n && (!points || !aligned(points, 16))))
         return set_error(MSM377_EINVAL, "padd_chain: NULL or non-16-byte-aligned pointer");
     cudaStream_t s = as_stream(stream);
     const uint4* p = reinterpret_cast<const uint4*>(points);
     if (flags & MSM377_EDWARDS) {
-        if (lanes == 4)
+        if (lanes == 128)
+            k_chain_edw<<<1, 128, 0, s>>>(p, n, out);
+        else if (lanes == 4)
             k_chain_ed4<<<1, 32, 0, s>>>(p, n, out);
         else
             k_chain_ed1<<<1, 32, 0, s>>>(p, n, out);

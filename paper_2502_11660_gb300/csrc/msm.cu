@@ -40,6 +40,7 @@
 #include "common.cuh"
 #include "ec.cuh"
 #include "ed.cuh"
+#include "wpt.cuh"
 
 namespace {
 
@@ -145,6 +146,18 @@ struct ModelXyzz {
     static __device__ __forceinline__ void add4_mem(acc& P, const uint4* q, fe* sh, int l) {
         ec::add4(P, MemQ{q}, sh, l, true);
     }
+    // four-warp group operations (wpt.cuh)
+    static __device__ __forceinline__ void gset_inf(const wpt::Group& g) { wpt::xyzz_set_inf(g); }
+    static __device__ __forceinline__ void gdbl(const wpt::Group& g) { wpt::xyzz_dbl(g); }
+    static __device__ __forceinline__ void gadd(const wpt::Group& g, const wpt::Operand& q) { wpt::xyzz_add(g, q); }
+    static __device__ __forceinline__ void to_affine4(affine& A, const fe (&c)[4]) {
+        xyzz P;
+        P.X = c[0];
+        P.Y = c[1];
+        P.ZZ = c[2];
+        P.ZZZ = c[3];
+        ec::to_affine(A, P);
+    }
 };
 
 struct ModelEdwards {
@@ -185,6 +198,17 @@ struct ModelEdwards {
     static __device__ __forceinline__ void dbl4(acc& P, fe* sh, int l) { ed::dbl4(P, sh, l, true); }
     static __device__ __forceinline__ void add4_mem(acc& P, const uint4* q, fe* sh, int l) {
         ed::add4(P, MemQE{q}, sh, l, true);
+    }
+    static __device__ __forceinline__ void gset_inf(const wpt::Group& g) { wpt::ed_set_inf(g); }
+    static __device__ __forceinline__ void gdbl(const wpt::Group& g) { wpt::ed_dbl(g); }
+    static __device__ __forceinline__ void gadd(const wpt::Group& g, const wpt::Operand& q) { wpt::ed_add(g, q); }
+    static __device__ __forceinline__ void to_affine4(affine& A, const fe (&c)[4]) {
+        ed::ext P;
+        P.X = c[0];
+        P.Y = c[1];
+        P.Z = c[2];
+        P.T = c[3];
+        ed::to_weierstrass(A, P);
     }
 };
 
@@ -1214,85 +1238,60 @@ __global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restri
 
 // ---------------------------------------------------------------- stage 7
 
-// The two latency-bound chains with four lanes per point operation (dbl4 / add4 of
-// the model): each group of four lanes of a warp holds one accumulator; all 32
-// lanes take part (every __syncwarp is warp-wide).
-constexpr int kGroups = 8;  // groups of four lanes per warp
+// The two latency-bound chains run on one group of four warps per block: each
+// point operation's products are spread over the warps (one product per warp and
+// formula level) and each product over the lanes of its warp (wpt.cuh, wfq.cuh).
+// The next operand's loads are issued before the current operation, so they
+// overlap it.
 
-// Every group of the warp ends with acc = sum_{j < cnt} 2^(e j) X_j (X_j at
-// x + j * kXyzzVec). With 2^q groups of four lanes and r = ceil(cnt / 2^q) terms
-// each, group i forms T_i = sum_{j < r} 2^(e j) X_{ir+j} by Horner (e (r - 1)
-// doublings, r additions); then q rounds of a tree give sum_i 2^(e r i) T_i: in the
-// round of stride s group i + s doubles a copy of its partial e r s times and group
-// i (a multiple of 2s) adds it. The critical path is e (r 2^q - 1) doublings and
-// r + q additions (Horner alone: e (cnt - 1) and cnt); q is chosen to minimise its
-// multiplication depth. Every group runs the same operations (groups past 2^q work
-// on the identity and on copies), so every __syncwarp is warp-wide; group 0 holds
-// the result (the other groups' acc is not meaningful).
+// Block w: S_w = L sum_{k < logG} 2^k Z_k + Z_logG for window w, by Horner from the
+// top term.
 template <class M>
-__device__ __forceinline__ void weighted_sum4(typename M::acc& acc, const uint4* __restrict__ x, int cnt, int e,
-                                              fe (*sh)[4], uint4* pub, uint4* idn, int g, int l) {
-    if ((threadIdx.x & 31) == 0) {
-        typename M::acc id;
-        M::set_inf(id);
-        M::store(idn, id);
-    }
-    int q = 0, r = cnt, best = e * (cnt - 1) * M::kDblDepth + cnt * M::kAddDepth;
-    for (int qq = 1; (1 << qq) <= kGroups; ++qq) {
-        const int rr = (cnt + (1 << qq) - 1) >> qq;
-        const int cost = e * (rr * (1 << qq) - 1) * M::kDblDepth + (rr + qq) * M::kAddDepth;
-        if (cost < best) best = cost, q = qq, r = rr;
-    }
-    __syncwarp();
-    M::set_inf(acc);
-    for (int j = r - 1; j >= 0; --j) {
-        if (j < r - 1)
-            for (int t = 0; t < e; ++t) M::dbl4(acc, sh[g], l);
-        const int k = g * r + j;
-        M::add4_mem(acc, k < cnt ? x + (size_t)k * kXyzzVec : idn, sh[g], l);
-    }
-    for (int st = 1; st < (1 << q); st <<= 1) {
-        typename M::acc D = acc;
-        for (int t = 0; t < e * r * st; ++t) M::dbl4(D, sh[g], l);
-        if (l == 0) M::store(pub + g * kXyzzVec, D);
-        __syncwarp();
-        typename M::acc R = acc;
-        M::add4_mem(R, pub + ((g + st) & (kGroups - 1)) * kXyzzVec, sh[g], l);
-        if ((g & (2 * st - 1)) == 0) acc = R;
-        __syncwarp();  // every lane has read pub before the next round writes it
-    }
-}
-
-// Warp w: S_w = L sum_{k < logG} 2^k Z_k + Z_logG for window w.
-template <class M>
-__global__ void __launch_bounds__(32) k_window_horner4(const uint4* __restrict__ Z, int nwin, int logG, int log2L,
-                                                       uint4* __restrict__ S) {
-    __shared__ fe sh[kGroups][4];
-    __shared__ uint4 pub[kGroups * kXyzzVec];
-    __shared__ uint4 idn[kXyzzVec];
-    const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
+__global__ void __launch_bounds__(128) k_window_horner_w(const uint4* __restrict__ Z, int nwin, int logG, int log2L,
+                                                         uint4* __restrict__ S) {
+    __shared__ uint32_t slots[wpt::kSlots * 12];
+    wpt::Group g;
+    wpt::init(g, slots);
     const int w = blockIdx.x;
-    if (w >= nwin) return;  // whole warp
-    const uint4* z = Z + (size_t)w * (logG + 1) * kXyzzVec;
-    typename M::acc acc;
-    weighted_sum4<M>(acc, z, logG, 1, sh, pub, idn, g, l);
-    for (int t = 0; t < log2L; ++t) M::dbl4(acc, sh[g], l);
-    M::add4_mem(acc, z + (size_t)logG * kXyzzVec, sh[g], l);
-    if (lane == 0) M::store(S + (size_t)w * kXyzzVec, acc);
+    if (w >= nwin) return;  // whole block
+    const uint32_t* z = reinterpret_cast<const uint32_t*>(Z + (size_t)w * (logG + 1) * kXyzzVec);
+    constexpr size_t kWords = 4 * kXyzzVec;
+    M::gset_inf(g);
+    wpt::Operand next = wpt::load_operand(z + (size_t)(logG > 0 ? logG - 1 : logG) * kWords, 4);
+    for (int k = logG - 1; k >= 0; --k) {
+        const wpt::Operand q = next;   // Z_k
+        next = wpt::load_operand(z + (size_t)(k > 0 ? k - 1 : logG) * kWords, 4);
+        if (k < logG - 1) M::gdbl(g);
+        M::gadd(g, q);
+    }
+    for (int t = 0; t < log2L; ++t) M::gdbl(g);
+    M::gadd(g, next);                  // Z_logG
+    wpt::store_acc(g, reinterpret_cast<uint32_t*>(S + (size_t)w * kXyzzVec));
 }
 
-// sum_w 2^(c w) S_w, then the affine result in standard form (lane 0 writes it).
+// sum_w 2^(c w) S_w by Horner over the windows, then the affine result in standard
+// form (thread 0 writes it after the inversion).
 template <class M>
-__global__ void __launch_bounds__(32) k_chain4(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
-    __shared__ fe sh[kGroups][4];
-    __shared__ uint4 pub[kGroups * kXyzzVec];
-    __shared__ uint4 idn[kXyzzVec];
-    const int lane = threadIdx.x & 31, g = lane >> 2, l = lane & 3;
-    typename M::acc acc;
-    weighted_sum4<M>(acc, S, W, c, sh, pub, idn, g, l);
-    if (lane != 0) return;
+__global__ void __launch_bounds__(128) k_chain_w(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
+    __shared__ uint32_t slots[wpt::kSlots * 12];
+    wpt::Group g;
+    wpt::init(g, slots);
+    const uint32_t* s = reinterpret_cast<const uint32_t*>(S);
+    constexpr size_t kWords = 4 * kXyzzVec;
+    M::gset_inf(g);
+    wpt::Operand next = wpt::load_operand(s + (size_t)(W - 1) * kWords, 4);
+    for (int j = W - 1; j >= 0; --j) {
+        const wpt::Operand q = next;   // S_j
+        if (j > 0) next = wpt::load_operand(s + (size_t)(j - 1) * kWords, 4);
+        if (j < W - 1)
+            for (int t = 0; t < c; ++t) M::gdbl(g);
+        M::gadd(g, q);
+    }
+    if (threadIdx.x != 0) return;
+    fe acc[4];
+    wpt::read_acc(g, acc);
     affine A;
-    M::to_affine(A, acc);
+    M::to_affine4(A, acc);
     if (!ec::is_inf(A)) {
         fq::from_mont(A.x, A.x);
         fq::from_mont(A.y, A.y);
@@ -1701,8 +1700,8 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
         zout = tmp;
     }
     // 7. window combination and normalisation
-    k_window_horner4<M><<<(unsigned)p.W, 32, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
-    k_chain4<M><<<1, 32, 0, s>>>(S, p.W, p.c, out);
+    k_window_horner_w<M><<<(unsigned)p.W, 128, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
+    k_chain_w<M><<<1, 128, 0, s>>>(S, p.W, p.c, out);
     note_launches(2);
     return check_launch("msm tail");
 }

@@ -1,8 +1,8 @@
 """GPU parity of the alternative multiplications (fq_mul_batch_variant) vs Python
 integers: the paper's Barrett reduction (Sec. III-C; also checked against the
 oracle's own Barrett), the Karatsuba-top Montgomery product and the carry-save
-radix-2^24 Montgomery product and the two-pass-row CIOS product, all
-bit-exact and canonical."""
+radix-2^24 Montgomery product, the two-pass-row CIOS product and the one-warp-per-
+product form of the window chains, all bit-exact and canonical."""
 import random
 
 import pytest
@@ -24,6 +24,7 @@ VARIANTS = {
     "carrysave": (3, lambda x, y: x * y * RINV % fq.P),
     "cios_twopass": (4, lambda x, y: x * y * RINV % fq.P),
     "cios_doublerow": (5, lambda x, y: x * y * RINV % fq.P),
+    "warp": (6, lambda x, y: x * y * RINV % fq.P),
 }
 
 
@@ -56,3 +57,20 @@ def test_barrett_matches_the_papers_reduction_in_the_oracle():
 
 def test_unknown_variant_is_rejected():
     assert pkg.lib().fq_mul_batch_variant(None, None, None, 4, 9, None) == -1
+
+
+def test_warp_product_on_unreduced_operands_and_carry_runs():
+    """The warp form takes operands below 8p (the unreduced sums and differences of the
+    point formulas). Edge values make the carry resolution run through every lane:
+    all-ones limbs, 2^k - 1 and 2^k, multiples of p and 8p - 1."""
+    rng = random.Random(99)
+    edges = [0, 1, 2, fq.P - 1, fq.P, fq.P + 1, 2 * fq.P - 1, 2 * fq.P, 4 * fq.P - 1, 6 * fq.P + 3,
+             8 * fq.P - 1, (1 << 376) - 1, 1 << 376, (1 << 379) - 1, (1 << 32) - 1, (1 << 64) - 1,
+             int("ffffffff" * 11, 16), (1 << 352) - (1 << 32)]
+    edges = [e for e in edges if e < 8 * fq.P]
+    pairs = [(x, y) for x in edges for y in edges]
+    pairs += [(rng.randrange(8 * fq.P), rng.randrange(8 * fq.P)) for _ in range(5000)]
+    A = soa_of_ints([x for x, _ in pairs])
+    B = soa_of_ints([y for _, y in pairs])
+    got = ints_of_soa(pkg.to_host(pkg.fq_mul_batch_variant(pkg.to_device(A), pkg.to_device(B), 6)))
+    assert got == [x * y * RINV % fq.P for x, y in pairs]

@@ -1,7 +1,8 @@
 """GPU parity of the dependent-chain experiment (Sec. V-A): padd_chain sums a point
 stream strictly in order; the result must equal the closed form sum_i s_i G for
-P_i = s_i G, for the XYZZ model on one thread and the Edwards model on one and on
-four lanes, including repeated points (P + P) and cancelling pairs (P + (-P))."""
+P_i = s_i G, for the XYZZ model on one thread and the Edwards model on one lane,
+four lanes and four warps, including repeated points (P + P) and cancelling pairs
+(P + (-P))."""
 import numpy as np
 import pytest
 import torch
@@ -14,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 pkg = pytest.importorskip("paper_2502_11660_gb300")
 
-VARIANTS = [(False, 1), (True, 1), (True, 4)]
+VARIANTS = [(False, 1), (True, 1), (True, 4), (True, 128)]
 
 
 def _stream(n, tag):
@@ -33,7 +34,7 @@ def _want(seeds):
     return g1.mul(k, g1.G)
 
 
-@pytest.mark.parametrize("edwards,lanes", VARIANTS, ids=["xyzz-1", "edwards-1", "edwards-4"])
+@pytest.mark.parametrize("edwards,lanes", VARIANTS, ids=["xyzz-1", "edwards-1", "edwards-4", "edwards-128"])
 @pytest.mark.parametrize("n", [0, 1, 2, 3, 100, 4096])
 def test_chain_sum(edwards, lanes, n):
     seeds, pts = _stream(n, tag=31 + n)
@@ -48,5 +49,6 @@ def test_chain_rejects_bad_arguments():
     assert L.padd_chain(None, 0, None, 0, 1, None) == -1
     out = torch.empty(24, dtype=torch.int32, device="cuda")
     assert L.padd_chain(None, 0, out.data_ptr(), 0, 4, None) == -1          # four lanes need Edwards
+    assert L.padd_chain(None, 0, out.data_ptr(), 0, 128, None) == -1        # so do four warps
     assert L.padd_chain(None, 0, out.data_ptr(), pkg.GLV, 1, None) == -1
     assert L.padd_chain(None, 0, out.data_ptr(), pkg.EDWARDS, 3, None) == -1
