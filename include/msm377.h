@@ -207,6 +207,19 @@ int msm_g1_default_c(size_t n, int signed_digits, uint32_t flags);
  * the autotuner. */
 int msm_g1_set_window_table(const int32_t *c_by_log2n, int len, uint32_t flags);
 
+/* Installs one measured schedule entry for signed digits and n in [2^log2n, 2^(log2n+1))
+ * in the table of the mode named by flags (MSM377_EDWARDS / MSM377_GLV /
+ * MSM377_PRECOMPUTED): c (window width, used when opts.c == 0), chunk (items per
+ * accumulation thread, 2..256), sort (1 counting sort, 2 LSD radix sort) and
+ * reduce_log2 (log2 of the level-1 bucket-reduction threads, 8..20); 0 in a field
+ * keeps the built-in rule. Process-wide, like the window tables (written by the
+ * autotuner); workspace sizes depend on it, so install before sizing workspaces. */
+int msm_g1_set_schedule(uint32_t flags, int log2n, int c, int chunk, int sort, int reduce_log2);
+
+/* The schedule msm_g1 would use for n points with these options: out4 = {c, chunk,
+ * sort (1 counting, 2 radix), log2 of the level-1 reduction threads}. */
+int msm_g1_schedule(size_t n, const msm_opts *opts, int32_t *out4);
+
 /* Bytes of the stored form of n points for flags (a combination of MSM377_EDWARDS
  * and MSM377_GLV; 0 for other bits): XYZZ 96 per stored point, Edwards 144;
  * n stored points, or 2n with GLV, interleaved: P_0, phi(P_0), P_1, phi(P_1), ...

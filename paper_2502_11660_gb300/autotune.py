@@ -8,7 +8,9 @@ table per curve model / GLV combination; tune and install the one you run.
 Tables can be saved to and loaded from a JSON file keyed by the device name.
 
 One synthetic point set of the largest size tuned is generated on the device and
-prepared once per curve model; smaller sizes time a prefix of it.
+prepared once per curve model; smaller sizes time a prefix of it. tune_schedule()
+also searches, per size, the accumulation chunk size, the sort and the bucket
+reduction's parallelism (msm_g1_set_schedule), one coordinate at a time.
 """
 from __future__ import annotations
 
@@ -107,6 +109,83 @@ def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda", edwards: boo
                 table[k] = best[near]
     return {"table": table, "timings": timings, "device": torch.cuda.get_device_name(device),
             "edwards": edwards, "glv": glv, "precomputed": precomputed}
+
+
+def time_schedule(n: int, c: int, chunk: int, sort: int, reduce_log2: int, reps: int = 3, device="cuda",
+                  seed: int = 11, edwards: bool = False, glv: bool = False) -> float:
+    """Median milliseconds of msm_g1 at size n with one schedule entry installed for 2^floor(log2 n)."""
+    from . import msm_g1_set_schedule
+    k = int(np.log2(n))
+    msm_g1_set_schedule(k, c, chunk, sort, reduce_log2, edwards=edwards, glv=glv)
+    return time_msm(n, 0, reps, device, seed, edwards=edwards, glv=glv)
+
+
+# chunk sizes (items per accumulation thread), sorts (1 counting, 2 radix) and level-1
+# reduction thread counts searched after the window width
+CHUNKS = (0, 16, 32, 48, 96, 128)
+SORTS = (1, 2)
+REDUCE_LOG2 = (0, 13, 14, 16, 17)
+
+
+def tune_schedule(log2_sizes=range(10, 23), reps: int = 3, device="cuda", edwards: bool = False,
+                  glv: bool = False) -> dict:
+    """Per size: the window width c (candidates as in tune()), then, at that c, the chunk
+    size, the sort and the number of level-1 reduction threads, one coordinate at a
+    time (each step keeps the fastest value; 0 = the built-in rule). Installs every
+    entry as it goes and returns {"schedule": {k: (c, chunk, sort, reduce_log2)},
+    "ms": {k: {field: {value: ms}}}}."""
+    sched, ms = {}, {}
+    for k in log2_sizes:
+        n = 1 << k
+        cur = [0, 0, 0, 0]
+        rec = {}
+        t = {c: time_schedule(n, c, 0, 0, 0, reps, device, edwards=edwards, glv=glv)
+             for c in candidates(k, glv)}
+        cur[0] = min(t, key=t.get)
+        rec["c"] = t
+        for field, values in ((1, CHUNKS), (2, SORTS), (3, REDUCE_LOG2)):
+            t = {}
+            for v in values:
+                trial = list(cur)
+                trial[field] = v
+                t[v] = time_schedule(n, *trial, reps=reps, device=device, edwards=edwards, glv=glv)
+            cur[field] = min(t, key=t.get)
+            rec[("c", "chunk", "sort", "reduce_log2")[field]] = t
+        from . import msm_g1_set_schedule
+        msm_g1_set_schedule(k, *cur, edwards=edwards, glv=glv)
+        sched[k] = tuple(cur)
+        ms[k] = rec
+    return {"schedule": sched, "ms": ms, "device": torch.cuda.get_device_name(device), "edwards": edwards,
+            "glv": glv}
+
+
+def install_schedule(schedule: dict, edwards: bool = False, glv: bool = False) -> None:
+    from . import msm_g1_set_schedule
+    for k, entry in schedule.items():
+        msm_g1_set_schedule(int(k), *[int(x) for x in entry], edwards=edwards, glv=glv)
+
+
+def clear_schedule(edwards: bool = False, glv: bool = False, precomputed: bool = False) -> None:
+    from . import msm_g1_set_schedule
+    for k in range(32):
+        msm_g1_set_schedule(k, 0, 0, 0, 0, edwards=edwards, glv=glv, precomputed=precomputed)
+
+
+def save_schedule(result: dict, path: str) -> None:
+    with open(path, "w") as f:
+        json.dump({"device": result.get("device"), "edwards": result.get("edwards"), "glv": result.get("glv"),
+                   "schedule": {str(k): list(v) for k, v in result["schedule"].items()}}, f, indent=1)
+
+
+def load_schedule(path: str) -> dict | None:
+    """A saved schedule table, if it was measured on this device model."""
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    if torch.cuda.is_available() and rec.get("device") != torch.cuda.get_device_name():
+        return None
+    return rec
 
 
 def _flags(edwards: bool, glv: bool, precomputed: bool) -> int:

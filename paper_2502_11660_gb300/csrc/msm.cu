@@ -1336,10 +1336,13 @@ int ilog2(uint64_t v) {
     return r;
 }
 
-// Tuned window widths for signed digits by floor(log2 n) (0 = not tuned), one
-// table per mode (Edwards, GLV), set by msm_g1_set_window_table from a measured
-// table.
-std::atomic<int> g_ctable[8][32];
+// Tuned schedules for signed digits by floor(log2 n), one table per mode (Edwards,
+// GLV, fixed-base), set from measured tables by msm_g1_set_window_table (window
+// widths) and msm_g1_set_schedule (every field); 0 = the built-in rule.
+std::atomic<int> g_ctable[8][32];      // window width c
+std::atomic<int> g_ktable[8][32];      // items per accumulation chunk K
+std::atomic<int> g_sorttable[8][32];   // 1 counting sort, 2 LSD radix sort
+std::atomic<int> g_rtable[8][32];      // log2 of the level-1 reduction threads
 
 int table_mode(uint32_t flags) {
     return ((flags & MSM377_EDWARDS) ? 1 : 0) | ((flags & MSM377_GLV) ? 2 : 0) |
@@ -1394,7 +1397,12 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     // Measured on GB300: the counting sort (ranks taken in the counting pass, no
     // atomics in the scatter) beats the radix passes for every plan; the radix sort
     // stays available for comparison.
-    p->counting = (o->flags & MSM377_RADIX_SORT) ? 0 : 1;
+    const int lgn = n > 1 ? ilog2(n) : 0;
+    const int tmode = table_mode(o->flags);
+    const int tsort = (p->sgn && lgn < 32) ? g_sorttable[tmode][lgn].load(std::memory_order_relaxed) : 0;
+    const int tk = (p->sgn && lgn < 32) ? g_ktable[tmode][lgn].load(std::memory_order_relaxed) : 0;
+    const int tr = (p->sgn && lgn < 32) ? g_rtable[tmode][lgn].load(std::memory_order_relaxed) : 0;
+    p->counting = ((o->flags & MSM377_RADIX_SORT) || tsort == 2) ? 0 : 1;
     p->tiles = (items + kSortTile - 1) / kSortTile;
     // Chunks of K <= 64 items, one per thread, sized so that the chunks over all
     // windows fill whole waves of resident accumulation threads (152 SMs x 3 blocks
@@ -1406,6 +1414,7 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     size_t K = (total + waves * kWave - 1) / (waves * kWave);
     if (K < 2) K = 2;
     if (K > 64) K = 64;
+    if (tk > 0) K = (size_t)tk;        // measured choice (2..256)
     p->K = (int)K;
     p->cpw = (uint32_t)((items + K - 1) / K);
     if (p->cpw == 0) p->cpw = 1;
@@ -1416,7 +1425,8 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     // fewer segment sums for the bit-sum stage, but fewer threads for the running sums)
     uint64_t group_buckets = (uint64_t)p->W * p->Bp;
     uint32_t L = 2;
-    while (L < p->Bp && group_buckets / (2 * L) >= kReduceThreads) L <<= 1;
+    const uint64_t reduce_threads = tr > 0 ? (1ull << tr) : kReduceThreads;
+    while (L < p->Bp && group_buckets / (2 * L) >= reduce_threads) L <<= 1;
     if (L > p->Bp) L = p->Bp;
     p->L = L;
     p->G = p->Bp / L;
@@ -1515,6 +1525,33 @@ extern "C" int msm_g1_set_window_table(const int32_t* c_by_log2n, int len, uint3
     const int mode = table_mode(flags);
     for (int k = 0; k < 32; ++k)
         g_ctable[mode][k].store(k < len ? c_by_log2n[k] : 0, std::memory_order_relaxed);
+    return MSM377_OK;
+}
+
+extern "C" int msm_g1_set_schedule(uint32_t flags, int log2n, int c, int chunk, int sort, int reduce_log2) {
+    if (flags & ~(MSM377_EDWARDS | MSM377_GLV | MSM377_PRECOMPUTED))
+        return set_error(MSM377_EINVAL, "msm_g1_set_schedule: flags 0x%x (only EDWARDS, GLV and PRECOMPUTED)",
+                         flags);
+    if (log2n < 0 || log2n >= 32 || (c && (c < 2 || c > 20)) || (chunk && (chunk < 2 || chunk > 256)) ||
+        sort < 0 || sort > 2 || (reduce_log2 && (reduce_log2 < 8 || reduce_log2 > 20)))
+        return set_error(MSM377_EINVAL, "msm_g1_set_schedule: log2n %d c %d chunk %d sort %d reduce_log2 %d", log2n,
+                         c, chunk, sort, reduce_log2);
+    const int mode = table_mode(flags);
+    g_ctable[mode][log2n].store(c, std::memory_order_relaxed);
+    g_ktable[mode][log2n].store(chunk, std::memory_order_relaxed);
+    g_sorttable[mode][log2n].store(sort, std::memory_order_relaxed);
+    g_rtable[mode][log2n].store(reduce_log2, std::memory_order_relaxed);
+    return MSM377_OK;
+}
+
+extern "C" int msm_g1_schedule(size_t n, const msm_opts* opts, int32_t* out4) {
+    if (!opts || !out4) return set_error(MSM377_EINVAL, "msm_g1_schedule: NULL argument");
+    Plan p;
+    if (!make_plan(n, opts, &p)) return set_error(MSM377_EINVAL, "msm_g1_schedule: bad options");
+    out4[0] = p.c;
+    out4[1] = p.K;
+    out4[2] = p.counting ? 1 : 2;
+    out4[3] = ilog2((uint64_t)p.W * p.G);
     return MSM377_OK;
 }
 
