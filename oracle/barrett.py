@@ -7,6 +7,8 @@ Sec. III-C: a*b mod M by Barrett reduction in three multiplications:
   k = bitlen(M), mu = floor(2^(2k) / M), the "high parts" are shifts by k-1 and
   k+1 bits and the "low parts" are residues mod 2^(k+1).
 
+Sec. III-E: the looser reduction for operands in [0, 6M) (k = 378), below.
+
 Sec. III-B / III-D: a 377-bit integer is held as 16 elements of 25 bits packed
 into two 8-lane vectors; each element may grow to 26 bits. Coarse carry
 propagation runs two rounds of
@@ -36,6 +38,37 @@ def barrett_reduce_coarse(x: int, M: int) -> int:
     if r < 0:
         r += mod
     return r
+
+
+# Sec. III-E: with the fine reduction [0, 3M) -> [0, M) skipped after the first
+# multiplications and 3M added to differences, the operands of the final
+# multiplications lie in [0, 6M); a looser Barrett step with "a parameter k set to
+# 378" still brings the product into [0, 4M). Reading: the step above with the bit
+# length k = 378 in place of bitlen(M) = 377.
+LOOSE_K = 378
+
+
+def barrett_reduce_loose(x: int, M: int, k: int = LOOSE_K) -> int:
+    """q1 = floor(x / 2^(k-1)), mu = floor(2^(2k) / M), q3 = floor(q1 mu / 2^(k+1)),
+    r = (x - q3 M) mod 2^(k+1), no correction step."""
+    mu = (1 << (2 * k)) // M
+    q3 = ((x >> (k - 1)) * mu) >> (k + 1)
+    mod = 1 << (k + 1)
+    return ((x % mod) - (q3 * M) % mod) % mod
+
+
+def loose_bound(M: int, xmax: int, k: int = LOOSE_K):
+    """A bound B with x - q3 M < B M for 0 <= x < xmax, as an exact fraction.
+
+    With q1 = x / 2^(k-1) - e1 and mu = 2^(2k) / M - e2 (e1 in [0, 1), e2 the fixed
+    fractional part of 2^(2k) / M), x / M - q1 mu / 2^(k+1) = e2 x / 2^(2k)
+    + e1 2^(k-1) / M - e1 e2 / 2^(k+1) <= e2 x / 2^(2k) + 2^(k-1) / M, and the floor
+    of q3 adds less than 1: B = 1 + e2 xmax / 2^(2k) + 2^(k-1) / M. Also
+    x - q3 M >= 0, since q3 <= x / M. When B M <= 2^(k+1) the remainder taken
+    mod 2^(k+1) is the exact x - q3 M."""
+    from fractions import Fraction
+    e2 = Fraction(1 << (2 * k), M) - ((1 << (2 * k)) // M)
+    return 1 + e2 * Fraction(xmax, 1 << (2 * k)) + Fraction(1 << (k - 1), M)
 
 
 def barrett_mulmod(a: int, b: int, M: int) -> int:

@@ -148,3 +148,37 @@ def test_elements_roundtrip():
         e = barrett.to_elems(v, FACTS["elements"])
         assert all(0 <= x < (1 << 25) for x in e)
         assert barrett.from_elems(e) == v
+
+
+def test_loose_barrett_sec_III_E():
+    """The looser reduction: operands below 6M, k = 378, remainder in [0, 4M) (Sec. III-E).
+    The bound is proven for BLS12-377's p (exact fraction), then checked on random
+    products, on the largest product and on products whose dropped low bits are all
+    ones (the worst case of the first truncation)."""
+    M = fq.P
+    k, lo_in, lo_out = FACTS["loose_k"], FACTS["loose_input_range"], FACTS["loose_output_range"]
+    assert barrett.LOOSE_K == k
+    xmax = (lo_in * M) ** 2
+    B = barrett.loose_bound(M, xmax, k)
+    assert B < lo_out                          # x - q3 M < 4M for every x < (6M)^2 ...
+    assert lo_out * M <= 1 << (k + 1)          # ... so the residue mod 2^(k+1) is exact
+    rng = random.Random(12)
+    xs = [0, 1, M - 1, M, xmax - 1, (lo_in * M - 1) ** 2, (lo_in * M - 1) * (3 * M)]
+    xs += [rng.randrange(xmax) for _ in range(20000)]
+    xs += [(rng.randrange(xmax >> (k - 1)) << (k - 1)) | ((1 << (k - 1)) - 1) for _ in range(5000)]
+    worst = 0
+    for x in (x for x in xs if x < xmax):
+        r = barrett.barrett_reduce_loose(x, M, k)
+        assert 0 <= r < lo_out * M and (r - x) % M == 0
+        worst = max(worst, r)
+    assert worst >= 3 * M                      # the range really is wider than Sec. III-C's [0, 3M)
+
+
+def test_loose_barrett_needs_k_378():
+    """With k = bitlen(M) = 377 the same step fails on operands below 6M: near the top
+    of the product range its remainder no longer fits mod 2^(k+1)."""
+    M = fq.P
+    x = (6 * M - 1) ** 2
+    r = barrett.barrett_reduce_loose(x, M, 377)
+    assert (r - x) % M != 0
+    assert barrett.loose_bound(M, x + 1, 377) * M > 1 << 378
