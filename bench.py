@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--c", type=int, default=0)
     ap.add_argument("--mode", default="best", choices=["best"] + list(MODES))
     ap.add_argument("--no-extras", action="store_true", help="skip every extra beyond the headline")
+    ap.add_argument("--only", default="", choices=["", "batch_ops"],
+                    help="run one extra alone (no headline): batch_ops = the Fq multiplications, their variants, "
+                         "the mixed PADDs and the integer-multiply probe")
+    ap.add_argument("--batch-ops-n", type=int, default=1 << 24, help="elements of the batch_ops workloads")
     return ap.parse_args()
 
 
@@ -730,10 +734,9 @@ def padd_expected(h, out, case, i1, i2, pool_seeds, m, samples):
     return bool(np.array_equal(got_rows, want)), {k2: int((cs == k2).sum()) for k2 in range(5)}
 
 
-def batch_ops(h, peak, hbm_peak):
+def batch_ops(h, peak, hbm_peak, n=1 << 24):
     """2^24 independent Fq multiplications and 2^24 mixed PADDs (1 % edge cases each)."""
     pkg, torch, dev, stream = h.pkg, h.torch, h.dev, h.stream
-    n = 1 << 24
     a, b = synth.workloads.fq_pairs(n, tag=1)
     mA = pkg.fq_to_montgomery(pkg.to_device(a.T.copy(), dev))
     mB = pkg.fq_to_montgomery(pkg.to_device(b.T.copy(), dev))
@@ -759,7 +762,8 @@ def batch_ops(h, peak, hbm_peak):
     for name, v in (("cios", pkg.FQMUL_CIOS), ("barrett", pkg.FQMUL_BARRETT),
                     ("karatsuba", pkg.FQMUL_KARATSUBA), ("carrysave", pkg.FQMUL_CARRYSAVE),
                     ("cios_twopass", pkg.FQMUL_CIOS_TWOPASS), ("cios_doublerow", pkg.FQMUL_CIOS_DOUBLEROW),
-                    ("warp_per_product", pkg.FQMUL_WARP)):
+                    ("warp_per_product", pkg.FQMUL_WARP), ("paper_25bit_loose_barrett", pkg.FQMUL_PAPER),
+                    ("fips", pkg.FQMUL_FIPS)):
         ms_v = timed(lambda v=v: pkg.fq_mul_batch_variant(mA, mB, v, out=out))
         variants[name] = {"ms_2^24": ms_v, "mul_per_s": n / (ms_v / 1e3)}
     del mA, mB, out
@@ -767,7 +771,7 @@ def batch_ops(h, peak, hbm_peak):
     acc, q, case, i1, i2, pool_seeds = padd_inputs(h, n)
     outp = torch.empty_like(acc)
     ms_padd = timed(lambda: pkg.padd_batch(acc, q, out=outp, form=pkg.FORM_MONTGOMERY), reps=3)
-    step = n // 4096
+    step = max(1, n // 4096)
     samples = sorted(set(range(0, n, step)) | set(torch.nonzero(case != 0)[:512, 0].tolist()))
     padd_ok, counts = padd_expected(h, outp, case, i1, i2, pool_seeds, 1 << 16, samples)
     edge = {nm: float((case == cc).float().mean().item()) for cc, nm in
@@ -913,10 +917,24 @@ def serve(h, edw=False, gl=False, nreq=2000, nsets=8, set_size=1 << 22, load=0.8
             "scalars": "fresh per request, drawn on the device from the request seed"}
 
 
+def run_only(args):
+    """One extra alone on cuda:0 (small captures of its kernels); prints its JSON."""
+    import torch
+
+    import paper_2502_11660_gb300 as pkg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    h = Harness(pkg, torch, dev, torch.cuda.current_stream(dev))
+    peak = pkg.imad_probe(20000, stream=h.stream)
+    print(json.dumps({"batch_ops": batch_ops(h, peak, measured_hbm_peak(), n=args.batch_ops_n)}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args)
 

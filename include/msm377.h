@@ -96,6 +96,18 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
  *                          quotient, its multiple of p) with warp-wide carry
  *                          resolution; the low-latency form the MSM's window chains
  *                          use. Operands may be any values below 8p here.
+ *   MSM377_FQMUL_PAPER     the paper's own format and reduction (Sec. III-B .. III-E)
+ *                          on standard-form operands below 6p (the unreduced operands
+ *                          of its final multiplications): 16 elements of 25 bits,
+ *                          schoolbook column sums, the two-round coarse carry
+ *                          (Sec. III-D), and the looser Barrett step with k = 378
+ *                          (q1 = x >> 377, mu = floor(2^756 / p), q3 = q1 mu >> 379,
+ *                          r = (x - q3 p) mod 2^379). The result is that remainder,
+ *                          r = a b (mod p) with 0 <= r < 4p, not reduced further.
+ *   MSM377_FQMUL_FIPS      a b 2^-384 mod p by product scanning with the Montgomery
+ *                          reduction folded in: column k of a b + m p summed into one
+ *                          three-word accumulator, quotient digit m_k = -t0 when
+ *                          column k < 12 completes, columns 12..23 the result.
  * MSM377_EINVAL for another variant. */
 #define MSM377_FQMUL_CIOS 0
 #define MSM377_FQMUL_BARRETT 1
@@ -104,6 +116,8 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
 #define MSM377_FQMUL_CIOS_TWOPASS 4
 #define MSM377_FQMUL_CIOS_DOUBLEROW 5
 #define MSM377_FQMUL_WARP 6
+#define MSM377_FQMUL_PAPER 7
+#define MSM377_FQMUL_FIPS 8
 int fq_mul_batch_variant(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, int variant,
                          void *stream);
 
@@ -425,9 +439,9 @@ uint64_t msm377_launch_count(void);
 /* ------------------------------------------------------------------------
  * Micro-benchmark for the roofline denominator: runs `iters` rounds of
  * Montgomery-row-shaped carry chains (mad.lo.cc / madc.hi.cc of one product
- * adjacent, even- and odd-indexed limbs in two chains, two independent rows) on
- * every SM and writes the measured count of 32x32->64 limb products per second
- * into *products_per_s. Synchronous.
+ * adjacent, even- and odd-indexed limbs in two chains, two independent rows; every
+ * operand different in every thread) on every SM and writes the measured count of
+ * 32x32->64 limb products per second into *products_per_s. Synchronous.
  */
 int msm377_imad_probe(int iters, double *products_per_s, void *stream);
 

@@ -165,21 +165,23 @@ __global__ void k_gen_mul(const uint32_t* __restrict__ seeds, size_t n, uint32_t
 // Roofline probe: two independent 12-product rows per iteration, each in the shape
 // of a Montgomery multiplication row: two carry chains (the products with the
 // even- and the odd-indexed limbs), the low and high halves of one product
-// adjacent in a chain. (The same products as one low-half chain followed by one
-// high-half chain run at two thirds of this rate on GB300, so the denominator is
-// the faster shape.)
+// adjacent in a chain, which the compiler turns into one wide multiply-add per
+// product -- the cheapest form a 32 x 32 -> 64 product takes on the integer
+// pipe. Every operand differs from thread to thread: values equal across a warp
+// would be computed once per warp on the uniform datapath and overstate the rate.
 __global__ void k_imad_probe(int iters, uint32_t seed, uint32_t* sink) {
     uint32_t t[13], u[13], v[13], w[13], b[12];
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
     for (int k = 0; k < 13; ++k) {
-        t[k] = seed + k + threadIdx.x;
-        u[k] = seed * 3 + k;
-        v[k] = seed * 5 + k;
-        w[k] = seed * 7 + k + blockIdx.x;
+        t[k] = seed + k + tid;
+        u[k] = (seed * 3 + k) ^ (tid * 0x85ebca6bu);
+        v[k] = (seed * 5 + k) ^ (tid * 0xc2b2ae35u);
+        w[k] = (seed * 7 + k) ^ (tid * 0x27d4eb2fu);
     }
 #pragma unroll
-    for (int k = 0; k < 12; ++k) b[k] = seed ^ (0x9e3779b9u * (k + 1));
-    uint32_t x = threadIdx.x | 1u, y = blockIdx.x | 3u;
+    for (int k = 0; k < 12; ++k) b[k] = seed ^ (0x9e3779b9u * (k + 1)) ^ (tid * 0x165667b1u);
+    uint32_t x = tid | 1u, y = (tid * 0x9e3779b9u) | 3u;
     for (int it = 0; it < iters; ++it) {
 #define PROBE_CHAIN(T, A, B0, B1, B2, B3, B4, B5)                                                  \
     asm("mad.lo.cc.u32 %0, %13, %14, %0;\n\t"                                                     \

@@ -613,6 +613,59 @@ __device__ __forceinline__ void mul_doublerow(fe& r, const fe& a, const fe& b) {
 
 // ---------------------------------------------------------------- kernel
 
+// Product scanning (column by column) with the Montgomery reduction folded in
+// (finely integrated product scanning): column k of a b + m p is summed into one
+// three-word accumulator (t0, t1, t2), the quotient digit m_k = -t0 is taken when
+// column k < 12 is complete (t0 + m_k p_0 = t0 + m_k = 0 mod 2^32), and columns
+// 12..23 give the result words. Every product is added as one low/high pair into
+// the same two accumulator words, so each is one wide multiply-add (no product
+// lands on a register pair shifted by one limb, as the rows of CIOS do), and the
+// modulus limbs are register operands rather than immediates. 144 + 132 products;
+// with a b < p R the result is below 2p, as for CIOS.
+__device__ __forceinline__ void fips_acc(uint32_t& t0, uint32_t& t1, uint32_t& t2, uint32_t x, uint32_t y) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(t0), "+r"(t1), "+r"(t2)
+        : "r"(x), "r"(y));
+}
+
+__device__ __forceinline__ void mul_fips(fe& r, const fe& a, const fe& b) {
+    uint32_t p[N], m[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) p[j] = fq::kP[j];
+    uint32_t t0 = 0, t1 = 0, t2 = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+#pragma unroll
+        for (int i = 0; i <= k; ++i) fips_acc(t0, t1, t2, a.v[i], b.v[k - i]);
+#pragma unroll
+        for (int i = 0; i < k; ++i) fips_acc(t0, t1, t2, m[i], p[k - i]);
+        m[k] = 0u - t0;
+        // t0 + m_k p_0 = t0 + m_k = 0 (mod 2^32), carrying 1 unless t0 = 0
+        asm("add.cc.u32 %0, %0, %3;\n\t"
+            "addc.cc.u32 %1, %1, 0;\n\t"
+            "addc.u32 %2, %2, 0;"
+            : "+r"(t0), "+r"(t1), "+r"(t2)
+            : "r"(m[k]));
+        t0 = t1;
+        t1 = t2;
+        t2 = 0;
+    }
+#pragma unroll
+    for (int k = N; k < 2 * N - 1; ++k) {
+#pragma unroll
+        for (int i = k - N + 1; i < N; ++i) fips_acc(t0, t1, t2, a.v[i], b.v[k - i]);
+#pragma unroll
+        for (int i = k - N + 1; i < N; ++i) fips_acc(t0, t1, t2, m[i], p[k - i]);
+        r.v[k - N] = t0;
+        t0 = t1;
+        t1 = t2;
+        t2 = 0;
+    }
+    r.v[N - 1] = t0;
+}
+
 template <int V>
 __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
                                  uint32_t* __restrict__ out, size_t n) {
@@ -623,14 +676,17 @@ __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t*
             x[k] = a[k * n + i];
             y[k] = b[k * n + i];
         }
-        if (V == MSM377_FQMUL_CIOS) {
+        if (V == MSM377_FQMUL_CIOS || V == MSM377_FQMUL_FIPS) {
             fe fa, fb, fr;
 #pragma unroll
             for (int k = 0; k < N; ++k) {
                 fa.v[k] = x[k];
                 fb.v[k] = y[k];
             }
-            fq::mul_inl(fr, fa, fb);
+            if (V == MSM377_FQMUL_FIPS)
+                mul_fips(fr, fa, fb);
+            else
+                fq::mul_inl(fr, fa, fb);
             fq::canon(fr, fr);
 #pragma unroll
             for (int k = 0; k < N; ++k) r[k] = fr.v[k];
@@ -668,6 +724,143 @@ __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t*
     }
 }
 
+// ---- the paper's own format (Sec. III-B .. III-E): 16 elements of 25 bits in 32-bit
+// registers, schoolbook products summed per column, the two-round coarse carry, and
+// the looser Barrett step for operands below 6p (k = 378): q1 = x >> 377,
+// mu = floor(2^756 / p), q3 = (q1 mu) >> 379, r = (x - q3 p) mod 2^379, which lies
+// in [0, 4p) (for operands below 6p the error bound is 3.33 p on this p).
+constexpr int kEl = 16;
+constexpr uint32_t kMask25 = 0x1ffffffu;
+__device__ __constant__ static const uint32_t kPEl[kEl] = {
+    0x0000001u, 0x0600000u, 0x0002142u, 0x0860000u, 0x170b5d4u, 0x04a4000u, 0x188bee8u, 0x11e3de6u,
+    0x100f513u, 0x1116cf9u, 0x0524ec6u, 0x0b80d94u, 0x0ac63b0u, 0x0be2887u, 0x0b8e918u, 0x0000003u};
+__device__ __constant__ static const uint32_t kMuEl[kEl] = {   // floor(2^756 / p), 380 bits
+    0x136bff3u, 0x1ab18bcu, 0x0591f9fu, 0x1c4e215u, 0x03b5a1du, 0x14da05au, 0x1488d85u, 0x1035796u,
+    0x19ddac6u, 0x175a1bcu, 0x0f4f73bu, 0x0502c17u, 0x1a5db0fu, 0x19880c1u, 0x01508d0u, 0x0000013u};
+
+// 12 x 32-bit words -> 16 x 25-bit elements (values below 2^400)
+__device__ __forceinline__ void to_el(uint32_t (&e)[kEl], const uint32_t (&w)[N]) {
+#pragma unroll
+    for (int i = 0; i < kEl; ++i) {
+        const int bit = 25 * i, word = bit >> 5, off = bit & 31;
+        uint32_t v = w[word] >> off;
+        if (off > 7 && word + 1 < N) v |= w[word + 1] << (32 - off);
+        e[i] = v & kMask25;
+    }
+}
+
+// Column sums of x y: c[k] = sum_{i + j = k} x_i y_j (each product < 2^52 with
+// elements below 2^26, at most 16 per column: below 2^56).
+template <int NC>
+__device__ __forceinline__ void el_columns(uint64_t (&c)[NC], const uint32_t (&x)[kEl], const uint32_t (&y)[kEl]) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) c[k] = 0;
+#pragma unroll
+    for (int i = 0; i < kEl; ++i)
+#pragma unroll
+        for (int j = 0; j < kEl; ++j)
+            if (i + j < NC) c[i + j] += (uint64_t)x[i] * y[j];
+}
+
+// Sec. III-D coarse carry, two rounds over the whole column vector: o = in & 0x1ffffff
+// (taken as in - ((in >> 25) << 25), as on the AIE), c = in >> 25, o += carry of the
+// element below. Afterwards every element is below 2^26 (the value is unchanged; the
+// carry out of the top element is dropped, the caller's width covers the value).
+template <int NC>
+__device__ __forceinline__ void coarse_carry(uint64_t (&c)[NC]) {
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+        uint64_t carry = 0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const uint64_t hi = c[k] >> 25;
+            c[k] = c[k] - (hi << 25) + carry;
+            carry = hi;
+        }
+    }
+}
+
+// Accurate carry propagation: every element below 2^25.
+template <int NC>
+__device__ __forceinline__ void exact_carry(uint64_t (&c)[NC]) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const uint64_t v = c[k] + carry;
+        c[k] = v & kMask25;
+        carry = v >> 25;
+    }
+}
+
+// Elements lo .. lo + 15 of v >> (25 lo + s) for 0 < s < 25 (v normalised).
+template <int NC>
+__device__ __forceinline__ void el_shift(uint32_t (&q)[kEl], const uint64_t (&v)[NC], int lo, int s) {
+#pragma unroll
+    for (int i = 0; i < kEl; ++i) {
+        const uint32_t a = lo + i < NC ? (uint32_t)v[lo + i] : 0u;
+        const uint32_t b = lo + i + 1 < NC ? (uint32_t)v[lo + i + 1] : 0u;
+        q[i] = ((a >> s) | (b << (25 - s))) & kMask25;
+    }
+}
+
+__device__ __forceinline__ void mul_paper25(uint32_t (&r)[N], const uint32_t (&aw)[N], const uint32_t (&bw)[N]) {
+    uint32_t a[kEl], b[kEl], q[kEl], mu[kEl], pe[kEl];
+    to_el(a, aw);
+    to_el(b, bw);
+#pragma unroll
+    for (int i = 0; i < kEl; ++i) {
+        mu[i] = kMuEl[i];
+        pe[i] = kPEl[i];
+    }
+    uint64_t x[31];
+    el_columns(x, a, b);                  // mul_in: x = a b < 36 p^2 < 2^759
+    coarse_carry(x);
+    exact_carry(x);                       // the MSBs must be exact for q1
+    el_shift(q, x, 15, 2);                // q1 = x >> 377
+    uint64_t y[31];
+    el_columns(y, q, mu);                 // mul_mu
+    coarse_carry(y);
+    exact_carry(y);
+    el_shift(q, y, 15, 4);                // q3 = (q1 mu) >> 379
+    uint64_t z[kEl];
+    el_columns(z, q, pe);                 // mul_m, low 400 bits only
+    coarse_carry(z);
+    exact_carry(z);
+    // r = (x - q3 p) mod 2^379: 25-bit elements with a borrow, top element 4 bits
+    uint32_t re[kEl];
+    int64_t borrow = 0;
+#pragma unroll
+    for (int k = 0; k < kEl; ++k) {
+        const int64_t d = (int64_t)x[k] - (int64_t)z[k] - borrow;
+        borrow = d < 0 ? 1 : 0;
+        re[k] = (uint32_t)(d + (borrow << 25)) & kMask25;
+    }
+    re[kEl - 1] &= 0xfu;                  // bits 375..378
+#pragma unroll
+    for (int w = 0; w < N; ++w) r[w] = 0;
+#pragma unroll
+    for (int i = 0; i < kEl; ++i) {
+        const int bit = 25 * i, word = bit >> 5, off = bit & 31;
+        r[word] |= re[i] << off;
+        if (off > 7 && word + 1 < N) r[word + 1] |= re[i] >> (32 - off);
+    }
+}
+
+__global__ void k_fq_mul_paper25(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                                 uint32_t* __restrict__ out, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x[N], y[N], r[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            x[k] = a[k * n + i];
+            y[k] = b[k * n + i];
+        }
+        mul_paper25(r, x, y);
+#pragma unroll
+        for (int k = 0; k < N; ++k) out[k * n + i] = r[k];
+    }
+}
+
 // One warp per product (the chains' latency form, wfq.cuh): lanes hold the limbs,
 // three column products and warp-wide carry resolution. Operands below 8p.
 __global__ void k_fq_mul_warp(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
@@ -690,7 +883,7 @@ using namespace msm377;
 
 extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n, int variant,
                                     void* stream) {
-    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_WARP)
+    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_FIPS)
         return set_error(MSM377_EINVAL, "fq_mul_batch_variant: unknown variant %d", variant);
     if (n == 0) return MSM377_OK;
     if (!a || !b || !out) return set_error(MSM377_EINVAL, "fq_mul_batch_variant: NULL pointer");
@@ -716,6 +909,12 @@ extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32
             break;
         case MSM377_FQMUL_CIOS_TWOPASS:
             k_fq_mul_variant<MSM377_FQMUL_CIOS_TWOPASS><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        case MSM377_FQMUL_FIPS:
+            k_fq_mul_variant<MSM377_FQMUL_FIPS><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        case MSM377_FQMUL_PAPER:
+            k_fq_mul_paper25<<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
             break;
         case MSM377_FQMUL_WARP: {
             size_t wb = (n + 3) / 4;   // four warps (products) per block

@@ -235,3 +235,17 @@ def test_status_codes_and_validation_constant_match():
     body = re.search(r"kOrderR\[8\] = \{([^}]*)\}", src).group(1)
     words = [int(w.strip().rstrip("u"), 16) for w in body.split(",")]
     assert sum(w << (32 * k) for k, w in enumerate(words)) == fq.R
+
+
+def test_paper_format_constants_match_the_oracle():
+    """The 25-bit element tables of the paper-format variant hold p and mu = floor(2^756 / p)."""
+    from oracle import barrett, fq
+    src = open(os.path.join(ROOT, "paper_2502_11660_gb300", "csrc", "fqvar.cu")).read()
+
+    def elems(name):
+        body = re.search(name + r"\[kEl\] = \{([^}]*)\}", src).group(1)
+        body = re.sub(r"//[^\n]*", "", body)
+        return barrett.from_elems([int(w.strip().rstrip("u"), 16) for w in body.split(",") if w.strip()])
+
+    assert elems("kPEl") == fq.P
+    assert elems("kMuEl") == (1 << (2 * barrett.LOOSE_K)) // fq.P

@@ -25,6 +25,7 @@ VARIANTS = {
     "cios_twopass": (4, lambda x, y: x * y * RINV % fq.P),
     "cios_doublerow": (5, lambda x, y: x * y * RINV % fq.P),
     "warp": (6, lambda x, y: x * y * RINV % fq.P),
+    "fips": (8, lambda x, y: x * y * RINV % fq.P),
 }
 
 
@@ -74,3 +75,22 @@ def test_warp_product_on_unreduced_operands_and_carry_runs():
     B = soa_of_ints([y for _, y in pairs])
     got = ints_of_soa(pkg.to_host(pkg.fq_mul_batch_variant(pkg.to_device(A), pkg.to_device(B), 6)))
     assert got == [x * y * RINV % fq.P for x, y in pairs]
+
+
+def test_paper_format_equals_the_oracles_loose_barrett():
+    """MSM377_FQMUL_PAPER (16 x 25-bit elements, two-round coarse carry, the looser
+    Barrett step with k = 378; Sec. III-B .. III-E) returns exactly the oracle's
+    remainder in [0, 4p) for operands below 6p, including the largest ones."""
+    rng = random.Random(35)
+    top = 6 * fq.P
+    edges = [0, 1, fq.P - 1, fq.P, 3 * fq.P - 1, 4 * fq.P + 7, top - 1, top - 2, (1 << 379) - 1,
+             (1 << 377) - 1, 1 << 375, int("1ffffff" * 15, 16) % top]
+    pairs = [(x, y) for x in edges for y in edges]
+    pairs += [(rng.randrange(top), rng.randrange(top)) for _ in range(6000)]
+    pairs += [(top - 1 - rng.randrange(1 << 300), top - 1 - rng.randrange(1 << 300)) for _ in range(500)]
+    A = soa_of_ints([x for x, _ in pairs])
+    B = soa_of_ints([y for _, y in pairs])
+    got = ints_of_soa(pkg.to_host(pkg.fq_mul_batch_variant(pkg.to_device(A), pkg.to_device(B), pkg.FQMUL_PAPER)))
+    want = [barrett.barrett_reduce_loose(x * y, fq.P) for x, y in pairs]
+    assert got == want
+    assert all(0 <= r < 4 * fq.P for r in got)
