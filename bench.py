@@ -411,21 +411,26 @@ class Harness:
 
 def tuned_c(pkg, autotune, dev, log2n, edw, gl, pre, forced=0):
     """c for (mode, 2^log2n): the autotuner's measured choice (installed into the
-    library's table for that mode), or `forced`."""
+    library's tables for that mode; variable-base modes also tune the chunk size, the
+    sort, the reduction threads and the window groups), or `forced`."""
     if forced:
-        return forced, "given"
-    tuning = autotune.tune(log2_sizes=[log2n], reps=3, device=dev, edwards=edw, glv=gl, precomputed=pre)
-    table = tuning["table"]
-    autotune.install(table, edwards=edw, glv=gl, precomputed=pre)
-    c = pkg.msm_g1_default_c(1 << log2n, True, edw, gl, pre)
-    return c, {str(cc): round(v, 3) for cc, v in tuning["timings"][log2n].items()}
+        return forced, "given", None
+    if pre:
+        tuning = autotune.tune(log2_sizes=[log2n], reps=3, device=dev, edwards=edw, glv=gl, precomputed=pre)
+        autotune.install(tuning["table"], edwards=edw, glv=gl, precomputed=pre)
+        c = pkg.msm_g1_default_c(1 << log2n, True, edw, gl, pre)
+        return c, {str(cc): round(v, 3) for cc, v in tuning["timings"][log2n].items()}, None
+    tuning = autotune.tune_schedule(log2_sizes=[log2n], reps=3, device=dev, edwards=edw, glv=gl)
+    entry = tuning["schedule"][log2n]
+    ms = tuning["ms"][log2n]
+    return entry[0], {f: {str(v): round(t, 3) for v, t in d.items()} for f, d in ms.items()}, list(entry)
 
 
 def survey_mode(h, autotune, name, n, pts_std, sc_dev, ks, warmup, forced_c=0):
     """Autotune, prepare and time one mode for 10 steps; check one result against the closed form."""
     pkg, torch, dev = h.pkg, h.torch, h.dev
     edw, gl, pre = MODES[name]
-    c, timings = tuned_c(pkg, autotune, dev, int(np.log2(n)), edw, gl, pre, forced_c)
+    c, timings, entry = tuned_c(pkg, autotune, dev, int(np.log2(n)), edw, gl, pre, forced_c)
     t0 = time.perf_counter()
     if pre:
         prep = pkg.msm_points_precompute(pts_std, c=c, scalar_bits=BITS, glv=gl)
@@ -443,7 +448,9 @@ def survey_mode(h, autotune, name, n, pts_std, sc_dev, ks, warmup, forced_c=0):
     ms, st = h.steps(lambda j: pkg.msm_g1(prep, sc_dev[(warmup + j) % nsets], profile=True, **kw), 10, True)
     j = (warmup + 9) % nsets
     ok = verify_msm(pkg, dev, h.out, ks[j]) and pkg.msm_g1_status(ws, h.stream) == 0
+    sched = pkg.msm_g1_schedule(n, c=c, scalar_bits=BITS, edwards=edw, glv=gl, precomputed=pre)
     rec = {"c": c, "ms_per_step": statistics.mean(ms), "points_per_s": n / (statistics.mean(ms) / 1e3),
+           "schedule": sched, "schedule_entry": entry,
            "stages_ms": {s2: statistics.mean(x[s2] for x in st) for s2 in st[0]},
            "resident_set": {"GB": prep.numel() * 4 / 1e9, "setup_s": setup_s},
            "c_by_autotuner": timings, "verified": bool(ok)}
@@ -513,7 +520,20 @@ def run_ours(args):
     value = job_points_per_s(n, world, ms)
 
     ops = op_counts(sc_host[last], c, BITS, edw, gl, pre)
+    # the accumulation kernel alone for the roofline: with window groups the
+    # "accumulate" stage also holds the overlapped tails of earlier groups, so a few
+    # profiled steps run with one group (same c, chunk, sort, reduction)
+    sched = pkg.msm_g1_schedule(n, c=c, scalar_bits=BITS, edwards=edw, glv=gl, precomputed=pre)
     acc_ms = statistics.mean(x["accumulate"] for x in stage_ms)
+    entry = survey[mode].get("schedule_entry") or [c, 0, 0, 0, 0]
+    if sched["groups"] > 1:
+        pkg.msm_g1_set_schedule(k, *entry[:4], 1, edwards=edw, glv=gl)
+        ws1 = pkg.msm_g1_workspace(n, c=c, scalar_bits=BITS, prepared=True, device=dev, edwards=edw, glv=gl)
+        kw1 = dict(kw, workspace=ws1)
+        _, st1 = h.steps(lambda j: pkg.msm_g1(prep, sc_dev[j % nsets], profile=True, **kw1), 5, True)
+        acc_ms = statistics.mean(x["accumulate"] for x in st1)
+        pkg.msm_g1_set_schedule(k, *entry, edwards=edw, glv=gl)
+        del ws1
     achieved = ops["accumulate_products"] / (acc_ms / 1e3)
     hbm_peak = measured_hbm_peak()
     kname = "k_accumulate<%s>" % ("ModelEdwards" if edw else "ModelXyzz")
@@ -524,6 +544,9 @@ def run_ours(args):
                                "in this run",
                 "algorithmic_products_per_launch": ops["accumulate_products"],
                 "kernel_ms": acc_ms,
+                "kernel_ms_source": ("events around the accumulation launch in 5 profiled steps with one window group "
+                                     "(the timed steps overlap later groups' accumulation with earlier groups' tails)"
+                                     if sched["groups"] > 1 else "the timed steps' accumulate stage"),
                 "traffic": (rec["bytes_per_launch"] if rec else None),
                 "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel source "
                                    f"(hash {rec['kernel_hash']}), {rec['date']}, carried from "
@@ -564,11 +587,12 @@ def run_ours(args):
         result["fixed_base"] = fixed_base(h, autotune, n, pts_std, sc_dev, ks, args.warmup)
         # window widths measured for every size 2^10 .. 2^22 of the headline mode, installed
         # before the 2^22, batched and serving runs
-        tuning = autotune.tune(log2_sizes=range(10, 23), reps=3, device=dev, edwards=hm_edw, glv=hm_gl)
-        autotune.install(tuning["table"], edwards=hm_edw, glv=hm_gl)
-        result["autotune"] = {"mode": mode, "c_by_log2n": {str(q): tuning["table"][q] for q in range(10, 23)},
-                              "ms": {str(q): {str(cc): round(v, 3) for cc, v in t.items()}
-                                     for q, t in tuning["timings"].items()}}
+        tuning = autotune.tune_schedule(log2_sizes=range(10, 23), reps=3, device=dev, edwards=hm_edw, glv=hm_gl)
+        result["autotune"] = {"mode": mode,
+                              "schedule_by_log2n (c, chunk, sort, reduce_log2, groups; 0 = built-in rule)":
+                                  {str(q): list(v) for q, v in tuning["schedule"].items()},
+                              "ms": {str(q): {f: {str(v): round(t, 3) for v, t in d.items()} for f, d in rec.items()}
+                                     for q, rec in tuning["ms"].items()}}
         autotune.clear_cache()
         result["n_2e22"] = msm_2e22(h, autotune, mode)
         result["config0_2e12_c8_unsigned"] = msm_small(h)

@@ -224,15 +224,18 @@ int msm_g1_set_window_table(const int32_t *c_by_log2n, int len, uint32_t flags);
 /* Installs one measured schedule entry for signed digits and n in [2^log2n, 2^(log2n+1))
  * in the table of the mode named by flags (MSM377_EDWARDS / MSM377_GLV /
  * MSM377_PRECOMPUTED): c (window width, used when opts.c == 0), chunk (items per
- * accumulation thread, 2..256), sort (1 counting sort, 2 LSD radix sort) and
- * reduce_log2 (log2 of the level-1 bucket-reduction threads, 8..20); 0 in a field
- * keeps the built-in rule. Process-wide, like the window tables (written by the
- * autotuner); workspace sizes depend on it, so install before sizing workspaces. */
-int msm_g1_set_schedule(uint32_t flags, int log2n, int c, int chunk, int sort, int reduce_log2);
+ * accumulation thread, 2..256), sort (1 counting sort, 2 LSD radix sort),
+ * reduce_log2 (log2 of the level-1 bucket-reduction threads, 8..20) and groups
+ * (window groups, 1..8: the accumulation runs group by group and each group's
+ * merges and bucket reduction run on a high-priority helper stream of the caller's
+ * stream, overlapping the next group's accumulation); 0 in a field keeps the
+ * built-in rule. Process-wide, like the window tables (written by the autotuner);
+ * workspace sizes depend on it, so install before sizing workspaces. */
+int msm_g1_set_schedule(uint32_t flags, int log2n, int c, int chunk, int sort, int reduce_log2, int groups);
 
-/* The schedule msm_g1 would use for n points with these options: out4 = {c, chunk,
- * sort (1 counting, 2 radix), log2 of the level-1 reduction threads}. */
-int msm_g1_schedule(size_t n, const msm_opts *opts, int32_t *out4);
+/* The schedule msm_g1 would use for n points with these options: out5 = {c, chunk,
+ * sort (1 counting, 2 radix), log2 of the level-1 reduction threads, window groups}. */
+int msm_g1_schedule(size_t n, const msm_opts *opts, int32_t *out5);
 
 /* Bytes of the stored form of n points for flags (a combination of MSM377_EDWARDS
  * and MSM377_GLV; 0 for other bits): XYZZ 96 per stored point, Edwards 144;
@@ -269,7 +272,12 @@ size_t msm_points_precomputed_bytes(size_t n, const msm_opts *opts);
  * per 256 points and window). Subgroup points only, as MSM377_EDWARDS. */
 int msm_points_precompute(const uint32_t *points_std, size_t n, uint32_t *out, const msm_opts *opts);
 
-/* points: device, 24 u32 per point in standard form, or with MSM377_POINTS_PREPARED
+/* With more than one window group (a schedule option, msm_g1_set_schedule; one by
+ * default), the first msm_g1 call on a stream creates a helper stream of the highest
+ * priority and a few events for that stream (kept until the process exits; up to 32
+ * caller streams, beyond that the groups run in order on the caller's stream): make
+ * that first call outside stream capture.
+ * points: device, 24 u32 per point in standard form, or with MSM377_POINTS_PREPARED
  *   the stored form of msm_points_prepare_ex for the same flags; 16-byte aligned. scalars: device, 8 u32 per scalar, 16-byte aligned.
  * out: device, 24 u32: the affine sum in standard form, (0, 0) for O.
  * workspace: device, >= msm_g1_workspace_bytes(n, opts), 256-byte aligned; the

@@ -434,17 +434,19 @@ class ResidentSet:
 
 
 def msm_g1_set_schedule(log2n: int, c: int = 0, chunk: int = 0, sort: int = 0, reduce_log2: int = 0,
-                        edwards: bool = False, glv: bool = False, precomputed: bool = False) -> None:
+                        groups: int = 0, edwards: bool = False, glv: bool = False,
+                        precomputed: bool = False) -> None:
     """Installs one schedule entry (0 = built-in rule) for signed digits at n in [2^log2n, 2^(log2n+1))."""
     flags = _model_flags(edwards or precomputed, glv) | (PRECOMPUTED if precomputed else 0)
-    check(lib().msm_g1_set_schedule(flags, int(log2n), int(c), int(chunk), int(sort), int(reduce_log2)))
+    check(lib().msm_g1_set_schedule(flags, int(log2n), int(c), int(chunk), int(sort), int(reduce_log2),
+                                    int(groups)))
 
 
 def msm_g1_schedule(n: int, c: int = 0, signed: bool = True, scalar_bits: int = 0, prepared: bool = True,
                     edwards: bool = False, glv: bool = False, precomputed: bool = False) -> dict:
     """The schedule msm_g1 uses for these options: window c, chunk K, sort, level-1 reduction threads."""
     o = _opts(c, signed, scalar_bits, prepared or precomputed, edwards=edwards, glv=glv, precomputed=precomputed)
-    out = (ctypes.c_int32 * 4)()
+    out = (ctypes.c_int32 * 5)()
     check(lib().msm_g1_schedule(n, ctypes.byref(o), out))
     return {"c": int(out[0]), "chunk": int(out[1]), "sort": "counting" if out[2] == 1 else "radix",
-            "reduce_threads_log2": int(out[3])}
+            "reduce_threads_log2": int(out[3]), "groups": int(out[4])}

@@ -71,7 +71,7 @@ SIGNATURES = {
     "msm_g1_batched_workspace_bytes": (c_size, [ctypes.POINTER(MsmJob), c_size, ctypes.POINTER(MsmOpts)]),
     "msm_g1_batched": (c_int, [ctypes.POINTER(MsmJob), c_size, c_void, c_size, ctypes.POINTER(MsmOpts)]),
     "msm_points_validate": (c_int, [c_u32p, c_size, ctypes.c_uint32, c_void]),
-    "msm_g1_set_schedule": (c_int, [ctypes.c_uint32, c_int, c_int, c_int, c_int, c_int]),
+    "msm_g1_set_schedule": (c_int, [ctypes.c_uint32, c_int, c_int, c_int, c_int, c_int, c_int]),
     "msm_g1_schedule": (c_int, [c_size, ctypes.POINTER(MsmOpts), ctypes.POINTER(ctypes.c_int32)]),
     "msm_points_create": (c_int, [c_u32p, c_size, ctypes.POINTER(MsmOpts), ctypes.POINTER(ctypes.c_void_p)]),
     "msm_points_destroy": (c_int, [c_void]),

@@ -111,46 +111,47 @@ def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda", edwards: boo
             "edwards": edwards, "glv": glv, "precomputed": precomputed}
 
 
-def time_schedule(n: int, c: int, chunk: int, sort: int, reduce_log2: int, reps: int = 3, device="cuda",
-                  seed: int = 11, edwards: bool = False, glv: bool = False) -> float:
+def time_schedule(n: int, c: int, chunk: int, sort: int, reduce_log2: int, groups: int = 0, reps: int = 3,
+                  device="cuda", seed: int = 11, edwards: bool = False, glv: bool = False) -> float:
     """Median milliseconds of msm_g1 at size n with one schedule entry installed for 2^floor(log2 n)."""
     from . import msm_g1_set_schedule
     k = int(np.log2(n))
-    msm_g1_set_schedule(k, c, chunk, sort, reduce_log2, edwards=edwards, glv=glv)
+    msm_g1_set_schedule(k, c, chunk, sort, reduce_log2, groups, edwards=edwards, glv=glv)
     return time_msm(n, 0, reps, device, seed, edwards=edwards, glv=glv)
 
 
-# chunk sizes (items per accumulation thread), sorts (1 counting, 2 radix) and level-1
-# reduction thread counts searched after the window width
+# chunk sizes (items per accumulation thread), sorts (1 counting, 2 radix), level-1
+# reduction thread counts and window groups searched after the window width
 CHUNKS = (0, 16, 32, 48, 96, 128)
 SORTS = (1, 2)
 REDUCE_LOG2 = (0, 13, 14, 16, 17)
+GROUPS = (1, 2, 4)
 
 
 def tune_schedule(log2_sizes=range(10, 23), reps: int = 3, device="cuda", edwards: bool = False,
                   glv: bool = False) -> dict:
     """Per size: the window width c (candidates as in tune()), then, at that c, the chunk
-    size, the sort and the number of level-1 reduction threads, one coordinate at a
-    time (each step keeps the fastest value; 0 = the built-in rule). Installs every
-    entry as it goes and returns {"schedule": {k: (c, chunk, sort, reduce_log2)},
-    "ms": {k: {field: {value: ms}}}}."""
+    size, the sort, the number of level-1 reduction threads and the window groups, one
+    coordinate at a time (each step keeps the fastest value; 0 = the built-in rule).
+    Installs every entry as it goes and returns {"schedule": {k: (c, chunk, sort,
+    reduce_log2, groups)}, "ms": {k: {field: {value: ms}}}}."""
     sched, ms = {}, {}
     for k in log2_sizes:
         n = 1 << k
-        cur = [0, 0, 0, 0]
+        cur = [0, 0, 0, 0, 0]
         rec = {}
-        t = {c: time_schedule(n, c, 0, 0, 0, reps, device, edwards=edwards, glv=glv)
+        t = {c: time_schedule(n, c, 0, 0, 0, 0, reps, device, edwards=edwards, glv=glv)
              for c in candidates(k, glv)}
         cur[0] = min(t, key=t.get)
         rec["c"] = t
-        for field, values in ((1, CHUNKS), (2, SORTS), (3, REDUCE_LOG2)):
+        for field, values in ((1, CHUNKS), (2, SORTS), (3, REDUCE_LOG2), (4, GROUPS)):
             t = {}
             for v in values:
                 trial = list(cur)
                 trial[field] = v
                 t[v] = time_schedule(n, *trial, reps=reps, device=device, edwards=edwards, glv=glv)
             cur[field] = min(t, key=t.get)
-            rec[("c", "chunk", "sort", "reduce_log2")[field]] = t
+            rec[("c", "chunk", "sort", "reduce_log2", "groups")[field]] = t
         from . import msm_g1_set_schedule
         msm_g1_set_schedule(k, *cur, edwards=edwards, glv=glv)
         sched[k] = tuple(cur)
@@ -168,7 +169,7 @@ def install_schedule(schedule: dict, edwards: bool = False, glv: bool = False) -
 def clear_schedule(edwards: bool = False, glv: bool = False, precomputed: bool = False) -> None:
     from . import msm_g1_set_schedule
     for k in range(32):
-        msm_g1_set_schedule(k, 0, 0, 0, 0, edwards=edwards, glv=glv, precomputed=precomputed)
+        msm_g1_set_schedule(k, 0, 0, 0, 0, 0, edwards=edwards, glv=glv, precomputed=precomputed)
 
 
 def save_schedule(result: dict, path: str) -> None:

@@ -169,6 +169,9 @@ __global__ void k_gen_mul(const uint32_t* __restrict__ seeds, size_t n, uint32_t
 // product -- the cheapest form a 32 x 32 -> 64 product takes on the integer
 // pipe. Every operand differs from thread to thread: values equal across a warp
 // would be computed once per warp on the uniform datapath and overstate the rate.
+// Where the probe stores its (never true) "keep the work observable" result.
+__device__ uint32_t g_probe_sink[1];
+
 __global__ void k_imad_probe(int iters, uint32_t seed, uint32_t* sink) {
     uint32_t t[13], u[13], v[13], w[13], b[12];
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,24 +295,27 @@ extern "C" int msm377_imad_probe(int iters, double* products_per_s, void* stream
     MSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaStream_t s = as_stream(stream);
     uint32_t* sink = nullptr;
-    MSM_CUDA_TRY(cudaMallocAsync(&sink, sizeof(uint32_t), s));
+    MSM_CUDA_TRY(cudaGetSymbolAddress(reinterpret_cast<void**>(&sink), g_probe_sink));
     const unsigned block = 256, blocks_per_sm = 8;
     const unsigned grid = (unsigned)sms * blocks_per_sm;
-    cudaEvent_t e0, e1;
-    MSM_CUDA_TRY(cudaEventCreate(&e0));
-    MSM_CUDA_TRY(cudaEventCreate(&e1));
-    k_imad_probe<<<grid, block, 0, s>>>(iters / 10 + 1, 1u, sink);  // warm-up
-    MSM_CUDA_TRY(cudaEventRecord(e0, s));
-    k_imad_probe<<<grid, block, 0, s>>>(iters, 7u, sink);
-    note_launches(2);
-    MSM_CUDA_TRY(cudaEventRecord(e1, s));
-    MSM_CUDA_TRY(cudaEventSynchronize(e1));
+    cudaEvent_t e[2] = {nullptr, nullptr};
     float ms = 0.f;
-    MSM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFreeAsync(sink, s);
-    MSM_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaError_t err = cudaEventCreate(&e[0]);
+    if (err == cudaSuccess) err = cudaEventCreate(&e[1]);
+    if (err == cudaSuccess) {
+        k_imad_probe<<<grid, block, 0, s>>>(iters / 10 + 1, 1u, sink);  // warm-up
+        err = cudaEventRecord(e[0], s);
+    }
+    if (err == cudaSuccess) {
+        k_imad_probe<<<grid, block, 0, s>>>(iters, 7u, sink);
+        note_launches(2);
+        err = cudaEventRecord(e[1], s);
+    }
+    if (err == cudaSuccess) err = cudaEventSynchronize(e[1]);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e[0], e[1]);
+    for (cudaEvent_t ev : e)
+        if (ev) cudaEventDestroy(ev);
+    if (err != cudaSuccess) return set_error(MSM377_ECUDA, "msm377_imad_probe: %s", cudaGetErrorString(err));
     double products = (double)grid * block * (double)iters * 2.0 * 12.0;
     *products_per_s = products / ((double)ms * 1e-3);
     return MSM377_OK;

@@ -34,6 +34,11 @@ int profile_mark(cudaStream_t s);
 // *status (device memory) unless it already holds an error.
 int launch_validate(const uint32_t* points_std, size_t n, bool subgroup, int* status, cudaStream_t s);
 
+// msm_g1 with the tails of window groups overlapped on a helper stream (overlap)
+// or run in order on the caller's stream (no stream or event is created).
+int msm_g1_run(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out, void* workspace,
+               size_t workspace_bytes, const msm_opts* opts, bool overlap);
+
 inline unsigned grid_for(size_t n, unsigned block) {
     return static_cast<unsigned>((n + block - 1) / block);
 }

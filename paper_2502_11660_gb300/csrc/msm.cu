@@ -261,6 +261,9 @@ __global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out,
 // domain (D = 0: order 2 or 4, never in the subgroup), become the Edwards
 // identity (0, 1, 0).
 constexpr int kEdChunk = 8;
+// The GLV pair path of the preparation needs every lane's first row and row count
+// even (pairs P, phi(P) never straddle two lanes).
+static_assert(kEdChunk % 2 == 0, "kEdChunk must be even");
 
 __device__ __forceinline__ fe shfl_fe_up(const fe& a, int off) {
     fe r;
@@ -1343,6 +1346,7 @@ std::atomic<int> g_ctable[8][32];      // window width c
 std::atomic<int> g_ktable[8][32];      // items per accumulation chunk K
 std::atomic<int> g_sorttable[8][32];   // 1 counting sort, 2 LSD radix sort
 std::atomic<int> g_rtable[8][32];      // log2 of the level-1 reduction threads
+std::atomic<int> g_gtable[8][32];      // window groups (1 = no overlap of tails with accumulation)
 
 int table_mode(uint32_t flags) {
     return ((flags & MSM377_EDWARDS) ? 1 : 0) | ((flags & MSM377_GLV) ? 2 : 0) |
@@ -1364,7 +1368,10 @@ int default_c(size_t n, int sgn, uint32_t flags) {
     return c;
 }
 
-bool make_plan(size_t n, const msm_opts* o, Plan* p) {
+constexpr int kMaxGroups = 8;
+
+// allow_groups = false: one window group (batched calls overlap whole jobs instead).
+bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
     if (!o) return false;
     p->n = n;
     p->edw = (o->flags & MSM377_EDWARDS) ? 1 : 0;
@@ -1402,13 +1409,30 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     const int tsort = (p->sgn && lgn < 32) ? g_sorttable[tmode][lgn].load(std::memory_order_relaxed) : 0;
     const int tk = (p->sgn && lgn < 32) ? g_ktable[tmode][lgn].load(std::memory_order_relaxed) : 0;
     const int tr = (p->sgn && lgn < 32) ? g_rtable[tmode][lgn].load(std::memory_order_relaxed) : 0;
+    const int tg = (p->sgn && lgn < 32) ? g_gtable[tmode][lgn].load(std::memory_order_relaxed) : 0;
     p->counting = ((o->flags & MSM377_RADIX_SORT) || tsort == 2) ? 0 : 1;
     p->tiles = (items + kSortTile - 1) / kSortTile;
-    // Chunks of K <= 64 items, one per thread, sized so that the chunks over all
-    // windows fill whole waves of resident accumulation threads (152 SMs x 3 blocks
-    // of 128 on a GB300): m waves of K items rather than a last, partly idle wave.
+    // Window groups (a schedule option): the accumulation runs group by group on the
+    // caller's stream and each group's merges, bucket reduction and per-window sums
+    // run on a higher-priority helper stream as soon as its accumulation is done,
+    // overlapping the next group's accumulation. Built-in rule: one group. Measured
+    // on GB300 (Edwards + GLV, c = 16): 2^20 one group 6.17 ms, two 6.55, four 7.28;
+    // 2^22 20.7 / 22.0 / 22.6 ms -- the overlapped tails slow the accumulation more
+    // than they save, so the autotuner keeps one group at every size measured.
+    int groups = 1;
+    if (allow_groups && !p->pre) {
+        groups = tg > 0 ? tg : 1;
+        if (groups > p->W) groups = p->W;
+        if (groups > kMaxGroups) groups = kMaxGroups;
+    }
+    p->gw = (p->W + groups - 1) / groups;
+    p->ngroups = (p->W + p->gw - 1) / p->gw;
+    // Chunks of K <= 64 items, one per thread, sized so that the chunks of one
+    // accumulation launch (one window group) fill whole waves of resident threads
+    // (152 SMs x 3 blocks of 128 on a GB300): m waves of K items rather than a last,
+    // partly idle wave.
     constexpr size_t kWave = 152 * 384;
-    const size_t total = (size_t)p->W * items;
+    const size_t total = (size_t)p->gw * items;
     size_t waves = (total + 64 * kWave - 1) / (64 * kWave);
     if (waves < 1) waves = 1;
     size_t K = (total + waves * kWave - 1) / (waves * kWave);
@@ -1418,8 +1442,6 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->K = (int)K;
     p->cpw = (uint32_t)((items + K - 1) / K);
     if (p->cpw == 0) p->cpw = 1;
-    p->gw = p->W;
-    p->ngroups = 1;
     // bucket reduction geometry: segments of L buckets, the longest L that still
     // leaves kReduceThreads level-1 threads over all windows (longer segments mean
     // fewer segment sums for the bit-sum stage, but fewer threads for the running sums)
@@ -1464,11 +1486,11 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p) {
     p->off_headflag = take(chunks * 4);
     p->off_tailkey = take(chunks * 4);
     p->off_start = take(chunks * 4);
-    p->off_Y = take((size_t)p->gw * p->G * XY);
-    p->off_V = take((size_t)p->gw * p->G * XY);
+    p->off_Y = take((size_t)p->ngroups * p->gw * p->G * XY);    // per group
+    p->off_V = take((size_t)p->ngroups * p->gw * p->G * XY);
     const size_t zs = (size_t)p->gw * (p->logG + 1) * p->Q;
-    p->off_P0 = take(zs * XY);
-    p->off_P1 = take(zs * XY);
+    p->off_P0 = take((size_t)p->ngroups * zs * XY);
+    p->off_P1 = take((size_t)p->ngroups * zs * XY);
     p->off_S = take((size_t)p->W * XY);
     p->total = off;
     return true;
@@ -1528,30 +1550,34 @@ extern "C" int msm_g1_set_window_table(const int32_t* c_by_log2n, int len, uint3
     return MSM377_OK;
 }
 
-extern "C" int msm_g1_set_schedule(uint32_t flags, int log2n, int c, int chunk, int sort, int reduce_log2) {
+extern "C" int msm_g1_set_schedule(uint32_t flags, int log2n, int c, int chunk, int sort, int reduce_log2,
+                                   int groups) {
     if (flags & ~(MSM377_EDWARDS | MSM377_GLV | MSM377_PRECOMPUTED))
         return set_error(MSM377_EINVAL, "msm_g1_set_schedule: flags 0x%x (only EDWARDS, GLV and PRECOMPUTED)",
                          flags);
     if (log2n < 0 || log2n >= 32 || (c && (c < 2 || c > 20)) || (chunk && (chunk < 2 || chunk > 256)) ||
-        sort < 0 || sort > 2 || (reduce_log2 && (reduce_log2 < 8 || reduce_log2 > 20)))
-        return set_error(MSM377_EINVAL, "msm_g1_set_schedule: log2n %d c %d chunk %d sort %d reduce_log2 %d", log2n,
-                         c, chunk, sort, reduce_log2);
+        sort < 0 || sort > 2 || (reduce_log2 && (reduce_log2 < 8 || reduce_log2 > 20)) || groups < 0 ||
+        groups > kMaxGroups)
+        return set_error(MSM377_EINVAL, "msm_g1_set_schedule: log2n %d c %d chunk %d sort %d reduce_log2 %d groups %d",
+                         log2n, c, chunk, sort, reduce_log2, groups);
     const int mode = table_mode(flags);
     g_ctable[mode][log2n].store(c, std::memory_order_relaxed);
     g_ktable[mode][log2n].store(chunk, std::memory_order_relaxed);
     g_sorttable[mode][log2n].store(sort, std::memory_order_relaxed);
     g_rtable[mode][log2n].store(reduce_log2, std::memory_order_relaxed);
+    g_gtable[mode][log2n].store(groups, std::memory_order_relaxed);
     return MSM377_OK;
 }
 
-extern "C" int msm_g1_schedule(size_t n, const msm_opts* opts, int32_t* out4) {
-    if (!opts || !out4) return set_error(MSM377_EINVAL, "msm_g1_schedule: NULL argument");
+extern "C" int msm_g1_schedule(size_t n, const msm_opts* opts, int32_t* out5) {
+    if (!opts || !out5) return set_error(MSM377_EINVAL, "msm_g1_schedule: NULL argument");
     Plan p;
     if (!make_plan(n, opts, &p)) return set_error(MSM377_EINVAL, "msm_g1_schedule: bad options");
-    out4[0] = p.c;
-    out4[1] = p.K;
-    out4[2] = p.counting ? 1 : 2;
-    out4[3] = ilog2((uint64_t)p.W * p.G);
+    out5[0] = p.c;
+    out5[1] = p.K;
+    out5[2] = p.counting ? 1 : 2;
+    out5[3] = ilog2((uint64_t)p.W * p.G);
+    out5[4] = p.ngroups;
     return MSM377_OK;
 }
 
@@ -1625,7 +1651,7 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     const size_t n = p.n;
     int* status = at<int>(workspace, p.off_status);
     if (reset_status)
-        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), s));  // status word, longest run of heads
+        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, (1 + kMaxGroups) * sizeof(int), s));  // status, longest runs
     const uint4* pts = reinterpret_cast<const uint4*>(points);
     if ((opts->flags & MSM377_VALIDATE) && !(opts->flags & MSM377_POINTS_PREPARED)) {
         const int r = launch_validate(points, n, (opts->flags & (MSM377_EDWARDS | MSM377_GLV)) != 0, status, s);
@@ -1695,19 +1721,22 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     return check_launch("msm head");
 }
 
-// Phase 5-7 of one MSM on stream s: partial merges, bucket reduction, window
-// combination and normalisation into out.
+// Phase 5-6 and the per-window sums of stage 7 for the windows of one group
+// (a.w0 .. a.w0 + a.nwin - 1) on stream s: partial merges, bucket reduction, and
+// S_w for each window, in group g's buffers.
 template <class M>
-int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s) {
-    uint4* Y = at<uint4>(workspace, p.off_Y);
-    uint4* V = at<uint4>(workspace, p.off_V);
-    uint4* P0 = at<uint4>(workspace, p.off_P0);
-    uint4* P1 = at<uint4>(workspace, p.off_P1);
+int enqueue_group_tail_m(const Plan& p, const AccArgs& a, int g, void* workspace, cudaStream_t s) {
+    const size_t yv = (size_t)p.gw * p.G * kXyzzVec;
+    const size_t zs = (size_t)p.gw * (p.logG + 1) * p.Q * kXyzzVec;
+    uint4* Y = at<uint4>(workspace, p.off_Y) + (size_t)g * yv;
+    uint4* V = at<uint4>(workspace, p.off_V) + (size_t)g * yv;
+    uint4* P0 = at<uint4>(workspace, p.off_P0) + (size_t)g * zs;
+    uint4* P1 = at<uint4>(workspace, p.off_P1) + (size_t)g * zs;
     uint4* S = at<uint4>(workspace, p.off_S);
-    const size_t nchunks = (size_t)p.W * p.cpw;
+    const size_t nchunks = (size_t)a.nwin * p.cpw;
     // 5. merge partial sums of runs crossing chunk edges (log depth)
     int32_t* start = at<int32_t>(workspace, p.off_start);
-    int* maxspan = at<int>(workspace, p.off_status) + 1;
+    int* maxspan = at<int>(workspace, p.off_status) + 1 + g;
     k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, maxspan);
     note_launches(1);
     for (uint32_t d = 1; d < p.cpw; d <<= 1) {
@@ -1716,11 +1745,11 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
     }
     k_merge_final<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a);
     note_launches(1);
-    // 6. bucket reduction, all windows
-    const size_t WG = (size_t)p.W * p.G;
-    k_reduce_segments<M><<<grid_for(WG, 128), 128, 0, s>>>(a.buckets, p.Bp, p.L, 0, p.W, p.G, Y, V);
-    const size_t nseg = (size_t)p.W * (p.logG + 1);
-    k_bitsums<M><<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, p.W, p.G, p.logG, p.Q, P0);
+    // 6. bucket reduction of the group's windows
+    const size_t WG = (size_t)a.nwin * p.G;
+    k_reduce_segments<M><<<grid_for(WG, 128), 128, 0, s>>>(a.buckets, p.Bp, p.L, a.w0, a.nwin, p.G, Y, V);
+    const size_t nseg = (size_t)a.nwin * (p.logG + 1);
+    k_bitsums<M><<<grid_for(nseg * p.Q, 128), 128, 0, s>>>(Y, V, a.nwin, p.G, p.logG, p.Q, P0);
     note_launches(2);
     uint32_t m = p.Q;
     uint4* zin = P0;
@@ -1736,26 +1765,123 @@ int enqueue_tail_m(const Plan& p, const AccArgs& a, void* workspace, uint32_t* o
         zin = zout;
         zout = tmp;
     }
-    // 7. window combination and normalisation
-    k_window_horner_w<M><<<(unsigned)p.W, 128, 0, s>>>(zin, p.W, p.logG, p.log2L, S);
-    k_chain_w<M><<<1, 128, 0, s>>>(S, p.W, p.c, out);
-    note_launches(2);
+    // 7a. the per-window sums S_w
+    k_window_horner_w<M><<<(unsigned)a.nwin, 128, 0, s>>>(zin, a.nwin, p.logG, p.log2L, S + (size_t)a.w0 * kXyzzVec);
+    note_launches(1);
     return check_launch("msm tail");
 }
 
-int enqueue_tail(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s) {
-    return p.edw ? enqueue_tail_m<ModelEdwards>(p, a, workspace, out, s)
-                 : enqueue_tail_m<ModelXyzz>(p, a, workspace, out, s);
+int enqueue_group_tail(const Plan& p, const AccArgs& a, int g, void* workspace, cudaStream_t s) {
+    return p.edw ? enqueue_group_tail_m<ModelEdwards>(p, a, g, workspace, s)
+                 : enqueue_group_tail_m<ModelXyzz>(p, a, g, workspace, s);
 }
 
+// 7b. the window combination and normalisation into out.
+int enqueue_chain(const Plan& p, void* workspace, uint32_t* out, cudaStream_t s) {
+    const uint4* S = at<uint4>(workspace, p.off_S);
+    if (p.edw)
+        k_chain_w<ModelEdwards><<<1, 128, 0, s>>>(S, p.W, p.c, out);
+    else
+        k_chain_w<ModelXyzz><<<1, 128, 0, s>>>(S, p.W, p.c, out);
+    note_launches(1);
+    return check_launch("msm chain");
+}
+
+// Phase 5-7 of one MSM as a single window group on stream s (batched calls).
+int enqueue_tail(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s) {
+    int r = enqueue_group_tail(p, a, 0, workspace, s);
+    if (r) return r;
+    return enqueue_chain(p, workspace, out, s);
+}
+
+// Accumulation of the windows a.w0 .. a.w0 + a.nwin - 1.
 int enqueue_accumulate(const Plan& p, const AccArgs& a, cudaStream_t s) {
-    const unsigned grid = grid_for((size_t)p.W * p.cpw, 128);
+    const unsigned grid = grid_for((size_t)a.nwin * p.cpw, 128);
     if (p.edw)
         k_accumulate<ModelEdwards><<<grid, 128, 0, s>>>(a);
     else
         k_accumulate<ModelXyzz><<<grid, 128, 0, s>>>(a);
     note_launches(1);
     return check_launch("msm accumulate");
+}
+
+// A helper stream of the highest priority and events, one set per caller stream
+// (so calls on different streams never share them), created on first use.
+struct Overlap {
+    cudaStream_t hi;
+    cudaEvent_t ev[kMaxGroups + 1];
+};
+constexpr int kOverlapSlots = 32;
+struct OverlapSlot {
+    bool used = false;
+    int dev = -1;
+    cudaStream_t caller = nullptr;
+    Overlap ov;
+};
+OverlapSlot g_overlap[kOverlapSlots];
+std::mutex g_overlap_mu;
+
+// nullptr when every slot is taken: the groups then run in sequence on s.
+const Overlap* overlap_for(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lock(g_overlap_mu);
+    for (auto& sl : g_overlap)
+        if (sl.used && sl.dev == dev && sl.caller == s) return &sl.ov;
+    for (auto& sl : g_overlap) {
+        if (sl.used) continue;
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return nullptr;
+        if (cudaStreamCreateWithPriority(&sl.ov.hi, cudaStreamNonBlocking, greatest) != cudaSuccess) return nullptr;
+        for (int i = 0; i <= kMaxGroups; ++i)
+            if (cudaEventCreateWithFlags(&sl.ov.ev[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        sl.used = true;
+        sl.dev = dev;
+        sl.caller = s;
+        return &sl.ov;
+    }
+    return nullptr;
+}
+
+// Phase 4-7 on stream s: the accumulation group by group, each group's tail on the
+// high-priority helper as soon as its accumulation is done (overlapping the next
+// group's accumulation), then the window chain on s. Without a helper (ov null, or
+// one group) everything runs in order on s. prof: stage marks after the last
+// accumulation and after the chain.
+int enqueue_body(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out, cudaStream_t s, const Overlap* ov,
+                 bool prof) {
+    int r;
+    if (p.ngroups <= 1 || !ov) {
+        for (int g = 0; g < p.ngroups; ++g) {
+            AccArgs ag = a;
+            ag.w0 = g * p.gw;
+            ag.nwin = (p.W - ag.w0) < p.gw ? (p.W - ag.w0) : p.gw;
+            if ((r = enqueue_accumulate(p, ag, s))) return r;
+        }
+        if (prof) profile_mark(s);
+        for (int g = 0; g < p.ngroups; ++g) {
+            AccArgs ag = a;
+            ag.w0 = g * p.gw;
+            ag.nwin = (p.W - ag.w0) < p.gw ? (p.W - ag.w0) : p.gw;
+            if ((r = enqueue_group_tail(p, ag, g, workspace, s))) return r;
+        }
+    } else {
+        for (int g = 0; g < p.ngroups; ++g) {
+            AccArgs ag = a;
+            ag.w0 = g * p.gw;
+            ag.nwin = (p.W - ag.w0) < p.gw ? (p.W - ag.w0) : p.gw;
+            if ((r = enqueue_accumulate(p, ag, s))) return r;
+            MSM_CUDA_TRY(cudaEventRecord(ov->ev[g], s));
+            MSM_CUDA_TRY(cudaStreamWaitEvent(ov->hi, ov->ev[g], 0));
+            if ((r = enqueue_group_tail(p, ag, g, workspace, ov->hi))) return r;
+        }
+        if (prof) profile_mark(s);
+        MSM_CUDA_TRY(cudaEventRecord(ov->ev[kMaxGroups], ov->hi));
+        MSM_CUDA_TRY(cudaStreamWaitEvent(s, ov->ev[kMaxGroups], 0));
+    }
+    if ((r = enqueue_chain(p, workspace, out, s))) return r;
+    if (prof) profile_mark(s);
+    return MSM377_OK;
 }
 
 // Library-owned helper streams for batched calls, per device, created once.
@@ -1814,8 +1940,10 @@ int join_into(DeviceAux* aux, cudaStream_t s, int k) {
 
 }  // namespace
 
-extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out,
-                      void* workspace, size_t workspace_bytes, const msm_opts* opts) {
+namespace msm377 {
+
+int msm_g1_run(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out, void* workspace,
+               size_t workspace_bytes, const msm_opts* opts, bool overlap) {
     if (!opts) return set_error(MSM377_EINVAL, "msm_g1: opts is NULL");
     if (!out) return set_error(MSM377_EINVAL, "msm_g1: out is NULL");
     cudaStream_t s = as_stream(opts->stream);
@@ -1846,13 +1974,14 @@ extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n,
     int r = enqueue_head(p, points, scalars, workspace, opts, s, &a);
     if (r) return r;
     if (prof) profile_mark(s);
-    r = enqueue_accumulate(p, a, s);
-    if (r) return r;
-    if (prof) profile_mark(s);
-    r = enqueue_tail(p, a, workspace, out, s);
-    if (r) return r;
-    if (prof) profile_mark(s);
-    return MSM377_OK;
+    return enqueue_body(p, a, workspace, out, s, (overlap && p.ngroups > 1) ? overlap_for(s) : nullptr, prof);
+}
+
+}  // namespace msm377
+
+extern "C" int msm_g1(const uint32_t* points, const uint32_t* scalars, size_t n, uint32_t* out,
+                      void* workspace, size_t workspace_bytes, const msm_opts* opts) {
+    return msm_g1_run(points, scalars, n, out, workspace, workspace_bytes, opts, true);
 }
 
 namespace {
@@ -1864,7 +1993,7 @@ bool batch_plans(const msm_job* jobs, size_t njobs, const msm_opts* opts, Plan* 
     for (size_t i = 0; i < njobs; ++i) {
         msm_opts o = *opts;
         if (jobs[i].c) o.c = jobs[i].c;
-        if (!make_plan(jobs[i].n, &o, &plans[i])) return false;
+        if (!make_plan(jobs[i].n, &o, &plans[i], false)) return false;
         off += align_up(plans[i].total, 256);
     }
     *total = off;
@@ -2016,7 +2145,7 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
     int r = device_aux(&aux);
     if (r) return r;
     cudaStream_t sc = aux->st[0], sp = aux->st[1];
-    MSM_CUDA_TRY(cudaMemsetAsync(at<int>(workspace, p.off_status), 0, 2 * sizeof(int), s));  // before the fork
+    MSM_CUDA_TRY(cudaMemsetAsync(at<int>(workspace, p.off_status), 0, (1 + kMaxGroups) * sizeof(int), s));  // before the fork
     r = fork_from(aux, s, 2);
     if (r) return r;
     uint4* prep = at<uint4>(workspace, p.off_points);
@@ -2042,9 +2171,7 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
     if (r) return r;
     r = join_into(aux, s, 2);
     if (r) return r;
-    r = enqueue_accumulate(p, acc, s);
-    if (r) return r;
-    r = enqueue_tail(p, acc, workspace, d_out, s);
+    r = enqueue_body(p, acc, workspace, d_out, s, p.ngroups > 1 ? overlap_for(s) : nullptr, false);
     if (r) return r;
     MSM_CUDA_TRY(cudaMemcpyAsync(out_host, d_out, 24 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     return msm_g1_status(workspace, &o);

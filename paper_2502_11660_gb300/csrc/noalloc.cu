@@ -89,5 +89,6 @@ extern "C" int msm_g1_noalloc(const uint32_t* points, const uint32_t* scalars, s
         }
         scratch = sc.ptr;
     }
-    return msm_g1(points, scalars, n, out, scratch, (size_t)MSM377_NOALLOC_SCRATCH_BYTES, opts);
+    // no overlap helper: this entry point creates no stream or event either
+    return msm_g1_run(points, scalars, n, out, scratch, (size_t)MSM377_NOALLOC_SCRATCH_BYTES, opts, false);
 }

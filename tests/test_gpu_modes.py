@@ -320,3 +320,50 @@ def test_precomputed_full_size_2e20(c):
         torch.cuda.synchronize()
         assert g1.from_limbs(pkg.to_host(out)) == want
     assert pkg.msm_g1_status(ws) == 0
+
+
+# ---------------------------------------------------------------- window groups (tails overlapped)
+
+@pytest.mark.parametrize("groups", [1, 2, 3, 4, 8])
+@pytest.mark.parametrize("edw,split", ALL_MODES, ids=ALL_IDS)
+def test_window_groups_give_the_closed_form(edw, split, groups):
+    """The accumulation in window groups with each group's tail on the helper stream
+    (1, 2, 3, 4, 8 groups over 8 to 16 windows) gives the same exact result."""
+    n = 1 << 18
+    prep, da, want = _resident(n, 18, edw, split)
+    k = 18
+    pkg.msm_g1_set_schedule(k, 16, 0, 0, 0, groups, edwards=edw, glv=split)
+    try:
+        sch = pkg.msm_g1_schedule(n, scalar_bits=253, edwards=edw, glv=split)
+        assert sch["c"] == 16 and sch["groups"] == min(groups, 8 if split else 16)
+        ws = pkg.msm_g1_workspace(n, scalar_bits=253, prepared=True, edwards=edw, glv=split)
+        for _ in range(2):
+            out = pkg.msm_g1(prep, da, workspace=ws, scalar_bits=253, prepared=True, edwards=edw, glv=split,
+                             profile=True)
+            st = pkg.profile_last()
+            assert set(st) == {"head", "accumulate", "tail"}
+            torch.cuda.synchronize()
+            assert g1.from_limbs(pkg.to_host(out)) == want
+    finally:
+        pkg.msm_g1_set_schedule(k, edwards=edw, glv=split)
+
+
+def test_window_groups_on_concurrent_streams():
+    """Calls on different streams get different helper streams: four MSMs in flight at once
+    (each in two window groups) all give their closed forms."""
+    n = 1 << 18
+    data = [msm_inputs(n, tag=900 + i) for i in range(4)]
+    streams = [torch.cuda.Stream() for _ in data]
+    outs, wss = [], []
+    kw = dict(scalar_bits=253, edwards=True, glv=True, c=15)
+    pkg.msm_g1_set_schedule(18, 15, 0, 0, 0, 2, edwards=True, glv=True)
+    for (a, s, pts), st in zip(data, streams):
+        with torch.cuda.stream(st):
+            ws = pkg.msm_g1_workspace(n, **kw)
+            wss.append(ws)
+            outs.append(pkg.msm_g1(pkg.to_device(pts), pkg.to_device(a), workspace=ws, stream=st, **kw))
+    assert pkg.msm_g1_schedule(n, prepared=False, **kw)["groups"] == 2
+    torch.cuda.synchronize()
+    pkg.msm_g1_set_schedule(18, edwards=True, glv=True)
+    for (a, s, _), o in zip(data, outs):
+        assert g1.from_limbs(pkg.to_host(o)) == closed_form_limbs(s, a)
