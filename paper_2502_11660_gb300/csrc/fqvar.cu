@@ -863,10 +863,11 @@ __global__ void k_fq_mul_paper25(const uint32_t* __restrict__ a, const uint32_t*
 
 // One warp per product (the chains' latency form, wfq.cuh): lanes hold the limbs,
 // three column products and warp-wide carry resolution. Operands below 8p.
-__global__ void k_fq_mul_warp(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
-                              uint32_t* __restrict__ out, size_t n) {
+__global__ void __launch_bounds__(128) k_fq_mul_warp(const uint32_t* __restrict__ a, const uint32_t* __restrict__ b,
+                                                     uint32_t* __restrict__ out, size_t n) {
+    __shared__ __align__(16) uint32_t scratch[4 * wfq::kScratchWords];
     wfq::Consts K;
-    wfq::init(K);
+    wfq::init(K, scratch + (threadIdx.x >> 5) * wfq::kScratchWords);
     const int l = wfq::lane();
     const size_t warps = (size_t)gridDim.x * (blockDim.x >> 5);
     for (size_t i = blockIdx.x * (size_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {

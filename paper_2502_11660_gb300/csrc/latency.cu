@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(32) k_chain_ed4(const uint4* __restrict__ pts,
 
 // Four warps per addition: level 1 {A, B, C} and level 2 {X3, Y3, T3, Z3} on one
 // warp each, every product spread over the lanes of its warp.
-__global__ void __launch_bounds__(128) k_chain_edw(const uint4* __restrict__ pts, size_t n, uint32_t* __restrict__ out) {
-    __shared__ uint32_t slots[wpt::kSlots * 12];
+__global__ void __launch_bounds__(128, 1) k_chain_edw(const uint4* __restrict__ pts, size_t n, uint32_t* __restrict__ out) {
+    __shared__ __align__(16) uint32_t slots[wpt::kSharedWords];
     wpt::Group g;
     wpt::init(g, slots);
     wpt::ed_set_inf(g);

@@ -1250,9 +1250,9 @@ __global__ void __launch_bounds__(kTreeThreads) k_sum_tree(const uint4* __restri
 // Block w: S_w = L sum_{k < logG} 2^k Z_k + Z_logG for window w, by Horner from the
 // top term.
 template <class M>
-__global__ void __launch_bounds__(128) k_window_horner_w(const uint4* __restrict__ Z, int nwin, int logG, int log2L,
+__global__ void __launch_bounds__(128, 1) k_window_horner_w(const uint4* __restrict__ Z, int nwin, int logG, int log2L,
                                                          uint4* __restrict__ S) {
-    __shared__ uint32_t slots[wpt::kSlots * 12];
+    __shared__ __align__(16) uint32_t slots[wpt::kSharedWords];
     wpt::Group g;
     wpt::init(g, slots);
     const int w = blockIdx.x;
@@ -1275,8 +1275,8 @@ __global__ void __launch_bounds__(128) k_window_horner_w(const uint4* __restrict
 // sum_w 2^(c w) S_w by Horner over the windows, then the affine result in standard
 // form (thread 0 writes it after the inversion).
 template <class M>
-__global__ void __launch_bounds__(128) k_chain_w(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
-    __shared__ uint32_t slots[wpt::kSlots * 12];
+__global__ void __launch_bounds__(128, 1) k_chain_w(const uint4* __restrict__ S, int W, int c, uint32_t* __restrict__ out) {
+    __shared__ __align__(16) uint32_t slots[wpt::kSharedWords];
     wpt::Group g;
     wpt::init(g, slots);
     const uint32_t* s = reinterpret_cast<const uint32_t*>(S);

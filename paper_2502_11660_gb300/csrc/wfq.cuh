@@ -9,9 +9,12 @@
 //   T = a b,   m = (T mod R) p' mod R  (p' = -p^-1 mod R),   U = (T + m p) / R.
 // In a column product lane k (< 24) sums its own column,
 //   sum_i lo(x_i y_{k-i}) + sum_i hi(x_i y_{k-1-i}),
-// with x_i broadcast by shuffles (or, for the constants p' and p of the two
-// reduction products, taken as immediates) and y_{k-d} fetched per lane by
-// shuffles, so the twelve rows run in parallel across lanes. The column sums (below 2^37) are then turned into words
+// with every limb x_i of the broadcast operand read by all lanes from the warp's
+// shared-memory scratch (three 16-byte loads of one address) and y_{k-d} either
+// fetched per lane by shuffles (the operand b) or, for the constants p' and p of
+// the two reduction products, kept per lane in registers -- so the twelve rows run
+// in parallel across lanes and a product costs about thirty shared-memory and
+// shuffle operations, the resource the four warps of a group share. The column sums (below 2^37) are then turned into words
 // in constant time: after adding the previous column's high part, each lane
 // either generates a carry, propagates one (its word is 2^32 - 1) or neither; with
 // G and P the warp's ballots of those flags, the carries into the lanes are the
@@ -28,25 +31,24 @@ namespace wfq {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// p and p' = -p^-1 mod 2^384 (so that T + ((T mod R) p' mod R) p = 0 mod R), as
-// compile-time limbs: in the two reduction products they are the broadcast
-// operand, so with the loops unrolled they enter the multiply-adds as immediates.
-__host__ __device__ constexpr uint32_t p_limb(int i) {
-    constexpr uint32_t v[12] = {0x00000001u, 0x8508c000u, 0x30000000u, 0x170b5d44u, 0xba094800u, 0x1ef3622fu,
-                                0x00f5138fu, 0x1a22d9f3u, 0x6ca1493bu, 0xc63b05c0u, 0x17c510eau, 0x01ae3a46u};
-    return v[i];
-}
-__host__ __device__ constexpr uint32_t pinv_limb(int i) {
-    constexpr uint32_t v[12] = {0xffffffffu, 0x8508bfffu, 0xa0000000u, 0xd1e94577u, 0x970debffu, 0x35ed1347u,
-                                0xcced7a13u, 0x5b245b86u, 0x806a3cecu, 0x22f80141u, 0xeec82e3du, 0xbfa5205fu};
-    return v[i];
-}
+// p' = -p^-1 mod 2^384 (so that T + ((T mod R) p' mod R) p = 0 mod R).
+__device__ __constant__ static const uint32_t kPInvNeg[12] = {
+    0xffffffffu, 0x8508bfffu, 0xa0000000u, 0xd1e94577u, 0x970debffu, 0x35ed1347u,
+    0xcced7a13u, 0x5b245b86u, 0x806a3cecu, 0x22f80141u, 0xeec82e3du, 0xbfa5205fu};
 
 __device__ __forceinline__ int lane() { return threadIdx.x & 31; }
 
-// Per-lane limbs of p, 2p and 4p (lane j < 12: limb j; 0 above).
+// Words of the per-warp shared-memory scratch a multiplication uses: the broadcast
+// operand, T mod R and the quotient m (12 words each, 16-byte aligned).
+constexpr int kScratchWords = 36;
+
+// Per-lane values: limb `lane` of p, 2p and 4p, the column operands p_{lane - d} and
+// p'_{lane - d} for d = 0..12 (0 outside the twelve limbs), and the shared-memory
+// address of this warp's scratch.
 struct Consts {
-    uint32_t p, p2, p4;
+    uint32_t p, p2, p4, p6;
+    uint32_t pc[13], qc[13];
+    uint32_t scratch;
 };
 
 __device__ __forceinline__ uint32_t limb_of(const uint32_t (&c)[12]) {
@@ -54,13 +56,43 @@ __device__ __forceinline__ uint32_t limb_of(const uint32_t (&c)[12]) {
     return l < 12 ? c[l] : 0u;
 }
 
-__device__ __forceinline__ void init(Consts& K) {
+__device__ __forceinline__ uint32_t normalize(uint32_t lo, uint32_t hi);
+__device__ __forceinline__ uint32_t keep12(uint32_t v);
+
+// scratch: this warp's kScratchWords words of shared memory, 16-byte aligned.
+__device__ __forceinline__ void init(Consts& K, uint32_t* scratch) {
     const int l = lane();
     K.p = limb_of(fq::kP);
     K.p2 = limb_of(fq::k2P);
+    const uint32_t q = limb_of(kPInvNeg);
     // 4p = 2 (2p): limbs of 2p shifted left by one bit across lanes
     const uint32_t below = __shfl_up_sync(kFull, K.p2, 1);
     K.p4 = l < 12 ? (K.p2 << 1) | (l ? below >> 31 : 0u) : 0u;
+    {   // 6p = 4p + 2p
+        const uint32_t s = K.p4 + K.p2;
+        K.p6 = keep12(normalize(s, (uint32_t)(s < K.p4)));
+    }
+#pragma unroll
+    for (int d = 0; d < 13; ++d) {
+        K.pc[d] = __shfl_sync(kFull, K.p, (l - d) & 31);   // negative sources wrap to lanes >= 20: zero
+        K.qc[d] = __shfl_sync(kFull, q, (l - d) & 31);
+    }
+    K.scratch = (uint32_t)__cvta_generic_to_shared(scratch);
+}
+
+// All twelve limbs of a distributed value in every lane, through the scratch slot
+// at byte offset `off` (written by lanes 0..11, then three 16-byte broadcast loads).
+__device__ __forceinline__ void broadcast(uint32_t (&x)[12], uint32_t v, const Consts& K, int off) {
+    const uint32_t a = K.scratch + off;
+    __syncwarp();                                   // earlier readers of the slot are done
+    if (lane() < 12) asm volatile("st.shared.u32 [%0], %1;" ::"r"(a + 4 * lane()), "r"(v) : "memory");
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(x[4 * q]), "=r"(x[4 * q + 1]), "=r"(x[4 * q + 2]), "=r"(x[4 * q + 3])
+                     : "r"(a + 16 * q)
+                     : "memory");
 }
 
 // y[d] = y_{lane - d} for d = 0..12 (y distributed; lanes past the twelve limbs and
@@ -71,35 +103,17 @@ __device__ __forceinline__ void spread(uint32_t y, uint32_t (&yc)[13]) {
     for (int d = 0; d < 13; ++d) yc[d] = __shfl_sync(kFull, y, (l - d) & 31);
 }
 
-// Lane k: sum_i lo(x_i y[i]) + hi(x_i y[i + 1]) for y[d] = y_{k-d}, as lo + 2^32 hi;
-// x distributed (its limbs broadcast by shuffles).
-__device__ __forceinline__ void columns(uint32_t x, const uint32_t (&y)[13], uint32_t& lo, uint32_t& hi) {
+// Lane k: sum_i lo(x_i y[i]) + hi(x_i y[i + 1]) for y[d] = y_{k-d}, as lo + 2^32 hi
+// (x in every lane's registers).
+__device__ __forceinline__ void columns(const uint32_t (&x)[12], const uint32_t (&y)[13], uint32_t& lo,
+                                        uint32_t& hi) {
     uint64_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
     for (int i = 0; i < 12; i += 2) {
-        const uint32_t x0 = __shfl_sync(kFull, x, i);
-        const uint32_t x1 = __shfl_sync(kFull, x, i + 1);
-        s0 += x0 * y[i];
-        s1 += __umulhi(x0, y[i + 1]);
-        s2 += x1 * y[i + 1];
-        s3 += __umulhi(x1, y[i + 2]);
-    }
-    const uint64_t s = (s0 + s1) + (s2 + s3);
-    lo = (uint32_t)s;
-    hi = (uint32_t)(s >> 32);
-}
-
-// The same with the compile-time x = p (P = true) or x = p'.
-template <bool P>
-__device__ __forceinline__ void columns_const(const uint32_t (&y)[13], uint32_t& lo, uint32_t& hi) {
-    uint64_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-    for (int i = 0; i < 12; i += 2) {
-        const uint32_t x0 = P ? p_limb(i) : pinv_limb(i), x1 = P ? p_limb(i + 1) : pinv_limb(i + 1);
-        s0 += x0 * y[i];
-        s1 += __umulhi(x0, y[i + 1]);
-        s2 += x1 * y[i + 1];
-        s3 += __umulhi(x1, y[i + 2]);
+        s0 += x[i] * y[i];
+        s1 += __umulhi(x[i], y[i + 1]);
+        s2 += x[i + 1] * y[i + 1];
+        s3 += __umulhi(x[i + 1], y[i + 2]);
     }
     const uint64_t s = (s0 + s1) + (s2 + s3);
     lo = (uint32_t)s;
@@ -125,24 +139,22 @@ __device__ __forceinline__ uint32_t normalize(uint32_t lo, uint32_t hi) {
 
 __device__ __forceinline__ uint32_t keep12(uint32_t v) { return lane() < 12 ? v : 0u; }
 
-// a b R^-1 mod p in [0, 2p) for a, b below 8p (distributed). Out of line: one copy
-// of the code for every call site of a kernel.
-static __device__ __noinline__ uint32_t mul_v(uint32_t a, uint32_t b) {
-    uint32_t yc[13], lo, hi;
+// a b R^-1 mod p in [0, 2p) for a, b below 8p (distributed).
+__device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b, const Consts& K) {
+    uint32_t x[12], yc[13], lo, hi;
     spread(b, yc);
-    columns(a, yc, lo, hi);
+    broadcast(x, a, K, 0);
+    columns(x, yc, lo, hi);
     const uint32_t t = normalize(lo, hi);           // T, lanes 0..23
-    spread(keep12(t), yc);
-    columns_const<false>(yc, lo, hi);
+    broadcast(x, keep12(t), K, 48);
+    columns(x, K.qc, lo, hi);
     const uint32_t m = keep12(normalize(lo, hi));   // T p' mod R
-    spread(m, yc);
-    columns_const<true>(yc, lo, hi);
+    broadcast(x, m, K, 96);
+    columns(x, K.pc, lo, hi);
     const uint64_t v = (uint64_t)lo + t;            // + T
     const uint32_t u = normalize((uint32_t)v, hi + (uint32_t)(v >> 32));
     return keep12(__shfl_down_sync(kFull, u, 12));  // (T + m p) / R
 }
-
-__device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b, const Consts&) { return mul_v(a, b); }
 
 // a + b (no reduction; for values that feed products).
 __device__ __forceinline__ uint32_t add_nr(uint32_t a, uint32_t b) {
@@ -155,6 +167,21 @@ __device__ __forceinline__ uint32_t add_nr(uint32_t a, uint32_t b) {
 __device__ __forceinline__ uint32_t sub_kp(uint32_t a, uint32_t b, uint32_t kp) {
     const int l = lane();
     const uint64_t v = (uint64_t)a + kp + (l < 12 ? ~b : 0u) + (l == 0 ? 1u : 0u);
+    return keep12(normalize((uint32_t)v, (uint32_t)(v >> 32)));
+}
+
+// sum of the P positive terms - sum of the Q negative terms + k p (kp = k p's limb
+// `lane`), with one carry resolution: each subtraction is a two's complement over
+// the twelve limbs, so the per-lane sum stays below 2^35 and its high part flows up.
+// Needs the result to be non-negative (the caller's k p covers the negative terms).
+template <int P, int Q>
+__device__ __forceinline__ uint32_t lincomb(const uint32_t (&pos)[P], const uint32_t (&neg)[Q], uint32_t kp) {
+    const int l = lane();
+    uint64_t v = (uint64_t)kp + (l == 0 ? (uint32_t)Q : 0u);
+#pragma unroll
+    for (int i = 0; i < P; ++i) v += pos[i];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v += l < 12 ? ~neg[i] : 0u;
     return keep12(normalize((uint32_t)v, (uint32_t)(v >> 32)));
 }
 

@@ -23,10 +23,12 @@ namespace wpt {
 using wfq::Consts;
 
 constexpr int kSlots = 18;
+// Shared words a group needs: the slots, then each warp's multiplication scratch.
+constexpr int kSharedWords = kSlots * 12 + 4 * wfq::kScratchWords;
 enum : int { X = 0, Y = 1, Z = 2, T = 3, ZZ = 2, ZZZ = 3 };
 
 struct Group {
-    uint32_t* s;   // kSlots x 12 words of shared memory
+    uint32_t* s;   // kSlots x 12 words of shared memory (then the warps' scratch)
     int w;         // warp index within the group, 0..3
     Consts K;
     uint32_t k;    // limb `lane` of the Edwards constant k = 2d (Montgomery form)
@@ -37,10 +39,11 @@ struct Group {
     __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) const { return wfq::mul(a, b, K); }
 };
 
+// slots: kSharedWords words of shared memory, 16-byte aligned.
 __device__ __forceinline__ void init(Group& g, uint32_t* slots) {
     g.s = slots;
     g.w = threadIdx.x >> 5;
-    wfq::init(g.K);
+    wfq::init(g.K, slots + kSlots * 12 + g.w * wfq::kScratchWords);
     g.k = wfq::limb_of(ed::kK);
     g.one = wfq::limb_of(fq::kOne);
 }
@@ -62,27 +65,31 @@ __device__ __forceinline__ void ed_set_inf(const Group& g) {   // (0, 1, 1, 0)
     __syncthreads();
 }
 
-// P = 2P (a = -1): level 1 {A = X^2, B = Y^2, Z^2, (X + Y)^2}; E = (X + Y)^2 - A - B,
-// G = B - A, H = -A - B, F = G - 2 Z^2; level 2 {E F, G H, E H, F G}.
+// P = 2P (a = -1): level 1 {A = X^2, B = Y^2, C = Z^2, X Y}; E = 2 X Y (= (X + Y)^2 -
+// A - B), G = B - A, H = -A - B, F = G - 2C, each one linear combination with a
+// single carry resolution; level 2 {E F, G H, E H, F G}. Ranges: E < 4p, G, H < 4p,
+// F = B - A - 2C + 6p < 8p.
 __device__ __forceinline__ void ed_dbl(const Group& g) {
     const Consts& K = g.K;
     switch (g.w) {
         case 0: g.st(4, g.mul(g.ld(X), g.ld(X))); break;
         case 1: g.st(5, g.mul(g.ld(Y), g.ld(Y))); break;
         case 2: g.st(6, g.mul(g.ld(Z), g.ld(Z))); break;
-        default: {
-            const uint32_t s = wfq::add_nr(g.ld(X), g.ld(Y));
-            g.st(7, g.mul(s, s));
-        }
+        default: g.st(7, g.mul(g.ld(X), g.ld(Y)));
     }
     __syncthreads();
+    const uint32_t A = g.ld(4), B = g.ld(5);
     switch (g.w) {
-        case 0: g.st(8, wfq::sub_nr2(wfq::sub_nr2(g.ld(7), g.ld(4), K), g.ld(5), K)); break;   // E < 6p
-        case 1: g.st(9, wfq::sub_nr2(g.ld(5), g.ld(4), K)); break;                            // G < 4p
-        case 2: g.st(10, wfq::sub_nr2(wfq::sub_nr2(0u, g.ld(4), K), g.ld(5), K)); break;      // H < 4p
+        case 0: {
+            const uint32_t xy = g.ld(7);
+            g.st(8, wfq::add_nr(xy, xy));                                            // E
+            break;
+        }
+        case 1: g.st(9, wfq::lincomb<1, 1>({B}, {A}, K.p2)); break;                  // G
+        case 2: g.st(10, wfq::lincomb<1, 2>({0u}, {A, B}, K.p4)); break;             // H
         default: {
-            const uint32_t G = wfq::sub_nr2(g.ld(5), g.ld(4), K);
-            g.st(11, wfq::sub_nr4(G, wfq::add_nr(g.ld(6), g.ld(6)), K));                    // F < 8p
+            const uint32_t C = g.ld(6);
+            g.st(11, wfq::lincomb<1, 3>({B}, {A, C, C}, K.p6));                      // F
         }
     }
     __syncthreads();
@@ -128,7 +135,9 @@ __device__ __forceinline__ Operand load_operand(const uint32_t* q, int ncoord) {
     return o;
 }
 
-// P += Q, Q stored (x, y, u = k x y): level 1 {A, B, C = T1 u2}, D = 2 Z1.
+// P += Q, Q stored (x, y, u = k x y) as loaded by load_operand(q, 3): level 1
+// {A, B, C = T1 u2} (the sums of Q's coordinates formed alongside those of P's),
+// D = 2 Z1.
 __device__ __forceinline__ void ed_madd(const Group& g, const Operand& q) {
     const Consts& K = g.K;
     switch (g.w) {
