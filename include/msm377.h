@@ -337,6 +337,16 @@ size_t msm_g1_resident_workspace_bytes(msm_points_t handle, size_t n, const msm_
 int msm_g1_resident(msm_points_t handle, size_t offset, size_t n, const uint32_t *scalars, uint32_t *out,
                     void *workspace, size_t workspace_bytes, const msm_opts *opts);
 
+/* End-to-end variant over a resident set (synchronous): copies scalars_host (8 u32
+ * per scalar, pageable or pinned) into the workspace, runs msm_g1_resident over
+ * points [offset, offset + n) and copies the 24-u32 affine result into out_host.
+ * This is a prover's step: the points (the committed bases) stay on the device,
+ * each step brings fresh scalars. workspace (device, 256-byte aligned) must hold
+ * msm_g1_resident_host_workspace_bytes(handle, n, opts). Returns the device status. */
+size_t msm_g1_resident_host_workspace_bytes(msm_points_t handle, size_t n, const msm_opts *opts);
+int msm_g1_resident_host(msm_points_t handle, size_t offset, size_t n, const uint32_t *scalars_host,
+                         uint32_t *out_host, void *workspace, size_t workspace_bytes, const msm_opts *opts);
+
 /* ------------------------------------------------------------------------
  * Batched MSM: many independent MSMs of uneven size in one call. The per-job
  * preparation, digits and sort run on library-owned helper streams; the bucket

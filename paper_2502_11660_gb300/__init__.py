@@ -421,6 +421,27 @@ class ResidentSet:
                                     ctypes.byref(o)))
         return out
 
+    def host_workspace(self, n: int) -> torch.Tensor:
+        nbytes = lib().msm_g1_resident_host_workspace_bytes(self._h, n, ctypes.byref(self._opts(0)))
+        if nbytes == 0:
+            raise MsmError(EINVAL, "bad resident MSM options")
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def msm_host(self, scalars: np.ndarray, offset: int = 0, workspace: torch.Tensor | None = None,
+                 stream=None) -> np.ndarray:
+        """Synchronous MSM over the set with host scalars (msm_g1_resident_host): the scalars
+        are copied in, the affine result (24 u32) copied out."""
+        sc = np.ascontiguousarray(scalars, dtype=np.uint32)
+        n = sc.shape[0]
+        if workspace is None:
+            workspace = self.host_workspace(n)
+        out = np.zeros(24, dtype=np.uint32)
+        o = self._opts(None if stream is None else stream)
+        check(lib().msm_g1_resident_host(self._h, offset, n, sc.ctypes.data_as(ctypes.c_void_p),
+                                         out.ctypes.data_as(ctypes.c_void_p), _p(workspace), workspace.numel(),
+                                         ctypes.byref(o)))
+        return out
+
     def close(self) -> None:
         if self._h is not None and self._h.value:
             check(lib().msm_points_destroy(self._h))

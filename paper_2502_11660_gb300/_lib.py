@@ -79,6 +79,9 @@ SIGNATURES = {
     "msm_points_data": (c_void, [c_void, c_size]),
     "msm_g1_resident_workspace_bytes": (c_size, [c_void, c_size, ctypes.POINTER(MsmOpts)]),
     "msm_g1_resident": (c_int, [c_void, c_size, c_size, c_u32p, c_u32p, c_void, c_size, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_resident_host_workspace_bytes": (c_size, [c_void, c_size, ctypes.POINTER(MsmOpts)]),
+    "msm_g1_resident_host": (c_int, [c_void, c_size, c_size, c_void, c_void, c_void, c_size,
+                                     ctypes.POINTER(MsmOpts)]),
 }
 
 

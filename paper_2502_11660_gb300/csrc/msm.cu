@@ -286,24 +286,17 @@ __device__ __forceinline__ fe shfl_fe(const fe& a, int src) {
     return r;
 }
 
-// Replaces den[j] (j < m, where ok[j]) by its inverse, with one inversion for
-// the whole warp: prefix and suffix products over the lanes' chunk products hand
-// every lane the inverse of its own product, from which it walks back through its
-// chunk. Every lane of the warp must call it (m may be 0; lanes carry 1 then).
-template <int K>
-__device__ __forceinline__ void warp_batch_inverse(fe (&den)[K], const bool (&ok)[K], int m) {
+// The inverse of every lane's acc (nonzero on every lane) with one field inversion
+// for the warp: prefix products P_l = acc_0 ... acc_l and suffix products
+// S_l = acc_{l+1} ... acc_31 over the lanes give acc_l^-1 = total^-1 P_{l-1} S_l.
+// Every lane of the warp must call it.
+__device__ __forceinline__ fe warp_lane_inverse(const fe& acc) {
     const int lane = threadIdx.x & 31;
     fe one;
     fq::set_one(one);
-    fe prefix[K];
-    fe acc = one;
-    for (int j = 0; j < m; ++j) {
-        prefix[j] = acc;                   // product of the valid den[0..j-1]
-        if (ok[j]) fq::mul(acc, acc, den[j]);
-    }
     fe pre = acc, y;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {  // P_l = acc_0 ... acc_l
+    for (int off = 1; off < 32; off <<= 1) {  // P_l
         y = shfl_fe_up(pre, off);
         if (lane >= off) fq::mul(pre, pre, y);
     }
@@ -313,7 +306,7 @@ __device__ __forceinline__ void warp_batch_inverse(fe (&den)[K], const bool (&ok
         y = shfl_fe_down(sacc, off);
         if (lane + off < 32) fq::mul(sacc, sacc, y);
     }
-    fe suf = shfl_fe_down(sacc, 1);           // S_l = acc_{l+1} ... acc_31
+    fe suf = shfl_fe_down(sacc, 1);           // S_l
     if (lane == 31) suf = one;
     const fe total = shfl_fe(pre, 31);
     fe tinv = one;
@@ -321,9 +314,26 @@ __device__ __forceinline__ void warp_batch_inverse(fe (&den)[K], const bool (&ok
     tinv = shfl_fe(tinv, 0);
     fe before = shfl_fe_up(pre, 1);           // P_{l-1}
     if (lane == 0) before = one;
-    fe inv;                                   // acc^-1 = total^-1 P_{l-1} S_l
+    fe inv;
     fq::mul(inv, tinv, before);
     fq::mul(inv, inv, suf);
+    return inv;
+}
+
+// Replaces den[j] (j < m, where ok[j]) by its inverse, with one inversion for
+// the whole warp: each lane multiplies its chunk, warp_lane_inverse hands it the
+// inverse of that product, from which it walks back through its chunk. Every lane
+// of the warp must call it (m may be 0; lanes carry 1 then).
+template <int K>
+__device__ __forceinline__ void warp_batch_inverse(fe (&den)[K], const bool (&ok)[K], int m) {
+    fe prefix[K];
+    fe acc;
+    fq::set_one(acc);
+    for (int j = 0; j < m; ++j) {
+        prefix[j] = acc;                   // product of the valid den[0..j-1]
+        if (ok[j]) fq::mul(acc, acc, den[j]);
+    }
+    fe inv = warp_lane_inverse(acc);
     for (int j = m - 1; j >= 0; --j) {
         if (!ok[j]) continue;
         fe dj;
@@ -440,24 +450,160 @@ __device__ __forceinline__ void store_ed_stored(uint4* o, fe x, fe y) {
     store_fe(o + 6, u);
 }
 
-// One warp covers 32 * kEdChunk consecutive stored points of rows [lo, hi); every
-// lane of every launched warp takes part in the shuffles (lanes past hi carry the
-// product 1).
-__global__ void __launch_bounds__(128, 4) k_prepare_ed(const uint4* __restrict__ in, uint4* __restrict__ out, size_t n,
-                                                    size_t np, size_t lo, size_t hi) {
-    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const size_t i0 = lo + t * kEdChunk;
-    const int m = i0 >= hi ? 0 : (int)(hi - i0 < (size_t)kEdChunk ? hi - i0 : (size_t)kEdChunk);
-    fe xe[kEdChunk], ye[kEdChunk];
-    bool ok[kEdChunk];
-    const bool pairs = np != n && (lo & 1) == 0 && (hi & 1) == 0;  // the same for the whole launch
-    ed_affine_chunk(in, n, np, i0, m, pairs, xe, ye, ok);
-    for (int j = 0; j < m; ++j) {
-        uint4* o = out + (size_t)ModelEdwards::kStored * (i0 + j);
-        if (ok[j])
-            store_ed_stored(o, xe[j], ye[j]);
-        else
-            store_ed_identity(o);
+__device__ __forceinline__ void load_fe_cg(fe& a, const uint4* p) {   // through L2 (written by this thread)
+    const uint4 u0 = __ldcg(p), u1 = __ldcg(p + 1), u2 = __ldcg(p + 2);
+    a.v[0] = u0.x; a.v[1] = u0.y; a.v[2] = u0.z; a.v[3] = u0.w;
+    a.v[4] = u1.x; a.v[5] = u1.y; a.v[6] = u1.z; a.v[7] = u1.w;
+    a.v[8] = u2.x; a.v[9] = u2.y; a.v[10] = u2.z; a.v[11] = u2.w;
+}
+
+// Stored Edwards rows of input points [a, b): row i, or rows 2i and 2i + 1 (P_i and
+// phi(P_i) = (beta x_i, y_i)) with GLV. Same map as above, arranged to cost fewer
+// multiplications and no local memory:
+//  * The inputs stay in standard form. Read as Montgomery residues, x and y stand
+//    for x / R and y / R; with the additive constants 1 and s entered in that same
+//    scale (the integers 1 and s) every quantity the map divides is scaled by the
+//    same power of R in numerator and denominator, so the Edwards coordinates come
+//    out exact, in Montgomery form, with no conversion multiplications.
+//  * GLV pair (P, phi(P)): one denominator t = y (a + s)(a' + s), a' = beta x + 1;
+//    from t^-1 and u = y (a + s): 1/(a' + s) = t^-1 u, w = t^-1 (a' + s) = 1/u,
+//    1/y = w (a + s), 1/(a + s) = w y; then x_e = c1 a / y, y_e = (a - s)/(a + s)
+//    per row. Single row: t = y (a + s), x_e = c1 a (a + s) / t,
+//    y_e = (a - s) y / t.
+//  * A warp takes batches of 32 K consecutive points (lane l: points
+//    base + 32 q + l, q < K) and inverts all their t with one field inversion
+//    (Montgomery's trick over the lane's K points, warp_lane_inverse over the
+//    lanes). Pass 1 writes each point's prefix product and the values pass 2
+//    needs into that point's own output rows; pass 2 reads them back (through
+//    L2) and overwrites the rows with the stored form.
+// A zero factor of t (the identity, or a point outside the map's domain) is
+// replaced by 1 and the rows it feeds become the Edwards identity.
+// s in standard form (the integer s, which is s / R as a Montgomery residue).
+__device__ __constant__ static const uint32_t kSStd[fq::N] = {
+    0xd09adc01u, 0x9c05824au, 0x0e1c7a7cu, 0x2e6bb28fu, 0xfc166427u, 0x2fe2cb65u,
+    0x183465a4u, 0x86ef0d33u, 0x15ccbf8eu, 0x59416eceu, 0x062d349eu, 0x0032d756u};
+
+__device__ __forceinline__ void add_one_raw(fe& r, const fe& a) {  // a + the integer 1
+    fe o;
+    fq::set_zero(o);
+    o.v[0] = 1;
+    fq::add(r, a, o);
+}
+
+__device__ __forceinline__ fe cst(const uint32_t (&c)[fq::N]) {
+    fe r;
+    ed::load_const(r, c);
+    return r;
+}
+
+__device__ __forceinline__ fe mont_one() {
+    fe r;
+    fq::set_one(r);
+    return r;
+}
+
+constexpr int kPrepBlocksPerSm = 3;
+
+template <bool kGlv>
+__global__ void __launch_bounds__(128, kPrepBlocksPerSm) k_prepare_ed(const uint4* __restrict__ in, uint4* out, size_t a, size_t b,
+                                                    int K) {
+    const int lane = threadIdx.x & 31;
+    const size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
+    const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const size_t per = 32 * (size_t)K;
+    const size_t nb = (b - a + per - 1) / per;
+    constexpr int kRows = kGlv ? 2 : 1;
+    constexpr int kVec = ModelEdwards::kStored;  // uint4 per stored row
+    for (size_t bt = warp; bt < nb; bt += warps) {
+        const size_t base = a + bt * per + lane;
+        fe acc = mont_one();
+        for (int q = 0; q < K; ++q) {            // pass 1
+            const size_t i = base + 32 * (size_t)q;
+            if (i >= b) break;
+            fe X, Y, A, D1, t;
+            load_fe(X, in + 6 * i);
+            load_fe(Y, in + 6 * i + 3);
+            const bool id = fq::is_zero_raw(X) && fq::is_zero_raw(Y);
+            add_one_raw(A, X);
+            fq::add(D1, A, cst(kSStd));
+            const bool okY = !id && !fq::is_zero(Y), ok1 = !id && !fq::is_zero(D1);
+            const fe Yf = okY ? Y : mont_one(), D1f = ok1 ? D1 : mont_one();
+            uint4* o = out + (size_t)kVec * kRows * i;
+            fq::mul(t, Yf, D1f);
+            if (kGlv) {
+                fe BX, D2;
+                fq::mul(BX, cst(kBeta), X);
+                add_one_raw(D2, BX);
+                fq::add(D2, D2, cst(kSStd));
+                const bool ok2 = !id && !fq::is_zero(D2);
+                store_fe(o + 6, t);              // u = y (a + s)
+                store_fe(o + 9, BX);
+                fq::mul(t, t, ok2 ? D2 : mont_one());
+            }
+            store_fe(o, acc);                    // prefix product
+            store_fe(o + 3, t);
+            fq::mul(acc, acc, t);
+        }
+        fe inv = warp_lane_inverse(acc);         // acc^-1 on every lane
+        for (int q = K - 1; q >= 0; --q) {       // pass 2
+            const size_t i = base + 32 * (size_t)q;
+            if (i >= b) continue;
+            uint4* o = out + (size_t)kVec * kRows * i;
+            fe X, Y, A, D1, pre, t, tinv;
+            load_fe(X, in + 6 * i);
+            load_fe(Y, in + 6 * i + 3);
+            load_fe_cg(pre, o);
+            load_fe_cg(t, o + 3);
+            fq::mul(tinv, inv, pre);             // t^-1
+            fq::mul(inv, inv, t);                // (prefix)^-1 for the next q down
+            const bool id = fq::is_zero_raw(X) && fq::is_zero_raw(Y);
+            add_one_raw(A, X);
+            fq::add(D1, A, cst(kSStd));
+            const bool okY = !id && !fq::is_zero(Y), ok1 = !id && !fq::is_zero(D1);
+            if (kGlv) {
+                fe u, BX, A2, D2, i2, w, iy, i1, cy;
+                load_fe_cg(u, o + 6);
+                load_fe_cg(BX, o + 9);
+                add_one_raw(A2, BX);
+                fq::add(D2, A2, cst(kSStd));
+                const bool ok2 = !id && !fq::is_zero(D2);
+                fq::mul(i2, tinv, u);                        // 1 / (a' + s)
+                fq::mul(w, tinv, ok2 ? D2 : mont_one());     // 1 / (y (a + s))
+                fq::mul(iy, w, ok1 ? D1 : mont_one());       // 1 / y
+                fq::mul(i1, w, okY ? Y : mont_one());        // 1 / (a + s)
+                fq::mul(cy, cst(ed::kC1), iy);               // c1 / y
+                fe xe, ye, d;
+                if (okY && ok1) {
+                    fq::mul(xe, A, cy);
+                    fq::sub(d, A, cst(kSStd));
+                    fq::mul(ye, d, i1);
+                    store_ed_stored(o, xe, ye);
+                } else {
+                    store_ed_identity(o);
+                }
+                if (okY && ok2) {
+                    fq::mul(xe, A2, cy);
+                    fq::sub(d, A2, cst(kSStd));
+                    fq::mul(ye, d, i2);
+                    store_ed_stored(o + kVec, xe, ye);
+                } else {
+                    store_ed_identity(o + kVec);
+                }
+            } else {
+                if (okY && ok1) {
+                    fe ct, xe, ye, d;
+                    fq::mul(ct, cst(ed::kC1), tinv);         // c1 / t
+                    fq::mul(xe, A, D1);
+                    fq::mul(xe, xe, ct);                     // c1 a (a + s) / t
+                    fq::sub(d, A, cst(kSStd));
+                    fq::mul(ye, d, Y);
+                    fq::mul(ye, ye, tinv);                   // (a - s) y / t
+                    store_ed_stored(o, xe, ye);
+                } else {
+                    store_ed_identity(o);
+                }
+            }
+        }
     }
 }
 
@@ -1502,15 +1648,32 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
 size_t stored_count(size_t n, uint32_t flags) { return (flags & MSM377_GLV) ? 2 * n : n; }
 int stored_vec(uint32_t flags) { return (flags & MSM377_EDWARDS) ? ModelEdwards::kStored : ModelXyzz::kStored; }
 
-// Stored rows of input points [a, b) (rows [a, b), or [2a, 2b) with GLV).
+// Stored rows of input points [a, b) (rows [a, b), or [2a, 2b) with GLV). The
+// Edwards kernel's points per lane are sized for `sizing` points (0: b - a), so the
+// launches of the chunks of one set, on separate streams, fill the GPU together.
 void launch_prepare_range(const uint4* in, uint4* out, size_t n, size_t a, size_t b, uint32_t flags,
-                          cudaStream_t s) {
+                          cudaStream_t s, size_t sizing = 0) {
     const size_t np = stored_count(n, flags);
     const size_t lo = stored_count(a, flags), hi = stored_count(b, flags);
     if (hi <= lo) return;
     if (flags & MSM377_EDWARDS) {
-        const size_t threads = (hi - lo + kEdChunk - 1) / kEdChunk;  // whole warps: grid_for rounds up to 128
-        k_prepare_ed<<<msm377::grid_for(threads, 128), 128, 0, s>>>(in, out, n, np, lo, hi);
+        // K points per lane: enough batches to give every resident warp (3 blocks of
+        // 4 warps per SM) about one, at least 2 and at most 32 points per lane
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t items = b - a, slots = (size_t)sms * kPrepBlocksPerSm * 4;
+        const size_t basis = sizing ? sizing : items;
+        size_t K = (basis + 32 * slots - 1) / (32 * slots);
+        K = K < 2 ? 2 : (K > 32 ? 32 : K);
+        const size_t batches = (items + 32 * K - 1) / (32 * K);
+        const size_t blocks = (batches + 3) / 4;
+        const size_t cap = (size_t)sms * kPrepBlocksPerSm;
+        const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
+        if (flags & MSM377_GLV)
+            k_prepare_ed<true><<<grid, 128, 0, s>>>(in, out, a, b, (int)K);
+        else
+            k_prepare_ed<false><<<grid, 128, 0, s>>>(in, out, a, b, (int)K);
     } else {
         k_prepare<<<msm377::grid_for(hi - lo, 256), 256, 0, s>>>(in, out, n, np, lo, hi);
     }
@@ -1887,7 +2050,9 @@ int enqueue_body(const Plan& p, const AccArgs& a, void* workspace, uint32_t* out
 // Library-owned helper streams for batched calls, per device, created once.
 constexpr int kMaxDevices = 64;
 constexpr int kAuxStreams = 16;
-constexpr int kHostChunks = 2;  // the copy is short (about 200 GB/s); fewer, full-size preparation launches
+constexpr int kHostChunks = 4;  // the copy (about 200 GB/s) is shorter than the preparation; small first chunk
+constexpr size_t kSplitPrepMin = size_t(1) << 15;  // msm_g1: prepare beside the head from this size on
+static_assert(1 + kHostChunks <= kAuxStreams, "msm_g1_host needs a copy stream and one stream per chunk");
 struct DeviceAux {
     bool ready = false;
     int sms = 0, acc_blocks_per_sm[2] = {0, 0};  // k_accumulate_batched per model
@@ -1971,10 +2136,35 @@ int msm_g1_run(const uint32_t* points, const uint32_t* scalars, size_t n, uint32
     if (!points || !scalars || !aligned(points, 16) || !aligned(scalars, 16))
         return set_error(MSM377_EINVAL, "msm_g1: points/scalars NULL or not 16-byte aligned");
     AccArgs a;
-    int r = enqueue_head(p, points, scalars, workspace, opts, s, &a);
-    if (r) return r;
+    // Standard-form points: their preparation (and validation) runs on the caller
+    // stream's high-priority helper while the digits and the sort, which need only
+    // the scalars, run on s; the accumulation waits for both.
+    const bool split = overlap && !prof && !(opts->flags & MSM377_POINTS_PREPARED) && n >= kSplitPrepMin;
+    const Overlap* ov = (overlap && (p.ngroups > 1 || split)) ? overlap_for(s) : nullptr;
+    int r;
+    if (split && ov) {
+        int* status = at<int>(workspace, p.off_status);
+        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, (1 + kMaxGroups) * sizeof(int), s));
+        MSM_CUDA_TRY(cudaEventRecord(ov->ev[0], s));
+        MSM_CUDA_TRY(cudaStreamWaitEvent(ov->hi, ov->ev[0], 0));
+        if (opts->flags & MSM377_VALIDATE) {
+            r = launch_validate(points, n, (opts->flags & (MSM377_EDWARDS | MSM377_GLV)) != 0, status, ov->hi);
+            if (r) return r;
+        }
+        uint4* prep = at<uint4>(workspace, p.off_points);
+        launch_prepare(reinterpret_cast<const uint4*>(points), prep, n, opts->flags, ov->hi);
+        MSM_CUDA_TRY(cudaEventRecord(ov->ev[1], ov->hi));
+        msm_opts op = *opts;
+        op.flags |= MSM377_POINTS_PREPARED;  // the plan keeps the prepared region in the workspace
+        r = enqueue_head(p, reinterpret_cast<const uint32_t*>(prep), scalars, workspace, &op, s, &a, false);
+        if (r) return r;
+        MSM_CUDA_TRY(cudaStreamWaitEvent(s, ov->ev[1], 0));
+    } else {
+        r = enqueue_head(p, points, scalars, workspace, opts, s, &a);
+        if (r) return r;
+    }
     if (prof) profile_mark(s);
-    return enqueue_body(p, a, workspace, out, s, (overlap && p.ngroups > 1) ? overlap_for(s) : nullptr, prof);
+    return enqueue_body(p, a, workspace, out, s, p.ngroups > 1 ? ov : nullptr, prof);
 }
 
 }  // namespace msm377
@@ -2138,21 +2328,23 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
         MSM_CUDA_TRY(cudaMemcpyAsync(out_host, d_out, 24 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         return msm_g1_status(workspace, &o);
     }
-    // The points travel in chunks on one helper stream and are prepared chunk by
-    // chunk on another, while the scalars' copy, digits and bucket sort run on the
-    // caller's stream; the accumulation waits for the last prepared chunk.
+    // The points travel in chunks on one helper stream and each chunk is prepared
+    // on a helper stream of its own as soon as it has arrived (the chunks' launches
+    // are sized to fill the GPU together), while the scalars' copy, digits and
+    // bucket sort run on the caller's stream; the accumulation waits for them all.
     DeviceAux* aux = nullptr;
     int r = device_aux(&aux);
     if (r) return r;
-    cudaStream_t sc = aux->st[0], sp = aux->st[1];
+    cudaStream_t sc = aux->st[0];
     MSM_CUDA_TRY(cudaMemsetAsync(at<int>(workspace, p.off_status), 0, (1 + kMaxGroups) * sizeof(int), s));  // before the fork
-    r = fork_from(aux, s, 2);
+    r = fork_from(aux, s, 1 + kHostChunks);
     if (r) return r;
     uint4* prep = at<uint4>(workspace, p.off_points);
     const size_t per = (n + kHostChunks - 1) / kHostChunks;
     for (int k = 0; k < kHostChunks; ++k) {
         const size_t a = (size_t)k * per, b = a + per < n ? a + per : n;
         if (a >= b) break;
+        cudaStream_t sp = aux->st[1 + k];
         MSM_CUDA_TRY(cudaMemcpyAsync(d_pts + 24 * a, points_host + 24 * a, (b - a) * 96, cudaMemcpyHostToDevice, sc));
         MSM_CUDA_TRY(cudaEventRecord(aux->chunk[k], sc));
         MSM_CUDA_TRY(cudaStreamWaitEvent(sp, aux->chunk[k], 0));
@@ -2161,7 +2353,7 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
                                 at<int>(workspace, p.off_status), sp);
             if (r) return r;
         }
-        launch_prepare_range(reinterpret_cast<const uint4*>(d_pts), prep, n, a, b, o.flags, sp);
+        launch_prepare_range(reinterpret_cast<const uint4*>(d_pts), prep, n, a, b, o.flags, sp, n);
     }
     MSM_CUDA_TRY(cudaMemcpyAsync(d_sc, scalars_host, n * 32, cudaMemcpyHostToDevice, s));
     msm_opts op = o;
@@ -2169,7 +2361,7 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
     AccArgs acc;
     r = enqueue_head(p, reinterpret_cast<const uint32_t*>(prep), d_sc, workspace, &op, s, &acc, false);
     if (r) return r;
-    r = join_into(aux, s, 2);
+    r = join_into(aux, s, 1 + kHostChunks);
     if (r) return r;
     r = enqueue_body(p, acc, workspace, d_out, s, p.ngroups > 1 ? overlap_for(s) : nullptr, false);
     if (r) return r;

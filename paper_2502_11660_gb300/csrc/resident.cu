@@ -259,3 +259,34 @@ extern "C" int msm_g1_resident(msm_points_t handle, size_t offset, size_t n, con
     if (r) return r;
     return msm_g1(msm_points_data(handle, offset), scalars, n, out, workspace, workspace_bytes, &o);
 }
+
+extern "C" size_t msm_g1_resident_host_workspace_bytes(msm_points_t handle, size_t n, const msm_opts* opts) {
+    const size_t core = msm_g1_resident_workspace_bytes(handle, n, opts);
+    if (!core) return 0;
+    return align_up(core, 256) + align_up(n * 32, 256) + 256;
+}
+
+extern "C" int msm_g1_resident_host(msm_points_t handle, size_t offset, size_t n, const uint32_t* scalars_host,
+                                    uint32_t* out_host, void* workspace, size_t workspace_bytes,
+                                    const msm_opts* opts) {
+    if (!handle || !opts || !out_host || !workspace)
+        return set_error(MSM377_EINVAL, "msm_g1_resident_host: NULL argument");
+    if (n && !scalars_host) return set_error(MSM377_EINVAL, "msm_g1_resident_host: scalars_host is NULL");
+    if (opts->flags & MSM377_PROFILE)
+        return set_error(MSM377_EINVAL, "msm_g1_resident_host: MSM377_PROFILE is not available here");
+    const size_t need = msm_g1_resident_host_workspace_bytes(handle, n, opts);
+    if (!need) return set_error(MSM377_EINVAL, "msm_g1_resident_host: bad options");
+    if (workspace_bytes < need)
+        return set_error(MSM377_ENOMEM, "msm_g1_resident_host: workspace %zu bytes, need %zu", workspace_bytes, need);
+    if (!aligned(workspace, 256)) return set_error(MSM377_EINVAL, "msm_g1_resident_host: workspace not 256-byte aligned");
+    const size_t core = align_up(msm_g1_resident_workspace_bytes(handle, n, opts), 256);
+    char* base = static_cast<char*>(workspace);
+    uint32_t* d_sc = reinterpret_cast<uint32_t*>(base + core);
+    uint32_t* d_out = reinterpret_cast<uint32_t*>(base + core + align_up(n * 32, 256));
+    cudaStream_t s = as_stream(opts->stream);
+    if (n) MSM_CUDA_TRY(cudaMemcpyAsync(d_sc, scalars_host, n * 32, cudaMemcpyHostToDevice, s));
+    int r = msm_g1_resident(handle, offset, n, d_sc, d_out, workspace, core, opts);
+    if (r) return r;
+    MSM_CUDA_TRY(cudaMemcpyAsync(out_host, d_out, 24 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    return msm_g1_status(workspace, opts);
+}

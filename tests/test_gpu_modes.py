@@ -367,3 +367,38 @@ def test_window_groups_on_concurrent_streams():
     pkg.msm_g1_set_schedule(18, edwards=True, glv=True)
     for (a, s, _), o in zip(data, outs):
         assert g1.from_limbs(pkg.to_host(o)) == closed_form_limbs(s, a)
+
+
+@pytest.mark.parametrize("edw,split", [(False, False)] + MODES, ids=["xyzz"] + MODE_IDS)
+def test_preparation_beside_the_head(edw, split):
+    """From 2^15 standard-form points on, msm_g1 prepares them on a helper stream while
+    the digits and the sort run; msm_g1_host prepares each copied chunk on a stream of
+    its own. A ragged size with the identity, a duplicate and a negated pair, with
+    and without validation, and a point outside the subgroup under validation."""
+    n = 40_001
+    a, s, pts = msm_inputs(n, tag=515)
+    a, s, pts = a.copy(), s.copy(), pts.copy()
+    pts[0] = 0
+    s[0] = 0
+    pts[n - 1] = 0
+    s[n - 1] = 0
+    pts[20000] = pts[20001]
+    s[20000] = s[20001]
+    pts[33333, :12] = pts[33334, :12]
+    pts[33333, 12:] = synth.int_to_limbs((fq.P - synth.limbs_to_int(pts[33334, 12:])) % fq.P, 12)
+    s[33333] = synth.int_to_limbs((fq.R - synth.limbs_to_int(s[33334])) % fq.R, 8)
+    want = closed_form_limbs(s, a)
+    kw = dict(scalar_bits=253, edwards=edw, glv=split)
+    ws = pkg.msm_g1_workspace(n, **kw)
+    for validate in (False, True):
+        out = pkg.msm_g1(pkg.to_device(pts), pkg.to_device(a), workspace=ws, validate=validate, **kw)
+        assert g1.from_limbs(pkg.to_host(out)) == want
+        assert pkg.msm_g1_status(ws) == 0
+        assert g1.from_limbs(pkg.msm_g1_host(pts, a, validate=validate, **kw)) == want
+    cof = pts.copy()
+    Q = g1.random_point(0xBADC0DE)
+    cof[n - 2] = np.array(g1.to_limbs(Q), dtype=np.uint32)
+    pkg.msm_g1(pkg.to_device(cof), pkg.to_device(a), workspace=ws, validate=True, **kw)
+    assert pkg.msm_g1_status(ws) == (pkg.ENOTONCURVE if (edw or split) else 0)
+    out = pkg.msm_g1(pkg.to_device(pts), pkg.to_device(a), workspace=ws, **kw)
+    assert g1.from_limbs(pkg.to_host(out)) == want and pkg.msm_g1_status(ws) == 0

@@ -164,3 +164,16 @@ def test_validate_in_msm_g1_host_call_and_set_creation():
     rs = pkg.ResidentSet(pkg.to_device(pts), edwards=True, glv=True, validate=True)
     assert g1.from_limbs(pkg.to_host(rs.msm(pkg.to_device(a)))) == want
     rs.close()
+
+
+def test_resident_host_call_equals_the_device_call():
+    """msm_g1_resident_host (host scalars in, host result out) over slices of a resident set."""
+    n = 3000
+    a, s, pts = msm_inputs(n, tag=506)
+    rs = pkg.ResidentSet(pkg.to_device(pts), edwards=True, glv=True)
+    ws = rs.host_workspace(n)
+    for off, m in ((0, n), (1000, 1500), (2999, 1)):
+        got = rs.msm_host(a[off:off + m], offset=off, workspace=ws)
+        assert g1.from_limbs(got) == closed_form_limbs(s[off:off + m], a[off:off + m]), (off, m)
+    assert not rs.msm_host(a[:0], offset=0, workspace=ws).any()      # n = 0: O
+    rs.close()
