@@ -502,7 +502,7 @@ __device__ __forceinline__ fe mont_one() {
     return r;
 }
 
-constexpr int kPrepBlocksPerSm = 3;
+constexpr int kPrepBlocksPerSm = 2;
 
 template <bool kGlv>
 __global__ void __launch_bounds__(128, kPrepBlocksPerSm) k_prepare_ed(const uint4* __restrict__ in, uint4* out, size_t a, size_t b,
@@ -1657,7 +1657,7 @@ void launch_prepare_range(const uint4* in, uint4* out, size_t n, size_t a, size_
     const size_t lo = stored_count(a, flags), hi = stored_count(b, flags);
     if (hi <= lo) return;
     if (flags & MSM377_EDWARDS) {
-        // K points per lane: enough batches to give every resident warp (3 blocks of
+        // K points per lane: enough batches to give every resident warp (2 blocks of
         // 4 warps per SM) about one, at least 2 and at most 32 points per lane
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
