@@ -807,7 +807,7 @@ def batch_ops(h, peak, hbm_peak, n=1 << 24):
                     ("karatsuba", pkg.FQMUL_KARATSUBA), ("carrysave", pkg.FQMUL_CARRYSAVE),
                     ("cios_twopass", pkg.FQMUL_CIOS_TWOPASS), ("cios_doublerow", pkg.FQMUL_CIOS_DOUBLEROW),
                     ("warp_per_product", pkg.FQMUL_WARP), ("paper_25bit_loose_barrett", pkg.FQMUL_PAPER),
-                    ("fips", pkg.FQMUL_FIPS)):
+                    ("fips", pkg.FQMUL_FIPS), ("cios_singlerow", pkg.FQMUL_CIOS_SINGLEROW)):
         ms_v = timed(lambda v=v: pkg.fq_mul_batch_variant(mA, mB, v, out=out))
         variants[name] = {"ms_2^24": ms_v, "mul_per_s": n / (ms_v / 1e3)}
     del mA, mB, out

@@ -75,7 +75,9 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
 /* Alternative multiplications, for comparison with fq_mul_batch's Montgomery CIOS
  * (same layout: structure-of-arrays [12][n], 16-byte aligned device arrays,
  * operands in [0, p), result canonical in [0, p)). The MSM does not use them.
- *   MSM377_FQMUL_CIOS      a b 2^-384 mod p, word-serial Montgomery (the library's)
+ *   MSM377_FQMUL_CIOS      a b 2^-384 mod p, word-serial Montgomery two words per step
+ *                          with the quotient digits kept as multiplications (the
+ *                          library's)
  *   MSM377_FQMUL_BARRETT   a b mod p on standard-form operands: the paper's Barrett
  *                          reduction (Sec. III-C), k = 377, mu = floor(2^754 / p),
  *                          remainder in [0, 3p) then at most two subtractions of p
@@ -89,8 +91,11 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
  *                          high halves (the library's multiplication runs each
  *                          row as two independent chains of adjacent low/high
  *                          halves of the even- and odd-indexed limbs' products)
- *   MSM377_FQMUL_CIOS_DOUBLEROW a b 2^-384 mod p, the same product two rows and two
- *                          quotient digits per step (accumulators shift two limbs)
+ *   MSM377_FQMUL_CIOS_DOUBLEROW a b 2^-384 mod p, the library's double-row steps with
+ *                          the digits written as plain negations (which the compiler
+ *                          folds into the digit products)
+ *   MSM377_FQMUL_CIOS_SINGLEROW a b 2^-384 mod p, one row and one digit per step, the
+ *                          library's earlier form
  *   MSM377_FQMUL_WARP      a b 2^-384 mod p with one warp per product: lane j holds
  *                          limb j, three column products (a b, the Montgomery
  *                          quotient, its multiple of p) with warp-wide carry
@@ -118,6 +123,7 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
 #define MSM377_FQMUL_WARP 6
 #define MSM377_FQMUL_PAPER 7
 #define MSM377_FQMUL_FIPS 8
+#define MSM377_FQMUL_CIOS_SINGLEROW 9
 int fq_mul_batch_variant(const uint32_t *a, const uint32_t *b, uint32_t *out, size_t n, int variant,
                          void *stream);
 

@@ -38,7 +38,7 @@ __all__ = [
     "imad_probe", "lib", "last_error", "profile_last", "launch_count", "MSM_STAGES", "PROFILE",
     "MsmJob", "msm_g1_batched", "msm_g1_batched_workspace", "EDWARDS", "GLV",
     "msm_points_prepared_bytes", "padd_chain", "fq_mul_batch_variant", "FQMUL_CIOS", "FQMUL_BARRETT",
-    "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE", "FQMUL_CIOS_TWOPASS", "FQMUL_CIOS_DOUBLEROW", "FQMUL_WARP", "FQMUL_PAPER", "FQMUL_FIPS", "PRECOMPUTED", "RADIX_SORT", "msm_points_precompute",
+    "FQMUL_KARATSUBA", "FQMUL_CARRYSAVE", "FQMUL_CIOS_TWOPASS", "FQMUL_CIOS_DOUBLEROW", "FQMUL_WARP", "FQMUL_PAPER", "FQMUL_FIPS", "FQMUL_CIOS_SINGLEROW", "PRECOMPUTED", "RADIX_SORT", "msm_points_precompute",
     "msm_points_precomputed_bytes", "VALIDATE", "ENOTONCURVE", "ERANGE", "ResidentSet", "msm_points_validate",
 ]
 
@@ -83,6 +83,7 @@ FQMUL_CIOS, FQMUL_BARRETT, FQMUL_KARATSUBA, FQMUL_CARRYSAVE, FQMUL_CIOS_TWOPASS,
 FQMUL_WARP = 6
 FQMUL_PAPER = 7
 FQMUL_FIPS = 8
+FQMUL_CIOS_SINGLEROW = 9
 
 
 def fq_mul_batch_variant(a: torch.Tensor, b: torch.Tensor, variant: int, out: torch.Tensor | None = None,

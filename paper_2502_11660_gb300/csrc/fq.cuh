@@ -1,12 +1,30 @@
 // Fq = GF(p), p the 377-bit BLS12-377 base-field prime, on sm_103a.
 //
 // Elements are 12 little-endian 32-bit limbs in Montgomery form x*R mod p with
-// R = 2^384. Multiplication is word-serial Montgomery (CIOS): for each limb a_i
-// the row a_i*b is added, then m = -t_0 (because -p^-1 = 0xffffffff mod 2^32,
-// p = 1 mod 2^46) and the row m*p is added, and the accumulator drops one word.
-// Each row runs as two independent mad.lo.cc / madc.hi.cc carry chains (the
-// products with the even- and with the odd-indexed limbs; see mul_inl). Every
-// chain sits in one asm statement so the carry flag never crosses statements.
+// R = 2^384. Multiplication is word-serial Montgomery (CIOS) taken two words at a
+// time: each step adds the rows a_2s*b and a_2s+1*b, then the two quotient digits
+// m0 = -t_0 and m1 = -t_1 (-p^-1 = 0xffffffff mod 2^32 because p = 1 mod 2^46)
+// with their rows m*p, and the accumulator drops two words (mont_dstep). Every row
+// runs as mad.lo.cc / madc.hi.cc carry chains of adjacent low/high halves (the
+// products with the even- and with the odd-indexed limbs in two accumulators);
+// every chain sits in one asm statement so the carry flag never crosses
+// statements.
+//
+// Two facts about how these chains compile on sm_103a, measured with ncu opcode
+// counts (a chain pair compiles either to one fused 64-bit multiply-add, four
+// cycles of the multiply pipe, or to a low and a high multiply, six cycles):
+//  * A pair fuses only when its 64-bit accumulator sits in an aligned register
+//    pair. Dropping one word per row misaligns every other row (the compiler then
+//    inserts a move per product); dropping two words per step keeps every pair
+//    aligned.
+//  * The compiler folds a negation into the multiplications it feeds, and a
+//    folded m*p_j does not fuse. So the digits are formed as t_k * (-1) with the
+//    -1 read through a volatile constant load (neg_one), which the compiler cannot
+//    see through: one extra multiply per digit, and all 276 products per
+//    multiplication fuse.
+// Against one word per row with m = -t_0 (mul_singlerow_inl, the earlier form):
+// 1128 instead of 1368 multiply-pipe cycles per product, and the MSM's
+// accumulation 4.63 -> 4.22 ms at 2^20 points.
 //
 // mul() is one out-of-line function. A point operation makes 10-14 calls; with
 // the body inlined at every call site the code of one point addition is about
@@ -21,10 +39,7 @@
 // All values kept in registers or memory by the curve code live in [0, 2p);
 // add/sub fold back into [0, 2p) with one masked correction of 2p, so every
 // product satisfies a*b < 4p^2 < p*R (R/p > 152). canon() maps [0, 2p) to [0, p).
-// Accumulator bound: with a, b < 2p < 2^378 a row adds less than 2^411 to each
-// of the two chains, whose values stay below 2^380 after each shift and below
-// 2^412 before it, so 13 words hold them; the result, below 2p, fits the 12
-// words of e + 2^32 o.
+// Accumulator bounds: see mont_dstep.
 //
 // (A carry-save variant in the style of the paper's Sec. III-D -- 16 digits of
 // 24 bits, 64-bit mad.wide column sums, two coarse carry rounds -- was built and
@@ -96,7 +111,10 @@ struct MontAcc {
     uint32_t e[13], o[13];
 };
 
-// One row: t += x b, m = -e[0], t += m p, shift (see mul_inl).
+// One row: t += x b, m = -e[0], t += m p, shift (mul_singlerow_inl). Within a row
+// the two accumulators e (even-indexed limbs of b) and o (odd, one word up) are
+// independent chains; with a, b < 2p a row adds less than 2^411 to each, whose
+// values stay below 2^380 after the shift and below 2^412 before it (13 words).
 __device__ __forceinline__ void mont_row(MontAcc& t, uint32_t x, const uint32_t* b) {
     uint32_t* e = t.e;
     uint32_t* o = t.o;
@@ -197,7 +215,237 @@ __device__ __forceinline__ void mont_final(fe& r, const MontAcc& t) {
           "r"(o[7]), "r"(o[8]), "r"(o[9]), "r"(o[10]));
 }
 
+// Two rows and two quotient digits per step, accumulators shifted by two limbs, so
+// the register pair holding the low and high half of one partial product keeps its
+// alignment from step to step.
+//
+// The running value is E + 2^32 O: E[k] at limb k holds the partial products that
+// start at an even limb (a low half at 2j, its high half at 2j + 1), O[k] at limb
+// k + 1 those that start at an odd limb. One step, for x0 = a_2s, x1 = a_2s+1:
+//   E += x0 b_even,  O += x0 b_odd,  O += x1 b_even,  E += 2^64 x1 b_odd (E[2..]),
+//   m0 = -E[0];  O += m0 p_odd;  E += m0 p_even, where p_0 = 1 leaves the high
+//   half of m0 p_0 zero and that slot adds O[0] (so limb 1 is held by E alone);
+//   m1 = -E[1];  E += 2^32 m1 (at limb 1) + 2^64 m1 p_odd (E[2..]);
+//   O += m1 p_even without its p_0 term (O[2..], limbs 3 up);
+//   then O[1] (limb 2) and the carry of limb 1 move into E, E[0] = E[1] = 0, and
+//   both accumulators drop two limbs.
+// The quotient digits are those of the word-serial form (the pair (m0, m1) is the
+// two-limb digit -t p^-1 mod 2^64), so the lazy result in [0, 2p) is the same.
+// Bounds: E stays below 2^444 and O below 2^413 within a step, so E[0..13] and
+// O[0..13] hold them and the top carries are zero.
+struct MontAccD {
+    uint32_t e[14], o[14];
+};
+
+__device__ __forceinline__ void mont_dstep(MontAccD& t, uint32_t x0, uint32_t x1, const uint32_t* b, uint32_t neg1) {
+    uint32_t* E = t.e;
+    uint32_t* O = t.o;
+    // E[0..11] += x0 b_even, carry into E[12..13]
+    asm("mad.lo.cc.u32 %0, %14, %15, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, %16, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, %16, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, %18, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, %18, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, %19, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, %19, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, %20, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, %20, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(E[0]), "+r"(E[1]), "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]),
+          "+r"(E[8]), "+r"(E[9]), "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(x0), "r"(b[0]), "r"(b[2]), "r"(b[4]), "r"(b[6]), "r"(b[8]), "r"(b[10]));
+    // O[0..11] += x0 b_odd, carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %14, %15, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, %16, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, %16, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, %18, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, %18, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, %19, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, %19, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, %20, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, %20, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(O[0]), "+r"(O[1]), "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]),
+          "+r"(O[8]), "+r"(O[9]), "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(x0), "r"(b[1]), "r"(b[3]), "r"(b[5]), "r"(b[7]), "r"(b[9]), "r"(b[11]));
+    // O[0..11] += x1 b_even (limbs 1..12), carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %14, %15, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, %15, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, %16, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, %16, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, %17, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, %18, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, %18, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, %19, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, %19, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, %20, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, %20, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(O[0]), "+r"(O[1]), "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]),
+          "+r"(O[8]), "+r"(O[9]), "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(x1), "r"(b[0]), "r"(b[2]), "r"(b[4]), "r"(b[6]), "r"(b[8]), "r"(b[10]));
+    // E[2..13] += x1 b_odd (limbs 2..13); no carry leaves E[13]
+    asm("mad.lo.cc.u32 %0, %12, %13, %0;\n\t"
+        "madc.hi.cc.u32 %1, %12, %13, %1;\n\t"
+        "madc.lo.cc.u32 %2, %12, %14, %2;\n\t"
+        "madc.hi.cc.u32 %3, %12, %14, %3;\n\t"
+        "madc.lo.cc.u32 %4, %12, %15, %4;\n\t"
+        "madc.hi.cc.u32 %5, %12, %15, %5;\n\t"
+        "madc.lo.cc.u32 %6, %12, %16, %6;\n\t"
+        "madc.hi.cc.u32 %7, %12, %16, %7;\n\t"
+        "madc.lo.cc.u32 %8, %12, %17, %8;\n\t"
+        "madc.hi.cc.u32 %9, %12, %17, %9;\n\t"
+        "madc.lo.cc.u32 %10, %12, %18, %10;\n\t"
+        "madc.hi.u32 %11, %12, %18, %11;"
+        : "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]), "+r"(E[8]), "+r"(E[9]),
+          "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(x1), "r"(b[1]), "r"(b[3]), "r"(b[5]), "r"(b[7]), "r"(b[9]), "r"(b[11]));
+    const uint32_t m0 = E[0] * neg1;   // -E[0], kept a multiplication (neg_one)
+    // O[0..11] += m0 p_odd (limbs 1..12), carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %14, 0x8508c000, %0;\n\t"
+        "madc.hi.cc.u32 %1, %14, 0x8508c000, %1;\n\t"
+        "madc.lo.cc.u32 %2, %14, 0x170b5d44, %2;\n\t"
+        "madc.hi.cc.u32 %3, %14, 0x170b5d44, %3;\n\t"
+        "madc.lo.cc.u32 %4, %14, 0x1ef3622f, %4;\n\t"
+        "madc.hi.cc.u32 %5, %14, 0x1ef3622f, %5;\n\t"
+        "madc.lo.cc.u32 %6, %14, 0x1a22d9f3, %6;\n\t"
+        "madc.hi.cc.u32 %7, %14, 0x1a22d9f3, %7;\n\t"
+        "madc.lo.cc.u32 %8, %14, 0xc63b05c0, %8;\n\t"
+        "madc.hi.cc.u32 %9, %14, 0xc63b05c0, %9;\n\t"
+        "madc.lo.cc.u32 %10, %14, 0x01ae3a46, %10;\n\t"
+        "madc.hi.cc.u32 %11, %14, 0x01ae3a46, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(O[0]), "+r"(O[1]), "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]),
+          "+r"(O[8]), "+r"(O[9]), "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(m0));
+    // E[0..11] += m0 p_even: limb 0 takes m0 (p_0 = 1), limb 1 takes O[0] in the
+    // zero high half of m0 p_0; carry into E[12..13]
+    asm("add.cc.u32 %0, %0, %15;\n\t"
+        "addc.cc.u32 %1, %1, %14;\n\t"
+        "madc.lo.cc.u32 %2, %15, 0x30000000, %2;\n\t"
+        "madc.hi.cc.u32 %3, %15, 0x30000000, %3;\n\t"
+        "madc.lo.cc.u32 %4, %15, 0xba094800, %4;\n\t"
+        "madc.hi.cc.u32 %5, %15, 0xba094800, %5;\n\t"
+        "madc.lo.cc.u32 %6, %15, 0x00f5138f, %6;\n\t"
+        "madc.hi.cc.u32 %7, %15, 0x00f5138f, %7;\n\t"
+        "madc.lo.cc.u32 %8, %15, 0x6ca1493b, %8;\n\t"
+        "madc.hi.cc.u32 %9, %15, 0x6ca1493b, %9;\n\t"
+        "madc.lo.cc.u32 %10, %15, 0x17c510ea, %10;\n\t"
+        "madc.hi.cc.u32 %11, %15, 0x17c510ea, %11;\n\t"
+        "addc.cc.u32 %12, %12, 0;\n\t"
+        "addc.u32 %13, %13, 0;"
+        : "+r"(E[0]), "+r"(E[1]), "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]),
+          "+r"(E[8]), "+r"(E[9]), "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(O[0]), "r"(m0));
+    const uint32_t m1 = E[1] * neg1;
+    // E[1..13] += m1 (limb 1, p_0 = 1) + 2^64 m1 p_odd (limbs 2..13): E[1] becomes 0
+    asm("add.cc.u32 %0, %0, %13;\n\t"
+        "madc.lo.cc.u32 %1, %13, 0x8508c000, %1;\n\t"
+        "madc.hi.cc.u32 %2, %13, 0x8508c000, %2;\n\t"
+        "madc.lo.cc.u32 %3, %13, 0x170b5d44, %3;\n\t"
+        "madc.hi.cc.u32 %4, %13, 0x170b5d44, %4;\n\t"
+        "madc.lo.cc.u32 %5, %13, 0x1ef3622f, %5;\n\t"
+        "madc.hi.cc.u32 %6, %13, 0x1ef3622f, %6;\n\t"
+        "madc.lo.cc.u32 %7, %13, 0x1a22d9f3, %7;\n\t"
+        "madc.hi.cc.u32 %8, %13, 0x1a22d9f3, %8;\n\t"
+        "madc.lo.cc.u32 %9, %13, 0xc63b05c0, %9;\n\t"
+        "madc.hi.cc.u32 %10, %13, 0xc63b05c0, %10;\n\t"
+        "madc.lo.cc.u32 %11, %13, 0x01ae3a46, %11;\n\t"
+        "madc.hi.u32 %12, %13, 0x01ae3a46, %12;"
+        : "+r"(E[1]), "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]), "+r"(E[8]),
+          "+r"(E[9]), "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(m1));
+    // O[2..11] += m1 (p_2 .. p_10) at limbs 3..12, carry into O[12..13]
+    asm("mad.lo.cc.u32 %0, %12, 0x30000000, %0;\n\t"
+        "madc.hi.cc.u32 %1, %12, 0x30000000, %1;\n\t"
+        "madc.lo.cc.u32 %2, %12, 0xba094800, %2;\n\t"
+        "madc.hi.cc.u32 %3, %12, 0xba094800, %3;\n\t"
+        "madc.lo.cc.u32 %4, %12, 0x00f5138f, %4;\n\t"
+        "madc.hi.cc.u32 %5, %12, 0x00f5138f, %5;\n\t"
+        "madc.lo.cc.u32 %6, %12, 0x6ca1493b, %6;\n\t"
+        "madc.hi.cc.u32 %7, %12, 0x6ca1493b, %7;\n\t"
+        "madc.lo.cc.u32 %8, %12, 0x17c510ea, %8;\n\t"
+        "madc.hi.cc.u32 %9, %12, 0x17c510ea, %9;\n\t"
+        "addc.cc.u32 %10, %10, 0;\n\t"
+        "addc.u32 %11, %11, 0;"
+        : "+r"(O[2]), "+r"(O[3]), "+r"(O[4]), "+r"(O[5]), "+r"(O[6]), "+r"(O[7]), "+r"(O[8]), "+r"(O[9]),
+          "+r"(O[10]), "+r"(O[11]), "+r"(O[12]), "+r"(O[13])
+        : "r"(m1));
+    // limb 1 is zero overall (E[1] = 0 now; O[0] was added into it); O[1] (limb 2)
+    // moves into E[2] with the carry up E
+    asm("add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.cc.u32 %3, %3, 0;\n\t"
+        "addc.cc.u32 %4, %4, 0;\n\t"
+        "addc.cc.u32 %5, %5, 0;\n\t"
+        "addc.cc.u32 %6, %6, 0;\n\t"
+        "addc.cc.u32 %7, %7, 0;\n\t"
+        "addc.cc.u32 %8, %8, 0;\n\t"
+        "addc.cc.u32 %9, %9, 0;\n\t"
+        "addc.cc.u32 %10, %10, 0;\n\t"
+        "addc.u32 %11, %11, 0;"
+        : "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]), "+r"(E[8]), "+r"(E[9]),
+          "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
+        : "r"(O[1]));
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        E[k] = E[k + 2];
+        O[k] = O[k + 2];
+    }
+    E[12] = E[13] = 0;
+    O[12] = O[13] = 0;
+}
+
+// r = E + 2^32 O after the last step (the words from 12 up cancel).
+__device__ __forceinline__ void mont_dfinal(fe& r, const MontAccD& t) {
+    const uint32_t* e = t.e;
+    const uint32_t* o = t.o;
+    r.v[0] = e[0];
+    asm("add.cc.u32 %0, %11, %22;\n\t"
+        "addc.cc.u32 %1, %12, %23;\n\t"
+        "addc.cc.u32 %2, %13, %24;\n\t"
+        "addc.cc.u32 %3, %14, %25;\n\t"
+        "addc.cc.u32 %4, %15, %26;\n\t"
+        "addc.cc.u32 %5, %16, %27;\n\t"
+        "addc.cc.u32 %6, %17, %28;\n\t"
+        "addc.cc.u32 %7, %18, %29;\n\t"
+        "addc.cc.u32 %8, %19, %30;\n\t"
+        "addc.cc.u32 %9, %20, %31;\n\t"
+        "addc.u32 %10, %21, %32;"
+        : "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]), "=r"(r.v[6]), "=r"(r.v[7]),
+          "=r"(r.v[8]), "=r"(r.v[9]), "=r"(r.v[10]), "=r"(r.v[11])
+        : "r"(e[1]), "r"(e[2]), "r"(e[3]), "r"(e[4]), "r"(e[5]), "r"(e[6]), "r"(e[7]), "r"(e[8]), "r"(e[9]),
+          "r"(e[10]), "r"(e[11]), "r"(o[0]), "r"(o[1]), "r"(o[2]), "r"(o[3]), "r"(o[4]), "r"(o[5]), "r"(o[6]),
+          "r"(o[7]), "r"(o[8]), "r"(o[9]), "r"(o[10]));
+}
+
+// -1, read through a volatile constant load so the compiler cannot fold it.
+__device__ __constant__ static volatile uint32_t kNegOne = 0xffffffffu;
+__device__ __forceinline__ uint32_t neg_one() { return kNegOne; }
+
 __device__ __forceinline__ void mul_inl(fe& r, const fe& a, const fe& b) {
+    MontAccD t = {};
+    const uint32_t neg1 = neg_one();
+#pragma unroll
+    for (int i = 0; i < N; i += 2) mont_dstep(t, a.v[i], a.v[i + 1], b.v, neg1);
+    mont_dfinal(r, t);
+}
+
+// The earlier form: one row and one digit m = -t_0 per step (the variant
+// MSM377_FQMUL_CIOS_SINGLEROW of fq_mul_batch_variant).
+__device__ __forceinline__ void mul_singlerow_inl(fe& r, const fe& a, const fe& b) {
     MontAcc t = {};
 #pragma unroll
     for (int i = 0; i < N; ++i) mont_row(t, a.v[i], b.v);
@@ -207,14 +455,15 @@ __device__ __forceinline__ void mul_inl(fe& r, const fe& a, const fe& b) {
 // Two independent products with their rows interleaved: four independent carry
 // chains in flight instead of two.
 __device__ __forceinline__ void mul2_inl(fe& r1, const fe& a1, const fe& b1, fe& r2, const fe& a2, const fe& b2) {
-    MontAcc t1 = {}, t2 = {};
+    MontAccD t1 = {}, t2 = {};
+    const uint32_t neg1 = neg_one();
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        mont_row(t1, a1.v[i], b1.v);
-        mont_row(t2, a2.v[i], b2.v);
+    for (int i = 0; i < N; i += 2) {
+        mont_dstep(t1, a1.v[i], a1.v[i + 1], b1.v, neg1);
+        mont_dstep(t2, a2.v[i], a2.v[i + 1], b2.v, neg1);
     }
-    mont_final(r1, t1);
-    mont_final(r2, t2);
+    mont_dfinal(r1, t1);
+    mont_dfinal(r2, t2);
 }
 
 // Out-of-line multiplication used by the point arithmetic (one copy of the code).

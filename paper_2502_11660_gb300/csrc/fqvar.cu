@@ -13,8 +13,12 @@
 //  * CARRYSAVE -- Montgomery on 16 digits of 24 bits in 32-bit registers, 64-bit
 //                 column sums and two rounds of coarse carry propagation (the
 //                 element format of Sec. III-B / III-D carried to the GPU).
-//  * CIOS_DOUBLEROW -- the same product two rows and two quotient digits per step,
-//                 accumulators shifted by two limbs (mul_doublerow).
+//  * CIOS_DOUBLEROW -- the library's double-row steps with the plain digit
+//                 m = -t (mul_doublerow): the compiler folds that negation into
+//                 the m p multiplications, which then do not fuse into 64-bit
+//                 multiply-adds (the library reads -1 through a volatile load).
+//  * CIOS_SINGLEROW -- the library's earlier form: one row and one digit per step
+//                 (fq::mul_singlerow_inl).
 //  * CIOS_TWOPASS -- the library's word-serial Montgomery product with each row
 //                 as one chain of low halves followed by one chain of high halves
 //                 (the library's multiplication runs each row as two independent
@@ -393,9 +397,10 @@ __device__ __forceinline__ void mul_cios_twopass(fe& r, const fe& a, const fe& b
 
 // ---- CIOS_DOUBLEROW: two rows and two quotient digits per step, accumulators
 // shifted by two limbs, so the register pair holding the low and high half of one
-// partial product keeps its alignment from step to step (bare product chains that
-// shift two limbs per row run 1.3x faster than chains that shift one; the whole
-// multiplication, with its extra carry words and the merge chain below, does not).
+// partial product keeps its alignment from step to step; here with the digits
+// formed as plain negations, which the compiler folds into the m p products (they
+// then split into a low and a high multiply). fq::mont_dstep is the same step with
+// the digits kept as multiplications by an opaque -1.
 //
 // The running value is E + 2^32 O: E[k] at limb k holds the partial products that
 // start at an even limb (a low half at 2j, its high half at 2j + 1), O[k] at limb
@@ -676,7 +681,7 @@ __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t*
             x[k] = a[k * n + i];
             y[k] = b[k * n + i];
         }
-        if (V == MSM377_FQMUL_CIOS || V == MSM377_FQMUL_FIPS) {
+        if (V == MSM377_FQMUL_CIOS || V == MSM377_FQMUL_FIPS || V == MSM377_FQMUL_CIOS_SINGLEROW) {
             fe fa, fb, fr;
 #pragma unroll
             for (int k = 0; k < N; ++k) {
@@ -685,6 +690,8 @@ __global__ void k_fq_mul_variant(const uint32_t* __restrict__ a, const uint32_t*
             }
             if (V == MSM377_FQMUL_FIPS)
                 mul_fips(fr, fa, fb);
+            else if (V == MSM377_FQMUL_CIOS_SINGLEROW)
+                fq::mul_singlerow_inl(fr, fa, fb);
             else
                 fq::mul_inl(fr, fa, fb);
             fq::canon(fr, fr);
@@ -884,7 +891,7 @@ using namespace msm377;
 
 extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32_t* out, size_t n, int variant,
                                     void* stream) {
-    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_FIPS)
+    if (variant < MSM377_FQMUL_CIOS || variant > MSM377_FQMUL_CIOS_SINGLEROW)
         return set_error(MSM377_EINVAL, "fq_mul_batch_variant: unknown variant %d", variant);
     if (n == 0) return MSM377_OK;
     if (!a || !b || !out) return set_error(MSM377_EINVAL, "fq_mul_batch_variant: NULL pointer");
@@ -913,6 +920,9 @@ extern "C" int fq_mul_batch_variant(const uint32_t* a, const uint32_t* b, uint32
             break;
         case MSM377_FQMUL_FIPS:
             k_fq_mul_variant<MSM377_FQMUL_FIPS><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
+            break;
+        case MSM377_FQMUL_CIOS_SINGLEROW:
+            k_fq_mul_variant<MSM377_FQMUL_CIOS_SINGLEROW><<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);
             break;
         case MSM377_FQMUL_PAPER:
             k_fq_mul_paper25<<<(unsigned)blocks, 256, 0, s>>>(a, b, out, n);

@@ -26,6 +26,7 @@ VARIANTS = {
     "cios_doublerow": (5, lambda x, y: x * y * RINV % fq.P),
     "warp": (6, lambda x, y: x * y * RINV % fq.P),
     "fips": (8, lambda x, y: x * y * RINV % fq.P),
+    "cios_singlerow": (9, lambda x, y: x * y * RINV % fq.P),
 }
 
 
@@ -57,7 +58,7 @@ def test_barrett_matches_the_papers_reduction_in_the_oracle():
 
 
 def test_unknown_variant_is_rejected():
-    assert pkg.lib().fq_mul_batch_variant(None, None, None, 4, 9, None) == -1
+    assert pkg.lib().fq_mul_batch_variant(None, None, None, 4, 10, None) == -1
 
 
 def test_warp_product_on_unreduced_operands_and_carry_runs():
