@@ -254,8 +254,9 @@ size_t msm_points_prepared_bytes(size_t n, uint32_t flags);
  * 16-byte aligned; (0, 0) = O) into the stored form that msm_g1 reads with
  * MSM377_POINTS_PREPARED and the same EDWARDS / GLV flags: out (16-byte aligned)
  * holds msm_points_prepared_bytes(n, flags). XYZZ: Montgomery affine (x, y).
- * Edwards: (x, y, k x y) in Montgomery form, one inversion per 8 points
- * (Montgomery's trick). out must not overlap points_std unless flags == 0. */
+ * Edwards: (x, y, k x y) in Montgomery form, one field inversion per warp batch of
+ * points (Montgomery's trick); the kernel uses out's rows as scratch between its
+ * two passes. out must not overlap points_std unless flags == 0. */
 int msm_points_prepare_ex(const uint32_t *points_std, size_t n, uint32_t *out, uint32_t flags,
                           void *stream);
 

@@ -253,15 +253,18 @@ __global__ void k_prepare(const uint4* __restrict__ in, uint4* __restrict__ out,
 
 // Weierstrass -> Edwards stored form. For (x_w, y_w), with a = x_w + 1:
 //   D = y_w (a + s),  x = c1 a (a + s) / D,  y = (a - s) y_w / D,  u = k x y.
-// The inverses of D come from one inversion per warp (Montgomery's trick twice:
-// each thread multiplies the D of its kEdChunk points, a warp scan multiplies the
+// The affine identity, and points outside the map's domain (D = 0: order 2 or 4,
+// never in the subgroup), become the Edwards identity (0, 1, 0).
+//
+// ed_affine_chunk (used by the fixed-base precomputation) takes kEdChunk points
+// per lane in registers: one inversion per warp (Montgomery's trick twice: each
+// thread multiplies the D of its kEdChunk points, a warp scan multiplies the
 // threads' products, lane 0 inverts the warp's total, and prefix and suffix
 // products hand every thread the inverse of its own product, from which it walks
-// back through its chunk). The affine identity, and points outside the map's
-// domain (D = 0: order 2 or 4, never in the subgroup), become the Edwards
-// identity (0, 1, 0).
+// back through its chunk). k_prepare_ed, below, is the same map arranged for the
+// preparation of whole sets.
 constexpr int kEdChunk = 8;
-// The GLV pair path of the preparation needs every lane's first row and row count
+// The GLV pair path of ed_affine_chunk needs every lane's first row and row count
 // even (pairs P, phi(P) never straddle two lanes).
 static_assert(kEdChunk % 2 == 0, "kEdChunk must be even");
 
