@@ -128,6 +128,7 @@ struct MemQE {
 struct ModelXyzz {
     using acc = xyzz;
     static constexpr int kDblDepth = 3, kAddDepth = 4;  // multiplication levels of dbl4 / add4
+    static constexpr int kAccBlocks = 3;  // accumulation blocks of 128 per SM (<= 168 registers)
     static constexpr int kStored = 6;  // affine (x, y)
     static __device__ __forceinline__ void set_inf(acc& P) { ec::set_inf(P); }
     static __device__ __forceinline__ void load(acc& P, const uint4* p) { load_xyzz(P, p); }
@@ -163,6 +164,7 @@ struct ModelXyzz {
 struct ModelEdwards {
     using acc = ed::ext;
     static constexpr int kDblDepth = 2, kAddDepth = 3;  // multiplication levels of dbl4 / add4
+    static constexpr int kAccBlocks = 4;  // accumulation blocks of 128 per SM (<= 128 registers)
     static constexpr int kStored = 9;  // (x, y, u = k x y), the paper's (X, Y, U) with Z = 1
     static __device__ __forceinline__ void set_inf(acc& P) { ed::set_inf(P); }
     static __device__ __forceinline__ void load(acc& P, const uint4* p) {
@@ -1169,11 +1171,13 @@ __device__ __forceinline__ void accumulate_chunk(const AccArgs& a, int w, uint32
     }
 }
 
-// At most 168 registers, so three blocks of 128 stay resident per SM (uncapped, the
-// XYZZ formulas with paired products take 190 and fit two: measured 7.00 ms per
-// accumulation at n = 2^20, c = 16, against 6.54 ms capped with a few spills).
+// Register caps per curve model (M::kAccBlocks blocks of 128 resident per SM), each
+// the faster of the caps measured at n = 2^20, c = 16: XYZZ at 168 registers, three
+// blocks (4 blocks: 5.75 vs 5.74 ms per accumulation; uncapped, 190 registers and two
+// blocks, slower still); Edwards at 128 registers, four blocks, with a few spills
+// (4.14 vs 4.24 ms at three blocks).
 template <class M>
-__global__ void __launch_bounds__(128, 3) k_accumulate(AccArgs a) {
+__global__ void __launch_bounds__(128, M::kAccBlocks) k_accumulate(AccArgs a) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (uint32_t)a.nwin * a.cpw) return;
     accumulate_chunk<M>(a, a.w0 + (int)(id / a.cpw), id % a.cpw);
@@ -1190,7 +1194,7 @@ struct BatchAcc {
 };
 
 template <class M>
-__global__ void __launch_bounds__(128) k_accumulate_batched(const __grid_constant__ BatchAcc b) {
+__global__ void __launch_bounds__(128, M::kAccBlocks) k_accumulate_batched(const __grid_constant__ BatchAcc b) {
     const uint32_t total = b.prefix[b.njobs];
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -1578,9 +1582,9 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
     p->ngroups = (p->W + p->gw - 1) / p->gw;
     // Chunks of K <= 64 items, one per thread, sized so that the chunks of one
     // accumulation launch (one window group) fill whole waves of resident threads
-    // (152 SMs x 3 blocks of 128 on a GB300): m waves of K items rather than a last,
-    // partly idle wave.
-    constexpr size_t kWave = 152 * 384;
+    // (152 SMs x kAccBlocks blocks of 128 on a GB300): m waves of K items rather than
+    // a last, partly idle wave.
+    const size_t kWave = (size_t)152 * 128 * (p->edw ? ModelEdwards::kAccBlocks : ModelXyzz::kAccBlocks);
     const size_t total = (size_t)p->gw * items;
     size_t waves = (total + 64 * kWave - 1) / (64 * kWave);
     if (waves < 1) waves = 1;
