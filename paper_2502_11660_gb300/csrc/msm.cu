@@ -462,27 +462,6 @@ __device__ __forceinline__ void load_fe_cg(fe& a, const uint4* p) {   // through
     a.v[8] = u2.x; a.v[9] = u2.y; a.v[10] = u2.z; a.v[11] = u2.w;
 }
 
-// Stored Edwards rows of input points [a, b): row i, or rows 2i and 2i + 1 (P_i and
-// phi(P_i) = (beta x_i, y_i)) with GLV. Same map as above, arranged to cost fewer
-// multiplications and no local memory:
-//  * The inputs stay in standard form. Read as Montgomery residues, x and y stand
-//    for x / R and y / R; with the additive constants 1 and s entered in that same
-//    scale (the integers 1 and s) every quantity the map divides is scaled by the
-//    same power of R in numerator and denominator, so the Edwards coordinates come
-//    out exact, in Montgomery form, with no conversion multiplications.
-//  * GLV pair (P, phi(P)): one denominator t = y (a + s)(a' + s), a' = beta x + 1;
-//    from t^-1 and u = y (a + s): 1/(a' + s) = t^-1 u, w = t^-1 (a' + s) = 1/u,
-//    1/y = w (a + s), 1/(a + s) = w y; then x_e = c1 a / y, y_e = (a - s)/(a + s)
-//    per row. Single row: t = y (a + s), x_e = c1 a (a + s) / t,
-//    y_e = (a - s) y / t.
-//  * A warp takes batches of 32 K consecutive points (lane l: points
-//    base + 32 q + l, q < K) and inverts all their t with one field inversion
-//    (Montgomery's trick over the lane's K points, warp_lane_inverse over the
-//    lanes). Pass 1 writes each point's prefix product and the values pass 2
-//    needs into that point's own output rows; pass 2 reads them back (through
-//    L2) and overwrites the rows with the stored form.
-// A zero factor of t (the identity, or a point outside the map's domain) is
-// replaced by 1 and the rows it feeds become the Edwards identity.
 // s in standard form (the integer s, which is s / R as a Montgomery residue).
 __device__ __constant__ static const uint32_t kSStd[fq::N] = {
     0xd09adc01u, 0x9c05824au, 0x0e1c7a7cu, 0x2e6bb28fu, 0xfc166427u, 0x2fe2cb65u,
@@ -509,9 +488,30 @@ __device__ __forceinline__ fe mont_one() {
 
 constexpr int kPrepBlocksPerSm = 2;
 
+// Stored Edwards rows of input points [a, b): row i, or rows 2i and 2i + 1 (P_i and
+// phi(P_i) = (beta x_i, y_i)) with GLV. Same map as above, arranged to cost fewer
+// multiplications and no local memory:
+//  * The inputs stay in standard form. Read as Montgomery residues, x and y stand
+//    for x / R and y / R; with the additive constants 1 and s entered in that same
+//    scale (the integers 1 and s) every quantity the map divides is scaled by the
+//    same power of R in numerator and denominator, so the Edwards coordinates come
+//    out exact, in Montgomery form, with no conversion multiplications.
+//  * GLV pair (P, phi(P)): one denominator t = y (a + s)(a' + s), a' = beta x + 1;
+//    from t^-1 and u = y (a + s): 1/(a' + s) = t^-1 u, w = t^-1 (a' + s) = 1/u,
+//    1/y = w (a + s), 1/(a + s) = w y; then x_e = c1 a / y, y_e = (a - s)/(a + s)
+//    per row. Single row: t = y (a + s), x_e = c1 a (a + s) / t,
+//    y_e = (a - s) y / t.
+//  * A warp takes batches of 32 K consecutive points (lane l: points
+//    base + 32 q + l, q < K) and inverts all their t with one field inversion
+//    (Montgomery's trick over the lane's K points, warp_lane_inverse over the
+//    lanes). Pass 1 writes each point's prefix product and the values pass 2
+//    needs into that point's own output rows; pass 2 reads them back (through
+//    L2) and overwrites the rows with the stored form.
+// A zero factor of t (the identity, or a point outside the map's domain) is
+// replaced by 1 and the rows it feeds become the Edwards identity.
 template <bool kGlv>
-__global__ void __launch_bounds__(128, kPrepBlocksPerSm) k_prepare_ed(const uint4* __restrict__ in, uint4* out, size_t a, size_t b,
-                                                    int K) {
+__global__ void __launch_bounds__(128, kPrepBlocksPerSm)
+    k_prepare_ed(const uint4* __restrict__ in, uint4* out, size_t a, size_t b, int K) {
     const int lane = threadIdx.x & 31;
     const size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
     const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
