@@ -1226,6 +1226,11 @@ __global__ void __launch_bounds__(128, M::kAccBlocks) k_accumulate_batched(const
 //  * k_merge_round(d): for heads at offset j = u - start[u] - 1 with j % 2d == 0,
 //    head[u] += head[u + d] when u + d continues the same run; ceil(log2 cpw) rounds
 //    leave each run's sum of heads at its first head;
+//  * k_merge_long: the rounds above are launched for d < kMergeRounds only (enough for
+//    the runs of random scalars, which cross a few chunk edges); a run with more heads
+//    is finished by one block that runs the remaining rounds (d = kMergeRounds,
+//    2 kMergeRounds, ...) over that run alone between block barriers. When no run is
+//    that long the launch returns at once: one launch instead of a dozen idle rounds;
 //  * k_merge_final: bucket = tail[start] + that sum.
 __global__ void k_merge_start(AccArgs a, int32_t* __restrict__ start, int* __restrict__ maxspan) {
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -1270,6 +1275,65 @@ __global__ void k_merge_round(AccArgs a, const int32_t* __restrict__ start, uint
     M::load(acc, a.head + (base + u) * kXyzzVec);
     M::add_mem(acc, a.head + (base + v) * kXyzzVec);
     M::store(a.head + (base + u) * kXyzzVec, acc);
+}
+
+constexpr uint32_t kMergeRounds = 8;   // rounds d = 1, 2, 4 launched one by one
+constexpr int kMergeLongThreads = 128;
+
+template <class M>
+__global__ void __launch_bounds__(kMergeLongThreads) k_merge_long(AccArgs a, const int32_t* __restrict__ start,
+                                                                  const int* __restrict__ maxspan) {
+    if ((uint32_t)*maxspan <= kMergeRounds) return;  // every run is complete already
+    __shared__ uint32_t first[kMergeLongThreads], span[kMergeLongThreads];
+    __shared__ uint32_t nfound;
+    const uint32_t nchunks = (uint32_t)a.nwin * a.cpw;
+    for (uint32_t tile = blockIdx.x * kMergeLongThreads; tile < nchunks; tile += gridDim.x * kMergeLongThreads) {
+        if (threadIdx.x == 0) nfound = 0;
+        __syncthreads();
+        // the first head (j = 0) of every run with more than kMergeRounds heads in this tile
+        const uint32_t id = tile + threadIdx.x;
+        if (id < nchunks) {
+            const int w = a.w0 + (int)(id / a.cpw);
+            const uint32_t u = id % a.cpw;
+            const size_t ci = (size_t)w * a.cpw + u;
+            const int32_t t0 = a.headflag[ci] != 0 ? start[ci] : -1;
+            if (t0 >= 0 && u == (uint32_t)t0 + 1) {
+                // the run's last item: the last index with this key (upper bound - 1)
+                const uint2* kv = a.kv + (size_t)w * a.n;
+                const uint32_t key = kv[(size_t)u * a.K].x;
+                size_t lo = (size_t)u * a.K, hi = a.n;
+                while (lo < hi) {
+                    const size_t mid = (lo + hi) >> 1;
+                    if (kv[mid].x <= key) lo = mid + 1; else hi = mid;
+                }
+                const uint32_t heads = (uint32_t)((lo - 1) / (size_t)a.K) - (uint32_t)t0;
+                if (heads > kMergeRounds) {
+                    const uint32_t k = atomicAdd(&nfound, 1u);
+                    first[k] = id;
+                    span[k] = heads;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t nf = nfound;
+        for (uint32_t r = 0; r < nf; ++r) {
+            const uint32_t f = first[r], S = span[r];
+            const int w = a.w0 + (int)(f / a.cpw);
+            const size_t h0 = (size_t)w * a.cpw + f % a.cpw;   // head j = 0 of the run
+            for (uint32_t d = kMergeRounds; d < S; d <<= 1) {
+                const uint32_t pairs = (S - d + 2 * d - 1) / (2 * d);   // j = 0, 2d, ... with j + d < S
+                for (uint32_t q = threadIdx.x; q < pairs; q += blockDim.x) {
+                    const size_t j = (size_t)q * 2 * d;
+                    typename M::acc acc;
+                    M::load(acc, a.head + (h0 + j) * kXyzzVec);
+                    M::add_mem(acc, a.head + (h0 + j + d) * kXyzzVec);
+                    M::store(a.head + (h0 + j) * kXyzzVec, acc);
+                }
+                __syncthreads();   // this level's sums are visible to the next level
+            }
+        }
+        __syncthreads();   // the list is read before the next tile overwrites it
+    }
 }
 
 template <class M>
@@ -1909,8 +1973,16 @@ int enqueue_group_tail_m(const Plan& p, const AccArgs& a, int g, void* workspace
     int* maxspan = at<int>(workspace, p.off_status) + 1 + g;
     k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, maxspan);
     note_launches(1);
-    for (uint32_t d = 1; d < p.cpw; d <<= 1) {
+    for (uint32_t d = 1; d < p.cpw && d < kMergeRounds; d <<= 1) {
         k_merge_round<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d, maxspan);
+        note_launches(1);
+    }
+    if (p.cpw > kMergeRounds) {
+        int dev = 0, sms = 152;
+        MSM_CUDA_TRY(cudaGetDevice(&dev));
+        MSM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const size_t want = (nchunks + kMergeLongThreads - 1) / kMergeLongThreads, cap = (size_t)sms * 4;
+        k_merge_long<M><<<(unsigned)(want < cap ? want : cap), kMergeLongThreads, 0, s>>>(a, start, maxspan);
         note_launches(1);
     }
     k_merge_final<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a);
