@@ -935,7 +935,7 @@ def serve(h, edw=False, gl=False, nreq=2000, nsets=8, set_size=1 << 22, load=0.8
     setup_s = time.perf_counter() - t0
     srv = serving.MsmServer(rs, slots=8, device=dev)
     # sustained capacity from a back-to-back burst of the same size mix, then 0.8 of it
-    calib = serving.poisson_requests(48, rate=1.0, nsets=nsets, set_size=set_size, lo_log2=12, hi_log2=22, tag=5)
+    calib = serving.poisson_requests(96, rate=1.0, nsets=nsets, set_size=set_size, lo_log2=12, hi_log2=22, tag=5)
     srv.run(calib[:8], realtime=False)
     cap = srv.run(calib, realtime=False)
     mean_n = float(np.mean([r.n for r in calib]))

@@ -122,7 +122,7 @@ def time_schedule(n: int, c: int, chunk: int, sort: int, reduce_log2: int, group
 
 # chunk sizes (items per accumulation thread), sorts (1 counting, 2 radix), level-1
 # reduction thread counts and window groups searched after the window width
-CHUNKS = (0, 16, 32, 48, 96, 128)
+CHUNKS = (0, 16, 32, 48, 64, 96, 128)
 SORTS = (1, 2)
 REDUCE_LOG2 = (0, 13, 14, 16, 17)
 GROUPS = (1, 2, 4)

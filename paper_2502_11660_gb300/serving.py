@@ -11,7 +11,10 @@ a request's arrival to the host seeing its completion event.
 
 Scalars are drawn on the device per request from the request's own seed (like
 witness-derived scalars that already live on the GPU in a prover); every GPU
-step is a call into libmsm377. With GLV the stored set interleaves P_i and
+step is a call into libmsm377. Each slot keeps its own device buffers (workspace,
+scalars, result), grown to the largest request it has served and reused by the
+next request on the same stream, so a warm server allocates nothing per request
+(the memory budget still admits requests by their own footprint). With GLV the stored set interleaves P_i and
 phi(P_i), so a request's slice is still one contiguous range of rows.
 """
 from __future__ import annotations
@@ -44,11 +47,15 @@ class Done:
     result: np.ndarray
 
 
-def device_scalars(n: int, seed: int, device) -> torch.Tensor:
-    """n scalars uniform in [0, 2^252) (below r), drawn on the device from `seed`."""
+def device_scalars(n: int, seed: int, device, out: torch.Tensor | None = None) -> torch.Tensor:
+    """n scalars uniform in [0, 2^252) (below r), drawn on the device from `seed`
+    (into `out`, an (n, 8) int32 view, when given)."""
     g = torch.Generator(device=device)
     g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
-    sc = torch.randint(-(2 ** 31), 2 ** 31, (n, 8), dtype=torch.int32, device=device, generator=g)
+    if out is None:
+        sc = torch.randint(-(2 ** 31), 2 ** 31, (n, 8), dtype=torch.int32, device=device, generator=g)
+    else:
+        sc = torch.randint(-(2 ** 31), 2 ** 31, (n, 8), dtype=torch.int32, device=device, generator=g, out=out)
     sc[:, 7] &= 0x0FFFFFFF
     return sc
 
@@ -85,6 +92,8 @@ class MsmServer:
         self.sets = sets
         self.device = torch.device(device)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
+        # per slot: workspace bytes, scalar words and the 24-word result, grown on demand
+        self.arenas: list[dict] = [{"ws": None, "sc": None, "out": None} for _ in range(slots)]
         if mem_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             mem_budget = int(free * 0.5)
@@ -95,13 +104,26 @@ class MsmServer:
         scalars and its result."""
         return self.sets.set(0).workspace_bytes(n) + 32 * n + 96
 
+    def _buffers(self, slot: int, rs: ResidentSet, n: int):
+        """The slot's buffers, grown to hold a request of n points. The slot's previous
+        request has completed (a slot is reused only after its event fired), so
+        replacing or reusing them is safe."""
+        a = self.arenas[slot]
+        need = rs.workspace_bytes(n)
+        if a["ws"] is None or a["ws"].numel() < need:
+            a["ws"] = torch.empty(need, dtype=torch.uint8, device=self.device)
+        if a["sc"] is None or a["sc"].shape[0] < n:
+            a["sc"] = torch.empty((n, 8), dtype=torch.int32, device=self.device)
+        if a["out"] is None:
+            a["out"] = torch.empty(24, dtype=torch.int32, device=self.device)
+        return a["ws"], a["sc"][:n], a["out"]
+
     def _launch(self, req: Request, slot: int):
         st = self.streams[slot]
         with torch.cuda.stream(st):
-            sc = device_scalars(req.n, req.seed, self.device)
             rs = self.sets.set(req.set_id)
-            ws = rs.workspace(req.n)
-            out = torch.empty(24, dtype=torch.int32, device=self.device)
+            ws, sc_buf, out = self._buffers(slot, rs, req.n)
+            sc = device_scalars(req.n, req.seed, self.device, out=sc_buf)
             rs.msm(sc, offset=req.offset, out=out, workspace=ws, stream=st)
             ev = torch.cuda.Event()
             ev.record(st)
