@@ -402,3 +402,21 @@ def test_preparation_beside_the_head(edw, split):
     assert pkg.msm_g1_status(ws) == (pkg.ENOTONCURVE if (edw or split) else 0)
     out = pkg.msm_g1(pkg.to_device(pts), pkg.to_device(a), workspace=ws, **kw)
     assert g1.from_limbs(pkg.to_host(out)) == want and pkg.msm_g1_status(ws) == 0
+
+
+@pytest.mark.parametrize("edw,split", [(False, False)] + MODES, ids=["xyzz"] + MODE_IDS)
+def test_few_distinct_scalars_long_runs(edw, split):
+    """Scalars drawn from five values plus a random quarter: every window has a few
+    buckets holding thousands of points, so many runs cross far more than 8 chunk edges
+    (the merge's long-run launch, several such runs per window and per block) next to
+    ordinary short runs."""
+    n = 24_000
+    a, s, pts = msm_inputs(n, tag=517)
+    a = a.copy()
+    rng = np.random.default_rng(517)
+    pick = rng.integers(0, 5, n)
+    keep = rng.random(n) < 0.25
+    a[~keep] = a[pick[~keep]]
+    want = closed_form_limbs(s, a)
+    for c, sg in [(6, True), (10, True), (9, False)]:
+        assert run(pts, a, c=c, signed=sg, scalar_bits=253, edwards=edw, glv=split) == want
