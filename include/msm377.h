@@ -76,8 +76,8 @@ int fq_to_montgomery(const uint32_t *in, uint32_t *out, size_t n, void *stream);
  * (same layout: structure-of-arrays [12][n], 16-byte aligned device arrays,
  * operands in [0, p), result canonical in [0, p)). The MSM does not use them.
  *   MSM377_FQMUL_CIOS      a b 2^-384 mod p, word-serial Montgomery two words per step
- *                          with the quotient digits kept as multiplications (the
- *                          library's)
+ *                          with the quotient digits formed out of the compiler's
+ *                          sight (the library's)
  *   MSM377_FQMUL_BARRETT   a b mod p on standard-form operands: the paper's Barrett
  *                          reduction (Sec. III-C), k = 377, mu = floor(2^754 / p),
  *                          remainder in [0, 3p) then at most two subtractions of p

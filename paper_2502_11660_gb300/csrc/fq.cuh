@@ -18,12 +18,13 @@
 //    inserts a move per product); dropping two words per step keeps every pair
 //    aligned.
 //  * The compiler folds a negation into the multiplications it feeds, and a
-//    folded m*p_j does not fuse. So the digits are formed as t_k * (-1) with the
-//    -1 read through a volatile constant load (neg_one), which the compiler cannot
-//    see through: one extra multiply per digit, and all 276 products per
-//    multiplication fuse.
+//    folded m*p_j does not fuse. So the digits are formed as (t_k ^ mask) + 1 with
+//    the all-ones mask read through a volatile constant load (neg_one), which the
+//    compiler cannot see through: two ALU operations per digit (t_k * (-1) with the
+//    same opaque -1 also works, but takes the multiply pipe), and all 276 products
+//    per multiplication fuse.
 // Against one word per row with m = -t_0 (mul_singlerow_inl, the earlier form):
-// 1128 instead of 1368 multiply-pipe cycles per product, and the MSM's
+// 1104 instead of 1368 multiply-pipe cycles per multiplication, and the MSM's
 // accumulation 4.63 -> 4.22 ms at 2^20 points.
 //
 // mul() is one out-of-line function. A point operation makes 10-14 calls; with
@@ -310,7 +311,7 @@ __device__ __forceinline__ void mont_dstep(MontAccD& t, uint32_t x0, uint32_t x1
         : "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]), "+r"(E[8]), "+r"(E[9]),
           "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
         : "r"(x1), "r"(b[1]), "r"(b[3]), "r"(b[5]), "r"(b[7]), "r"(b[9]), "r"(b[11]));
-    const uint32_t m0 = E[0] * neg1;   // -E[0], kept a multiplication (neg_one)
+    const uint32_t m0 = (E[0] ^ neg1) + 1u;   // -E[0], through the opaque mask (neg_one)
     // O[0..11] += m0 p_odd (limbs 1..12), carry into O[12..13]
     asm("mad.lo.cc.u32 %0, %14, 0x8508c000, %0;\n\t"
         "madc.hi.cc.u32 %1, %14, 0x8508c000, %1;\n\t"
@@ -348,7 +349,7 @@ __device__ __forceinline__ void mont_dstep(MontAccD& t, uint32_t x0, uint32_t x1
         : "+r"(E[0]), "+r"(E[1]), "+r"(E[2]), "+r"(E[3]), "+r"(E[4]), "+r"(E[5]), "+r"(E[6]), "+r"(E[7]),
           "+r"(E[8]), "+r"(E[9]), "+r"(E[10]), "+r"(E[11]), "+r"(E[12]), "+r"(E[13])
         : "r"(O[0]), "r"(m0));
-    const uint32_t m1 = E[1] * neg1;
+    const uint32_t m1 = (E[1] ^ neg1) + 1u;
     // E[1..13] += m1 (limb 1, p_0 = 1) + 2^64 m1 p_odd (limbs 2..13): E[1] becomes 0
     asm("add.cc.u32 %0, %0, %13;\n\t"
         "madc.lo.cc.u32 %1, %13, 0x8508c000, %1;\n\t"
@@ -431,7 +432,7 @@ __device__ __forceinline__ void mont_dfinal(fe& r, const MontAccD& t) {
           "r"(o[7]), "r"(o[8]), "r"(o[9]), "r"(o[10]));
 }
 
-// -1, read through a volatile constant load so the compiler cannot fold it.
+// All ones (-1), read through a volatile constant load so the compiler cannot fold it.
 __device__ __constant__ static volatile uint32_t kNegOne = 0xffffffffu;
 __device__ __forceinline__ uint32_t neg_one() { return kNegOne; }
 

@@ -16,7 +16,8 @@
 //  * CIOS_DOUBLEROW -- the library's double-row steps with the plain digit
 //                 m = -t (mul_doublerow): the compiler folds that negation into
 //                 the m p multiplications, which then do not fuse into 64-bit
-//                 multiply-adds (the library reads -1 through a volatile load).
+//                 multiply-adds (the library negates through a mask it reads
+//                 with a volatile load).
 //  * CIOS_SINGLEROW -- the library's earlier form: one row and one digit per step
 //                 (fq::mul_singlerow_inl).
 //  * CIOS_TWOPASS -- the library's word-serial Montgomery product with each row
@@ -400,7 +401,7 @@ __device__ __forceinline__ void mul_cios_twopass(fe& r, const fe& a, const fe& b
 // partial product keeps its alignment from step to step; here with the digits
 // formed as plain negations, which the compiler folds into the m p products (they
 // then split into a low and a high multiply). fq::mont_dstep is the same step with
-// the digits kept as multiplications by an opaque -1.
+// the digits formed through an opaque all-ones mask.
 //
 // The running value is E + 2^32 O: E[k] at limb k holds the partial products that
 // start at an even limb (a low half at 2j, its high half at 2j + 1), O[k] at limb
