@@ -486,7 +486,10 @@ __device__ __forceinline__ fe mont_one() {
     return r;
 }
 
-constexpr int kPrepBlocksPerSm = 2;
+// Blocks of 128 per SM for the Edwards preparation: the GLV form at four (128
+// registers, a few spills), the single-row form at two (its measured best: 0.54 ms for
+// 2^20 points against 0.60 at four).
+constexpr int prep_blocks_per_sm(bool glv) { return glv ? 4 : 2; }
 
 // Stored Edwards rows of input points [a, b): row i, or rows 2i and 2i + 1 (P_i and
 // phi(P_i) = (beta x_i, y_i)) with GLV. Same map as above, arranged to cost fewer
@@ -509,25 +512,8 @@ constexpr int kPrepBlocksPerSm = 2;
 //    L2) and overwrites the rows with the stored form.
 // A zero factor of t (the identity, or a point outside the map's domain) is
 // replaced by 1 and the rows it feeds become the Edwards identity.
-// The one-word-step multiplication (fq::mul_singlerow_inl), out of line: a shorter
-// dependent chain than fq::mul's two-word steps, which pays at the two warps per
-// scheduler of the GLV preparation (measured at 2^20 points: 0.97 vs 1.13 ms; the
-// single-row preparation measured the other way, 0.59 vs 0.54 ms, and keeps fq::mul).
-static __device__ __noinline__ fe mul_lat_v(fe a, fe b) {
-    fe r;
-    fq::mul_singlerow_inl(r, a, b);
-    return r;
-}
-template <bool kLat>
-__device__ __forceinline__ void pmul(fe& r, const fe& a, const fe& b) {
-    if (kLat)
-        r = mul_lat_v(a, b);
-    else
-        fq::mul(r, a, b);
-}
-
 template <bool kGlv>
-__global__ void __launch_bounds__(128, kPrepBlocksPerSm)
+__global__ void __launch_bounds__(128, prep_blocks_per_sm(kGlv))
     k_prepare_ed(const uint4* __restrict__ in, uint4* out, size_t a, size_t b, int K) {
     const int lane = threadIdx.x & 31;
     const size_t warp = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;
@@ -551,20 +537,20 @@ __global__ void __launch_bounds__(128, kPrepBlocksPerSm)
             const bool okY = !id && !fq::is_zero(Y), ok1 = !id && !fq::is_zero(D1);
             const fe Yf = okY ? Y : mont_one(), D1f = ok1 ? D1 : mont_one();
             uint4* o = out + (size_t)kVec * kRows * i;
-            pmul<kGlv>(t, Yf, D1f);
+            fq::mul(t, Yf, D1f);
             if (kGlv) {
                 fe BX, D2;
-                pmul<kGlv>(BX, cst(kBeta), X);
+                fq::mul(BX, cst(kBeta), X);
                 add_one_raw(D2, BX);
                 fq::add(D2, D2, cst(kSStd));
                 const bool ok2 = !id && !fq::is_zero(D2);
                 store_fe(o + 6, t);              // u = y (a + s)
                 store_fe(o + 9, BX);
-                pmul<kGlv>(t, t, ok2 ? D2 : mont_one());
+                fq::mul(t, t, ok2 ? D2 : mont_one());
             }
             store_fe(o, acc);                    // prefix product
             store_fe(o + 3, t);
-            pmul<kGlv>(acc, acc, t);
+            fq::mul(acc, acc, t);
         }
         fe inv = warp_lane_inverse(acc);         // acc^-1 on every lane
         for (int q = K - 1; q >= 0; --q) {       // pass 2
@@ -576,8 +562,8 @@ __global__ void __launch_bounds__(128, kPrepBlocksPerSm)
             load_fe(Y, in + 6 * i + 3);
             load_fe_cg(pre, o);
             load_fe_cg(t, o + 3);
-            pmul<kGlv>(tinv, inv, pre);             // t^-1
-            pmul<kGlv>(inv, inv, t);                // (prefix)^-1 for the next q down
+            fq::mul(tinv, inv, pre);             // t^-1
+            fq::mul(inv, inv, t);                // (prefix)^-1 for the next q down
             const bool id = fq::is_zero_raw(X) && fq::is_zero_raw(Y);
             add_one_raw(A, X);
             fq::add(D1, A, cst(kSStd));
@@ -589,24 +575,24 @@ __global__ void __launch_bounds__(128, kPrepBlocksPerSm)
                 add_one_raw(A2, BX);
                 fq::add(D2, A2, cst(kSStd));
                 const bool ok2 = !id && !fq::is_zero(D2);
-                pmul<kGlv>(i2, tinv, u);                        // 1 / (a' + s)
-                pmul<kGlv>(w, tinv, ok2 ? D2 : mont_one());     // 1 / (y (a + s))
-                pmul<kGlv>(iy, w, ok1 ? D1 : mont_one());       // 1 / y
-                pmul<kGlv>(i1, w, okY ? Y : mont_one());        // 1 / (a + s)
-                pmul<kGlv>(cy, cst(ed::kC1), iy);               // c1 / y
+                fq::mul(i2, tinv, u);                        // 1 / (a' + s)
+                fq::mul(w, tinv, ok2 ? D2 : mont_one());     // 1 / (y (a + s))
+                fq::mul(iy, w, ok1 ? D1 : mont_one());       // 1 / y
+                fq::mul(i1, w, okY ? Y : mont_one());        // 1 / (a + s)
+                fq::mul(cy, cst(ed::kC1), iy);               // c1 / y
                 fe xe, ye, d;
                 if (okY && ok1) {
-                    pmul<kGlv>(xe, A, cy);
+                    fq::mul(xe, A, cy);
                     fq::sub(d, A, cst(kSStd));
-                    pmul<kGlv>(ye, d, i1);
+                    fq::mul(ye, d, i1);
                     store_ed_stored(o, xe, ye);
                 } else {
                     store_ed_identity(o);
                 }
                 if (okY && ok2) {
-                    pmul<kGlv>(xe, A2, cy);
+                    fq::mul(xe, A2, cy);
                     fq::sub(d, A2, cst(kSStd));
-                    pmul<kGlv>(ye, d, i2);
+                    fq::mul(ye, d, i2);
                     store_ed_stored(o + kVec, xe, ye);
                 } else {
                     store_ed_identity(o + kVec);
@@ -614,12 +600,12 @@ __global__ void __launch_bounds__(128, kPrepBlocksPerSm)
             } else {
                 if (okY && ok1) {
                     fe ct, xe, ye, d;
-                    pmul<kGlv>(ct, cst(ed::kC1), tinv);         // c1 / t
-                    pmul<kGlv>(xe, A, D1);
-                    pmul<kGlv>(xe, xe, ct);                     // c1 a (a + s) / t
+                    fq::mul(ct, cst(ed::kC1), tinv);         // c1 / t
+                    fq::mul(xe, A, D1);
+                    fq::mul(xe, xe, ct);                     // c1 a (a + s) / t
                     fq::sub(d, A, cst(kSStd));
-                    pmul<kGlv>(ye, d, Y);
-                    pmul<kGlv>(ye, ye, tinv);                   // (a - s) y / t
+                    fq::mul(ye, d, Y);
+                    fq::mul(ye, ye, tinv);                   // (a - s) y / t
                     store_ed_stored(o, xe, ye);
                 } else {
                     store_ed_identity(o);
@@ -1745,18 +1731,19 @@ void launch_prepare_range(const uint4* in, uint4* out, size_t n, size_t a, size_
     const size_t lo = stored_count(a, flags), hi = stored_count(b, flags);
     if (hi <= lo) return;
     if (flags & MSM377_EDWARDS) {
-        // K points per lane: enough batches to give every resident warp (2 blocks of
-        // 4 warps per SM) about one, at least 2 and at most 32 points per lane
+        // K points per lane: enough batches to give every resident warp (per_sm blocks
+        // of 4 warps per SM) about one, at least 2 and at most 32 points per lane
         int dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const size_t items = b - a, slots = (size_t)sms * kPrepBlocksPerSm * 4;
+        const int per_sm = prep_blocks_per_sm((flags & MSM377_GLV) != 0);
+        const size_t items = b - a, slots = (size_t)sms * per_sm * 4;
         const size_t basis = sizing ? sizing : items;
         size_t K = (basis + 32 * slots - 1) / (32 * slots);
         K = K < 2 ? 2 : (K > 32 ? 32 : K);
         const size_t batches = (items + 32 * K - 1) / (32 * K);
         const size_t blocks = (batches + 3) / 4;
-        const size_t cap = (size_t)sms * kPrepBlocksPerSm;
+        const size_t cap = (size_t)sms * per_sm;
         const unsigned grid = (unsigned)(blocks < cap ? blocks : cap);
         if (flags & MSM377_GLV)
             k_prepare_ed<true><<<grid, 128, 0, s>>>(in, out, a, b, (int)K);
