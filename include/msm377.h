@@ -186,9 +186,10 @@ int g1_generator_mul(const uint32_t *seeds, size_t n, uint32_t *out, void *strea
  * window chain has no doublings; the mixed additions are the same in number. */
 #define MSM377_PRECOMPUTED 16u
 /* Sort the (bucket, point) pairs by 8-bit LSD radix passes instead of the default
- * counting sort over (window, bucket) bins (one pass of counts with each item's rank,
- * a scan, one scatter). Same result; kept for comparison (the counting sort measured
- * faster for every plan on GB300). */
+ * counting sort over (window, bucket) bins (counts and each item's rank per tile of
+ * items in shared-memory counters, a scan of the bin totals, one scatter). Same
+ * result; kept for comparison (the counting sort measured faster for every plan on
+ * GB300). */
 #define MSM377_RADIX_SORT 32u
 /* Check the input points before using them (Sec. I / II-C: the problem is a sum over
  * points of the BLS12-377 G1 group): every coordinate below p, every point on

@@ -1004,7 +1004,8 @@ constexpr int kScanBlock = 1024, kScanPer = 4, kScanTile = kScanBlock * kScanPer
 // Grid (items of a window / 256, windows): item i = w np + j of window w = blockIdx.y.
 // Counts per (window, key) bin; each item keeps its rank among the items of its bin
 // (the warp's share from one atomic per distinct bin, then the lanes' order), so the
-// scatter needs no atomics.
+// scatter needs no atomics. This global-counter form serves key ranges too wide for
+// the shared-memory tiles below (c >= 18 with signed digits, c >= 17 unsigned).
 __global__ void k_bin_count(const uint32_t* __restrict__ keys, size_t np, uint32_t nb,
                             uint32_t* __restrict__ counts, uint32_t* __restrict__ rank) {
     const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -1107,6 +1108,98 @@ __global__ void k_bin_scatter(const uint32_t* __restrict__ kin, const uint32_t* 
     const uint32_t key = kin[i];
     const size_t pos = (size_t)start[blockIdx.y * nb + key] + rank[i];
     if (pos < total) kvout[pos] = make_uint2(key, vin[i]);  // in bounds when the counts agree
+}
+
+// The same counting sort with the counts taken per tile in shared memory, for key
+// ranges whose counters fit there (no global atomics at all). Tile t of window w
+// holds items [t T, (t + 1) T); its block counts the tile's keys in 16-bit shared
+// counters packed two to a word (T < 2^16, so no count reaches the neighbour's
+// half) and gives each item its rank among the tile's items of the same key. The
+// tile counts go to cnt[w][t][key]; a column pass sums them into the bin totals, the
+// bin scan gives each (window, key) its offset, a second column pass turns cnt into
+// each tile's first slot per key (offset + counts of the earlier tiles), and an
+// item's slot is that plus its rank.
+constexpr int kTileThreads = 1024;
+constexpr uint32_t kTileItemsMax = 65535;
+constexpr size_t kTileSmemMax = 200 * 1024;    // packed counters of one block (GB300: 227 KB opt-in)
+
+// Grid (tiles, windows). Plain shared atomics: with random keys the counters rarely
+// collide. Measured on GB300 (n = 2^20, c = 16): one atomic per distinct key and
+// warp (found with match.any) made the head 0.09 ms slower with random scalars, and a
+// one-atomic path for warps whose keys are all equal moved it by at most 0.02 ms
+// with all-equal scalars.
+__global__ void __launch_bounds__(kTileThreads) k_tile_count(const uint32_t* __restrict__ keys, size_t np,
+                                                             uint32_t nb, uint32_t T, uint32_t ntiles,
+                                                             uint32_t* __restrict__ cnt, uint32_t* __restrict__ rank) {
+    extern __shared__ uint32_t h[];
+    const uint32_t hw = (nb + 1) / 2;
+    for (uint32_t k = threadIdx.x; k < hw; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    const size_t w = blockIdx.y;
+    const size_t lo = (size_t)blockIdx.x * T;
+    const size_t hi = lo + T < np ? lo + T : np;
+    const uint32_t* kw = keys + w * np;
+    uint32_t* rw = rank + w * np;
+    for (size_t j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+        const uint32_t key = kw[j];
+        if (key >= nb) continue;   // keys are below nb by construction
+        const uint32_t sh = (key & 1u) << 4;
+        const uint32_t old = atomicAdd(&h[key >> 1], 1u << sh);
+        rw[j] = (old >> sh) & 0xffffu;
+    }
+    __syncthreads();
+    uint32_t* cw = cnt + (w * ntiles + blockIdx.x) * nb;
+    for (uint32_t k = threadIdx.x; k < nb; k += blockDim.x) cw[k] = (h[k >> 1] >> ((k & 1u) << 4)) & 0xffffu;
+}
+
+// Thread (w, key): bins[w][key] <- the count over the window's tiles.
+__global__ void k_tile_totals(const uint32_t* __restrict__ cnt, uint32_t nb, uint32_t ntiles, uint32_t W,
+                              uint32_t* __restrict__ bins) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)W * nb) return;
+    const size_t w = id / nb, k = id % nb;
+    const uint32_t* c = cnt + w * ntiles * nb + k;
+    uint32_t run = 0;
+    for (uint32_t t = 0; t < ntiles; ++t) run += c[(size_t)t * nb];
+    bins[id] = run;
+}
+
+// Thread (w, key), after the bin scan: cnt[w][t][key] <- the slot of the tile's first
+// item of that key, start[w][key] plus the counts of tiles t' < t.
+__global__ void k_tile_offsets(uint32_t* __restrict__ cnt, uint32_t nb, uint32_t ntiles, uint32_t W,
+                               const uint32_t* __restrict__ start) {
+    const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (id >= (size_t)W * nb) return;
+    const size_t w = id / nb, k = id % nb;
+    uint32_t* c = cnt + w * ntiles * nb + k;
+    uint32_t run = start[id];
+    constexpr uint32_t kStep = 16;   // loads in flight per thread
+    for (uint32_t t0 = 0; t0 < ntiles; t0 += kStep) {
+        uint32_t v[kStep];
+#pragma unroll
+        for (uint32_t u = 0; u < kStep; ++u) v[u] = t0 + u < ntiles ? c[(size_t)(t0 + u) * nb] : 0u;
+#pragma unroll
+        for (uint32_t u = 0; u < kStep; ++u) {
+            if (t0 + u < ntiles) c[(size_t)(t0 + u) * nb] = run;
+            run += v[u];
+        }
+    }
+}
+
+// Grid (items of a window / 256, windows): each item to its tile's slot for the key
+// plus its rank.
+__global__ void k_tile_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                               const uint32_t* __restrict__ rank, uint2* __restrict__ kvout, size_t total,
+                               size_t np, uint32_t nb, uint32_t T, uint32_t ntiles, const uint32_t* __restrict__ cnt) {
+    const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const size_t w = blockIdx.y;
+    const size_t i = w * np + j;
+    const uint32_t key = kin[i];
+    if (key >= nb) return;
+    const size_t t = j / T;
+    const size_t pos = (size_t)cnt[(w * ntiles + t) * nb + key] + rank[i];
+    if (pos < total) kvout[pos] = make_uint2(key, vin[i]);
 }
 
 // ---------------------------------------------------------------- stages 4-5
@@ -1547,6 +1640,9 @@ struct Plan {
     size_t off_status, off_points, off_keys0, off_vals0, off_keys1, off_vals1, off_kv, off_rank, off_hist, off_dtot;
     int counting;                      // counting sort (else LSD radix sort)
     size_t nbins, off_bins, off_bsum;  // counting sort: bins (window, key) and scan tile totals
+    uint32_t ttiles, tT;               // counting sort in shared-memory tiles: tiles per window, items per
+                                       // tile (ttiles = 0: global counters)
+    size_t off_tcnt;                   // per-tile counts and prefixes [W][ttiles][Bp + 1]
     size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
     size_t off_S, off_start, total;
 };
@@ -1613,6 +1709,7 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
     p->W = p->pre ? 1 : p->Wd;
     p->items = p->pre ? (size_t)p->Wd * np : np;
     if (p->items >= (1ull << 31)) return false;
+    if ((uint64_t)p->W * p->items >= (1ull << 32)) return false;   // bin offsets are 32-bit
     const size_t items = p->items;
     p->B = p->sgn ? (1u << (p->c - 1)) : ((1u << p->c) - 1u);
     p->Bp = p->sgn ? p->B : (1u << p->c);
@@ -1632,6 +1729,25 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
     const int tg = (p->sgn && lgn < 32) ? g_gtable[tmode][lgn].load(std::memory_order_relaxed) : 0;
     p->counting = ((o->flags & MSM377_RADIX_SORT) || tsort == 2) ? 0 : 1;
     p->tiles = (items + kSortTile - 1) / kSortTile;
+    // Counting in shared-memory tiles when a block's packed counters fit: tiles of
+    // fewer than 2^16 items, about one wave of 1024-thread blocks (two per SM when
+    // the counters take at most 100 KB), and at least ~1024 items a tile.
+    p->ttiles = 0;
+    p->tT = 0;
+    {
+        const size_t smem = (size_t)((p->Bp + 2) / 2) * 4;
+        if (p->counting && items > 0 && smem <= kTileSmemMax) {
+            const size_t per_sm = smem <= 100 * 1024 ? 2 : 1;
+            const size_t fewest = (items + kTileItemsMax - 1) / kTileItemsMax;
+            size_t tl = (152 * per_sm + p->W - 1) / p->W;
+            const size_t cap = (items + 1023) / 1024;
+            if (tl > cap) tl = cap;
+            if (tl < fewest) tl = fewest;
+            if (tl < 1) tl = 1;
+            p->ttiles = (uint32_t)tl;
+            p->tT = (uint32_t)((items + tl - 1) / tl);
+        }
+    }
     // Window groups (a schedule option): the accumulation runs group by group on the
     // caller's stream and each group's merges, bucket reduction and per-window sums
     // run on a higher-priority helper stream as soon as its accumulation is done,
@@ -1700,6 +1816,7 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
     p->nbins = (size_t)p->W * (p->Bp + 1);  // keys 0 .. Bp of every window
     p->off_bins = take(p->nbins * 4);
     p->off_bsum = take(((p->nbins + kScanTile - 1) / kScanTile) * 4);
+    p->off_tcnt = take((size_t)p->W * p->ttiles * (p->Bp + 1) * 4);
     p->off_buckets = take((size_t)p->W * p->Bp * XY);
     p->off_head = take(chunks * XY);
     p->off_tail = take(chunks * XY);
@@ -1916,14 +2033,30 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
         uint32_t* bsum = at<uint32_t>(workspace, p.off_bsum);
         uint32_t* rank = at<uint32_t>(workspace, p.off_rank);
         const size_t ntiles = (p.nbins + kScanTile - 1) / kScanTile;
-        MSM_CUDA_TRY(cudaMemsetAsync(bins, 0, p.nbins * 4, s));
         const dim3 gw(grid_for(np, 256), (unsigned)p.W);
-        k_bin_count<<<gw, 256, 0, s>>>(keys[0], np, nb, bins, rank);
+        uint32_t* tcnt = at<uint32_t>(workspace, p.off_tcnt);
+        if (p.ttiles) {
+            // the counters of one block exceed the default 48 KB of dynamic shared memory
+            const size_t smem = (size_t)((nb + 1) / 2) * 4;
+            MSM_CUDA_TRY(cudaFuncSetAttribute(k_tile_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kTileSmemMax));
+            k_tile_count<<<dim3(p.ttiles, (unsigned)p.W), kTileThreads, smem, s>>>(keys[0], np, nb, p.tT, p.ttiles,
+                                                                                  tcnt, rank);
+            k_tile_totals<<<grid_for(p.nbins, 256), 256, 0, s>>>(tcnt, nb, p.ttiles, (uint32_t)p.W, bins);
+        } else {
+            MSM_CUDA_TRY(cudaMemsetAsync(bins, 0, p.nbins * 4, s));
+            k_bin_count<<<gw, 256, 0, s>>>(keys[0], np, nb, bins, rank);
+        }
         k_scan_tiles<<<(unsigned)ntiles, kScanBlock, 0, s>>>(bins, p.nbins, bsum);
         k_scan_totals<<<1, kScanBlock, 0, s>>>(bsum, ntiles);
         k_scan_add<<<grid_for(p.nbins, 256), 256, 0, s>>>(bins, p.nbins, bsum);
-        k_bin_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], rank, kv, total, np, nb, bins);
-        note_launches(5);
+        if (p.ttiles) {
+            k_tile_offsets<<<grid_for(p.nbins, 256), 256, 0, s>>>(tcnt, nb, p.ttiles, (uint32_t)p.W, bins);
+            k_tile_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], rank, kv, total, np, nb, p.tT, p.ttiles, tcnt);
+        } else {
+            k_bin_scatter<<<gw, 256, 0, s>>>(keys[0], vals[0], rank, kv, total, np, nb, bins);
+        }
+        note_launches(p.ttiles ? 7 : 5);
     } else {
         uint32_t* hist = at<uint32_t>(workspace, p.off_hist);
         uint32_t* dtot = at<uint32_t>(workspace, p.off_dtot);

@@ -46,6 +46,11 @@ def test_host_only_entry_points():
     assert L.msm_g1_workspace_bytes(10, ctypes.byref(pkg._opts(c=21))) == 0
     assert L.msm_g1_workspace_bytes(10, ctypes.byref(pkg._opts(scalar_bits=257))) == 0
     assert [pkg.msm_g1_default_c(1 << k) for k in (12, 20, 22)] == [8, 16, 17]
+    # the sort's bin offsets are 32-bit: windows x items per window must stay below 2^32
+    # (c = 16 signed over 253-bit scalars: 16 windows)
+    o16 = pkg._opts(c=16, signed=True, scalar_bits=253)
+    assert L.msm_g1_workspace_bytes((1 << 28) - 1, ctypes.byref(o16)) > 0
+    assert L.msm_g1_workspace_bytes(1 << 28, ctypes.byref(o16)) == 0
 
 
 def test_invalid_arguments_fail_before_touching_the_gpu():
