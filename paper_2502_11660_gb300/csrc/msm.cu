@@ -1217,6 +1217,8 @@ struct AccArgs {
     uint32_t Bp;
     int K;
     int w0, nwin;          // window range of this launch
+    const uint32_t* bin;   // counting sort: first kv slot of each (window, key) bin (else null)
+    uint32_t nb;           // keys per window (Bp + 1)
 };
 
 // Mixed additions of chunk t of window w. Flushes each run to its bucket, or to
@@ -1312,9 +1314,13 @@ __global__ void __launch_bounds__(128, M::kAccBlocks) k_accumulate_batched(const
     }
 }
 
-// Partial sums of runs that cross chunk edges are combined in log depth, so a
-// bucket holding a large share of the window (all-equal scalars, a nearly empty
-// top window) costs O(log) serial additions, not O(chunks):
+// Partial sums of runs that cross chunk edges. A run that continues into at most
+// kWalkHeads later chunks (the runs of random scalars at the usual chunk sizes) is
+// finished by the thread of its tail chunk, which adds the run's head partials in
+// order (k_merge_walk). Longer
+// runs are combined in log depth, so a bucket holding a large share of the window
+// (all-equal scalars, a nearly empty top window) costs O(log) serial additions, not
+// O(chunks); those kernels return at once unless the walk left such a run:
 //  * k_merge_start: for a chunk u whose first run continues an earlier chunk's
 //    run, start[u] = the chunk t0 where that run begins (its tail): the run's key
 //    first occurs at lower_bound(keys, key) in the sorted window, so t0 is that
@@ -1328,7 +1334,52 @@ __global__ void __launch_bounds__(128, M::kAccBlocks) k_accumulate_batched(const
 //    2 kMergeRounds, ...) over that run alone between block barriers. When no run is
 //    that long the launch returns at once: one launch instead of a dozen idle rounds;
 //  * k_merge_final: bucket = tail[start] + that sum.
-__global__ void k_merge_start(AccArgs a, int32_t* __restrict__ start, int* __restrict__ maxspan) {
+constexpr uint32_t kWalkHeads = 8;
+
+template <class M>
+__global__ void k_merge_walk(AccArgs a, int* __restrict__ longrun) {
+    const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (uint32_t)a.nwin * a.cpw) return;
+    const int w = a.w0 + (int)(id / a.cpw);
+    const uint32_t t = id % a.cpw;
+    const size_t ci = (size_t)w * a.cpw + t;
+    const uint32_t key = a.tailkey[ci];
+    if (key == kNone) return;
+    typename M::acc acc;
+    M::load(acc, a.tail + ci * kXyzzVec);
+    // The run starts in chunk t (a run that began earlier would make chunk t a head);
+    // it ends where its bin ends, so it has nh = (last item) / K - t heads. Without the
+    // bin table (radix sort) the heads' flags are counted instead.
+    uint32_t nh = kWalkHeads + 1;
+    if (a.bin) {
+        const size_t b = (size_t)w * a.nb + key;
+        const size_t end = key + 1 < a.nb ? (size_t)a.bin[b + 1] - (size_t)w * a.n : a.n;   // within the window
+        nh = (uint32_t)((end - 1) / (size_t)a.K) - t;
+    } else {
+#pragma unroll
+        for (uint32_t h = kWalkHeads + 1; h >= 1; --h) {
+            const uint32_t f = t + h < a.cpw ? a.headflag[ci + h] : 0u;
+            if (f == 0) nh = h - 1;      // the run ended before chunk t + h
+            if (f == 1) nh = h;          // the run ends in chunk t + h
+        }
+    }
+    if (nh > kWalkHeads) {               // tail key and all, for k_merge_start .. k_merge_final
+        *longrun = 1;
+        return;
+    }
+    for (uint32_t h = 1;; ++h) {       // the heads up to the one with flag 1
+        const uint32_t f = t + h < a.cpw ? a.headflag[ci + h] : 0u;
+        if (f == 0 || h > nh) break;     // the run ended before chunk t + h
+        M::add_mem(acc, a.head + (ci + h) * kXyzzVec);
+        if (f == 1) break;               // the run ends in chunk t + h
+    }
+    M::store(a.buckets + ((size_t)w * a.Bp + (key - 1)) * kXyzzVec, acc);
+    a.tailkey[ci] = kNone;
+}
+
+__global__ void k_merge_start(AccArgs a, const int* __restrict__ longrun, int32_t* __restrict__ start,
+                              int* __restrict__ maxspan) {
+    if (*longrun == 0) return;  // every run was finished by the walk
     const size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (id >= (size_t)a.nwin * a.cpw) return;
     const int w = a.w0 + (int)(id / a.cpw);
@@ -1433,7 +1484,8 @@ __global__ void __launch_bounds__(kMergeLongThreads) k_merge_long(AccArgs a, con
 }
 
 template <class M>
-__global__ void k_merge_final(AccArgs a) {
+__global__ void k_merge_final(AccArgs a, const int* __restrict__ longrun) {
+    if (*longrun == 0) return;  // every run was finished by the walk
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (uint32_t)a.nwin * a.cpw) return;
     const int w = a.w0 + (int)(id / a.cpw);
@@ -1685,6 +1737,9 @@ int default_c(size_t n, int sgn, uint32_t flags) {
 }
 
 constexpr int kMaxGroups = 8;
+// status words: the call's status, then per window group the longest run's head count
+// (k_merge_start) and whether a run outgrew the walk (k_merge_walk)
+constexpr int kStatusWords = 1 + 2 * kMaxGroups;
 
 // allow_groups = false: one window group (batched calls overlap whole jobs instead).
 bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
@@ -2006,7 +2061,7 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     const size_t n = p.n;
     int* status = at<int>(workspace, p.off_status);
     if (reset_status)
-        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, (1 + kMaxGroups) * sizeof(int), s));  // status, longest runs
+        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, kStatusWords * sizeof(int), s));  // status, longest runs
     const uint4* pts = reinterpret_cast<const uint4*>(points);
     if ((opts->flags & MSM377_VALIDATE) && !(opts->flags & MSM377_POINTS_PREPARED)) {
         const int r = launch_validate(points, n, (opts->flags & (MSM377_EDWARDS | MSM377_GLV)) != 0, status, s);
@@ -2089,6 +2144,8 @@ int enqueue_head(const Plan& p, const uint32_t* points, const uint32_t* scalars,
     a.K = p.K;
     a.w0 = 0;
     a.nwin = p.W;
+    a.bin = p.counting ? at<uint32_t>(workspace, p.off_bins) : nullptr;
+    a.nb = p.Bp + 1;
     return check_launch("msm head");
 }
 
@@ -2108,8 +2165,10 @@ int enqueue_group_tail_m(const Plan& p, const AccArgs& a, int g, void* workspace
     // 5. merge partial sums of runs crossing chunk edges (log depth)
     int32_t* start = at<int32_t>(workspace, p.off_start);
     int* maxspan = at<int>(workspace, p.off_status) + 1 + g;
-    k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, maxspan);
-    note_launches(1);
+    int* longrun = at<int>(workspace, p.off_status) + 1 + kMaxGroups + g;
+    k_merge_walk<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, longrun);
+    k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, longrun, start, maxspan);
+    note_launches(2);
     for (uint32_t d = 1; d < p.cpw && d < kMergeRounds; d <<= 1) {
         k_merge_round<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d, maxspan);
         note_launches(1);
@@ -2122,7 +2181,7 @@ int enqueue_group_tail_m(const Plan& p, const AccArgs& a, int g, void* workspace
         k_merge_long<M><<<(unsigned)(want < cap ? want : cap), kMergeLongThreads, 0, s>>>(a, start, maxspan);
         note_launches(1);
     }
-    k_merge_final<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a);
+    k_merge_final<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, longrun);
     note_launches(1);
     // 6. bucket reduction of the group's windows
     const size_t WG = (size_t)a.nwin * p.G;
@@ -2360,7 +2419,7 @@ int msm_g1_run(const uint32_t* points, const uint32_t* scalars, size_t n, uint32
     int r;
     if (split && ov) {
         int* status = at<int>(workspace, p.off_status);
-        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, (1 + kMaxGroups) * sizeof(int), s));
+        MSM_CUDA_TRY(cudaMemsetAsync(status, 0, kStatusWords * sizeof(int), s));
         MSM_CUDA_TRY(cudaEventRecord(ov->ev[0], s));
         MSM_CUDA_TRY(cudaStreamWaitEvent(ov->hi, ov->ev[0], 0));
         if (opts->flags & MSM377_VALIDATE) {
@@ -2552,7 +2611,7 @@ extern "C" int msm_g1_host(const uint32_t* points_host, const uint32_t* scalars_
     int r = device_aux(&aux);
     if (r) return r;
     cudaStream_t sc = aux->st[0];
-    MSM_CUDA_TRY(cudaMemsetAsync(at<int>(workspace, p.off_status), 0, (1 + kMaxGroups) * sizeof(int), s));  // before the fork
+    MSM_CUDA_TRY(cudaMemsetAsync(at<int>(workspace, p.off_status), 0, kStatusWords * sizeof(int), s));  // before the fork
     r = fork_from(aux, s, 1 + kHostChunks);
     if (r) return r;
     uint4* prep = at<uint4>(workspace, p.off_points);
