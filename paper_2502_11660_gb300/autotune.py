@@ -89,6 +89,20 @@ def candidates(log2n: int, glv: bool = False, precomputed: bool = False) -> list
     return sorted({max(3, base - 2), max(3, base - 1), base, base + 1, base + 2})
 
 
+# Window widths timed within this fraction of the fastest count as a tie, and the widest
+# of them is kept: fewer windows mean fewer mixed additions, which is what counts when
+# several MSMs share the GPU (batched calls, serving). Measured on GB300 at n = 2^16:
+# c = 12 and 16 within 0.4 % of each other alone, but 64 batched jobs took 37 ms with
+# c = 16 at that size and 53 ms with c = 12.
+C_TIE = 0.01
+
+
+def pick_c(t: dict) -> int:
+    """The widest window among those timed within C_TIE of the fastest."""
+    best = min(t.values())
+    return max(c for c, ms in t.items() if ms <= best * (1 + C_TIE))
+
+
 def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda", edwards: bool = False,
          glv: bool = False, precomputed: bool = False) -> dict:
     """Returns {"table": [c by log2 n], "timings": {k: {c: ms}}}; fills gaps from neighbours."""
@@ -99,7 +113,7 @@ def tune(log2_sizes=range(10, 23, 2), reps: int = 3, device="cuda", edwards: boo
         t = {c: time_msm(n, c, reps, device, edwards=edwards, glv=glv, precomputed=precomputed)
              for c in candidates(k, glv, precomputed)}
         timings[k] = t
-        best[k] = min(t, key=t.get)
+        best[k] = pick_c(t)
     table = [0] * 32
     keys = sorted(best)
     for k in range(32):
@@ -130,7 +144,7 @@ GROUPS = (1, 2, 4)
 
 def tune_schedule(log2_sizes=range(10, 23), reps: int = 3, device="cuda", edwards: bool = False,
                   glv: bool = False) -> dict:
-    """Per size: the window width c (candidates as in tune()), then, at that c, the chunk
+    """Per size: the window width c (candidates as in tune(), ties to the widest), then, at that c, the chunk
     size, the sort, the number of level-1 reduction threads and the window groups, one
     coordinate at a time (each step keeps the fastest value; 0 = the built-in rule).
     Installs every entry as it goes and returns {"schedule": {k: (c, chunk, sort,
@@ -142,7 +156,7 @@ def tune_schedule(log2_sizes=range(10, 23), reps: int = 3, device="cuda", edward
         rec = {}
         t = {c: time_schedule(n, c, 0, 0, 0, 0, reps, device, edwards=edwards, glv=glv)
              for c in candidates(k, glv)}
-        cur[0] = min(t, key=t.get)
+        cur[0] = pick_c(t)
         rec["c"] = t
         for field, values in ((1, CHUNKS), (2, SORTS), (3, REDUCE_LOG2), (4, GROUPS)):
             t = {}

@@ -1314,13 +1314,16 @@ __global__ void __launch_bounds__(128, M::kAccBlocks) k_accumulate_batched(const
     }
 }
 
-// Partial sums of runs that cross chunk edges. A run that continues into at most
-// kWalkHeads later chunks (the runs of random scalars at the usual chunk sizes) is
-// finished by the thread of its tail chunk, which adds the run's head partials in
-// order (k_merge_walk). Longer
-// runs are combined in log depth, so a bucket holding a large share of the window
-// (all-equal scalars, a nearly empty top window) costs O(log) serial additions, not
-// O(chunks); those kernels return at once unless the walk left such a run:
+// Partial sums of runs that cross chunk edges. When a bucket's run is expected to be
+// no longer than a chunk (items per bucket <= K), a run that continues into at most
+// kWalkHeads later chunks (every run of random scalars then) is finished by the
+// thread of its tail chunk, which adds the run's head partials in order
+// (k_merge_walk). With longer runs, serial additions on one thread would cost more
+// than the rounds below (measured at n = 2^22, c = 16: 256 items per bucket, chunks
+// of 64, 1 ms slower), so the walk is skipped and every run takes the log-depth path.
+// Longer runs are combined in log depth, so a bucket holding a large share of the
+// window (all-equal scalars, a nearly empty top window) costs O(log) serial additions,
+// not O(chunks); those kernels return at once unless the walk left such a run:
 //  * k_merge_start: for a chunk u whose first run continues an earlier chunk's
 //    run, start[u] = the chunk t0 where that run begins (its tail): the run's key
 //    first occurs at lower_bound(keys, key) in the sorted window, so t0 is that
@@ -1334,10 +1337,10 @@ __global__ void __launch_bounds__(128, M::kAccBlocks) k_accumulate_batched(const
 //    2 kMergeRounds, ...) over that run alone between block barriers. When no run is
 //    that long the launch returns at once: one launch instead of a dozen idle rounds;
 //  * k_merge_final: bucket = tail[start] + that sum.
-constexpr uint32_t kWalkHeads = 8;
+constexpr uint32_t kWalkHeads = 4;
 
 template <class M>
-__global__ void k_merge_walk(AccArgs a, int* __restrict__ longrun) {
+__global__ void k_merge_walk(AccArgs a, uint32_t H, int* __restrict__ longrun) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (uint32_t)a.nwin * a.cpw) return;
     const int w = a.w0 + (int)(id / a.cpw);
@@ -1350,20 +1353,19 @@ __global__ void k_merge_walk(AccArgs a, int* __restrict__ longrun) {
     // The run starts in chunk t (a run that began earlier would make chunk t a head);
     // it ends where its bin ends, so it has nh = (last item) / K - t heads. Without the
     // bin table (radix sort) the heads' flags are counted instead.
-    uint32_t nh = kWalkHeads + 1;
+    uint32_t nh = H + 1;
     if (a.bin) {
         const size_t b = (size_t)w * a.nb + key;
         const size_t end = key + 1 < a.nb ? (size_t)a.bin[b + 1] - (size_t)w * a.n : a.n;   // within the window
         nh = (uint32_t)((end - 1) / (size_t)a.K) - t;
     } else {
-#pragma unroll
-        for (uint32_t h = kWalkHeads + 1; h >= 1; --h) {
+        for (uint32_t h = H + 1; h >= 1; --h) {
             const uint32_t f = t + h < a.cpw ? a.headflag[ci + h] : 0u;
             if (f == 0) nh = h - 1;      // the run ended before chunk t + h
             if (f == 1) nh = h;          // the run ends in chunk t + h
         }
     }
-    if (nh > kWalkHeads) {               // tail key and all, for k_merge_start .. k_merge_final
+    if (nh > H) {                        // tail key and all, for k_merge_start .. k_merge_final
         *longrun = 1;
         return;
     }
@@ -1695,6 +1697,7 @@ struct Plan {
     uint32_t ttiles, tT;               // counting sort in shared-memory tiles: tiles per window, items per
                                        // tile (ttiles = 0: global counters)
     size_t off_tcnt;                   // per-tile counts and prefixes [W][ttiles][Bp + 1]
+    uint32_t walk;                     // heads a run's tail thread adds itself (0: no walk)
     size_t off_buckets, off_head, off_tail, off_headflag, off_tailkey, off_Y, off_V, off_P0, off_P1;
     size_t off_S, off_start, total;
 };
@@ -1832,6 +1835,7 @@ bool make_plan(size_t n, const msm_opts* o, Plan* p, bool allow_groups = true) {
     if (tk > 0) K = (size_t)tk;        // measured choice (2..256)
     p->K = (int)K;
     p->cpw = (uint32_t)((items + K - 1) / K);
+    p->walk = (items + p->Bp - 1) / p->Bp <= K ? kWalkHeads : 0u;   // runs about a chunk long at most
     if (p->cpw == 0) p->cpw = 1;
     // bucket reduction geometry: segments of L buckets, the longest L that still
     // leaves kReduceThreads level-1 threads over all windows (longer segments mean
@@ -2166,9 +2170,14 @@ int enqueue_group_tail_m(const Plan& p, const AccArgs& a, int g, void* workspace
     int32_t* start = at<int32_t>(workspace, p.off_start);
     int* maxspan = at<int>(workspace, p.off_status) + 1 + g;
     int* longrun = at<int>(workspace, p.off_status) + 1 + kMaxGroups + g;
-    k_merge_walk<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, longrun);
+    if (p.walk) {
+        k_merge_walk<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, p.walk, longrun);
+        note_launches(1);
+    } else {
+        MSM_CUDA_TRY(cudaMemsetAsync(longrun, 1, 1, s));   // nonzero: every run takes the rounds
+    }
     k_merge_start<<<grid_for(nchunks, 128), 128, 0, s>>>(a, longrun, start, maxspan);
-    note_launches(2);
+    note_launches(1);
     for (uint32_t d = 1; d < p.cpw && d < kMergeRounds; d <<= 1) {
         k_merge_round<M><<<grid_for(nchunks, 128), 128, 0, s>>>(a, start, d, maxspan);
         note_launches(1);

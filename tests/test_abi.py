@@ -254,3 +254,14 @@ def test_paper_format_constants_match_the_oracle():
 
     assert elems("kPEl") == fq.P
     assert elems("kMuEl") == (1 << (2 * barrett.LOOSE_K)) // fq.P
+
+
+def test_window_tuner_breaks_near_ties_toward_the_widest_window():
+    from paper_2502_11660_gb300 import autotune
+    # the fastest wins when it is clearly faster
+    assert autotune.pick_c({12: 1.30, 16: 1.00, 17: 1.20}) == 16
+    assert autotune.pick_c({11: 0.926, 12: 0.979, 13: 1.04}) == 11
+    # within C_TIE of the fastest, the widest window is kept (fewer windows, less work)
+    assert autotune.pick_c({12: 1.181, 13: 1.22, 16: 1.186, 17: 1.583}) == 16
+    assert autotune.pick_c({16: 20.69, 17: 20.25}) == 17
+    assert autotune.pick_c({5: 1.0}) == 5
