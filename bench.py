@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--c", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="with --c: items per accumulation thread for the run (0 = the built-in rule)")
     ap.add_argument("--mode", default="best", choices=["best"] + list(MODES))
     ap.add_argument("--no-extras", action="store_true", help="skip every extra beyond the headline")
     ap.add_argument("--only", default="", choices=["", "batch_ops"],
@@ -409,11 +411,15 @@ class Harness:
         return [a.elapsed_time(b) for a, b in ev], stages
 
 
-def tuned_c(pkg, autotune, dev, log2n, edw, gl, pre, forced=0):
+def tuned_c(pkg, autotune, dev, log2n, edw, gl, pre, forced=0, chunk=0):
     """c for (mode, 2^log2n): the autotuner's measured choice (installed into the
     library's tables for that mode; variable-base modes also tune the chunk size, the
-    sort, the reduction threads and the window groups), or `forced`."""
+    sort, the reduction threads and the window groups), or `forced` (with `chunk`
+    items per accumulation thread when nonzero)."""
     if forced:
+        if chunk and not pre:
+            autotune.install_schedule({log2n: [forced, chunk, 0, 0, 0]}, edwards=edw, glv=gl)
+            return forced, f"given, chunk {chunk}", None
         return forced, "given", None
     if pre:
         tuning = autotune.tune(log2_sizes=[log2n], reps=3, device=dev, edwards=edw, glv=gl, precomputed=pre)
@@ -426,11 +432,11 @@ def tuned_c(pkg, autotune, dev, log2n, edw, gl, pre, forced=0):
     return entry[0], {f: {str(v): round(t, 3) for v, t in d.items()} for f, d in ms.items()}, list(entry)
 
 
-def survey_mode(h, autotune, name, n, pts_std, sc_dev, ks, warmup, forced_c=0):
+def survey_mode(h, autotune, name, n, pts_std, sc_dev, ks, warmup, forced_c=0, chunk=0):
     """Autotune, prepare and time one mode for 10 steps; check one result against the closed form."""
     pkg, torch, dev = h.pkg, h.torch, h.dev
     edw, gl, pre = MODES[name]
-    c, timings, entry = tuned_c(pkg, autotune, dev, int(np.log2(n)), edw, gl, pre, forced_c)
+    c, timings, entry = tuned_c(pkg, autotune, dev, int(np.log2(n)), edw, gl, pre, forced_c, chunk)
     t0 = time.perf_counter()
     if pre:
         prep = pkg.msm_points_precompute(pts_std, c=c, scalar_bits=BITS, glv=gl)
@@ -486,7 +492,8 @@ def run_ours(args):
     survey, preps = {}, {}
     wanted = VARIABLE_MODES if args.mode == "best" else (args.mode,)
     for name in wanted:
-        survey[name], preps[name] = survey_mode(h, autotune, name, n, pts_std, sc_dev, ks, args.warmup, args.c)
+        survey[name], preps[name] = survey_mode(h, autotune, name, n, pts_std, sc_dev, ks, args.warmup, args.c,
+                                                args.chunk)
     mode = agree_on(min(survey, key=lambda m: survey[m]["ms_per_step"]), world)
     prep, ws, c, edw, gl, pre = preps[mode]
     for other in list(preps):
