@@ -89,11 +89,11 @@ def candidates(log2n: int, glv: bool = False, precomputed: bool = False) -> list
     return sorted({max(3, base - 2), max(3, base - 1), base, base + 1, base + 2})
 
 
-# Window widths timed within this fraction of the fastest count as a tie, and the widest
-# of them is kept: fewer windows mean fewer mixed additions, which is what counts when
-# several MSMs share the GPU (batched calls, serving). Measured on GB300 at n = 2^16:
-# c = 12 and 16 within 0.4 % of each other alone, but 64 batched jobs took 37 ms with
-# c = 16 at that size and 53 ms with c = 12.
+# Window widths timed within this fraction of the fastest count as a tie (about the
+# run-to-run spread of these timings on GB300: at n = 2^16, c = 12 and c = 16 came out
+# 0.4 % apart in one run and 1.4 % apart, either way, in two others), and the widest is
+# kept: fewer windows mean fewer mixed additions, which is what counts when several MSMs
+# share the GPU (batched calls, serving).
 C_TIE = 0.01
 
 
