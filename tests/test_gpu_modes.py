@@ -420,3 +420,24 @@ def test_few_distinct_scalars_long_runs(edw, split):
     want = closed_form_limbs(s, a)
     for c, sg in [(6, True), (10, True), (9, False)]:
         assert run(pts, a, c=c, signed=sg, scalar_bits=253, edwards=edw, glv=split) == want
+
+
+@pytest.mark.parametrize("edw,split", [(False, False)] + MODES, ids=["xyzz"] + MODE_IDS)
+def test_short_runs_walked_beside_long_runs(edw, split):
+    """Wide windows (c = 13, 14 over 2^14 points: a few items per bucket, so the tail
+    thread of each run adds the run's heads itself) with scalars drawn mostly from five
+    values: the buckets of those values hold thousands of points and take the log-depth
+    merge, while the random quarter's short runs are finished by the walk in the same call."""
+    n = 1 << 14
+    a, s, pts = msm_inputs(n, tag=611)
+    a = a.copy()
+    rng = np.random.default_rng(611)
+    pick = rng.integers(0, 5, n)
+    keep = rng.random(n) < 0.25
+    a[~keep] = a[pick[~keep]]
+    want = closed_form_limbs(s, a)
+    for c in (13, 14):
+        assert run(pts, a, c=c, signed=True, scalar_bits=253, edwards=edw, glv=split) == want
+    # random scalars only: every run short
+    a2, _ = synth.workloads.msm(n, 612)
+    assert run(pts, a2, c=14, signed=True, scalar_bits=253, edwards=edw, glv=split) == closed_form_limbs(s, a2)
